@@ -1,0 +1,164 @@
+/*
+ * hd.h -- C ABI of the GB300 (sm_103a) branch-and-bound for the one-sided
+ * Pompeiu-Hausdorff distance between triangle soups,
+ *
+ *     h(A, B) = max_{p in A} min_{q in B} |p - q|          (Section 3, Eq. hausdorff_distance)
+ *
+ * after Sacht & Jacobson, "Cascading upper bounds for triangle soup
+ * Pompeiu-Hausdorff distance" (SGP 2024).  A call returns l <= h(A,B) <= u with
+ * u - l <= eps (Section 3, Eq. output_bounds; the stopping rule of Section 3.1).
+ *
+ * Conventions for every entry point:
+ *   - Meshes are triangle soups: V is row-major nV x 3 (float32 or float64),
+ *     F is row-major nF x 3 int32 vertex indices (Section 3, first paragraph).
+ *   - Pointers are host or device memory as each argument says; the caller owns
+ *     them.  Host arrays are copied before the call returns.  Device arrays must
+ *     stay valid until the work queued on `stream` has finished.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Entry points that return results to the host synchronise that stream.
+ *   - Every entry point returns an HD_* status code; hd_status_str() names it.
+ *     On HD_ERR_INVALID nothing was launched.  On HD_ERR_CUDA the CUDA error
+ *     string is available from hd_last_error().
+ */
+#ifndef HD_H_
+#define HD_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+enum {
+  HD_OK = 0,            /* done; the bracket is within tolerance                        */
+  HD_ERR_INVALID = 1,   /* bad argument: empty mesh, index out of range, non-finite
+                           coordinate, tol <= 0, unknown option                          */
+  HD_ERR_CAPACITY = 2,  /* face cap m * n_A (Section 4) or the frontier memory limit was
+                           reached; [lower, upper] is still a valid bracket of h           */
+  HD_ERR_NUMERIC = 3,   /* every sub-triangle was discarded while u > l: only rounding can
+                           do this (Section 5.3, mesh 441717); FP64 mode only              */
+  HD_ERR_TIMEOUT = 4,   /* max_rounds reached; [lower, upper] is a valid bracket           */
+  HD_ERR_CUDA = 5       /* a CUDA call failed; see hd_last_error()                         */
+};
+
+/* vertex element types */
+enum { HD_F32 = 0, HD_F64 = 1 };
+/* tolerance modes: eps = tol, or eps = tol * (bbox diagonal of A's referenced vertices) */
+enum { HD_TOL_ABS = 0, HD_TOL_REL = 1 };
+/* arithmetic of the bound and distance computations */
+enum {
+  HD_FP64 = 0,  /* IEEE double, round-to-nearest, as in the paper (Section 4)              */
+  HD_MIXED = 1  /* FP32 with certified (outward-rounded) bounds; FP64 only for sliver
+                   triangles of B whose FP32 result cannot be certified tightly            */
+};
+
+typedef struct {
+  const void* V;     /* nV x 3 vertices, element type vtype                               */
+  int64_t nV;
+  const int32_t* F;  /* nF x 3 vertex indices                                             */
+  int64_t nF;
+  int32_t vtype;     /* HD_F32 or HD_F64                                                  */
+  int32_t on_device; /* 1: V and F are device pointers on the current device; 0: host    */
+} hd_mesh;
+
+typedef struct {
+  int32_t tol_mode;        /* HD_TOL_ABS or HD_TOL_REL                                    */
+  int32_t precision;       /* HD_FP64 or HD_MIXED                                         */
+  double max_face_factor;  /* m of Section 4: at most m * n_A faces are processed
+                              (n_A + 4 per split); default 1e7                           */
+  int64_t frontier_chunk;  /* most sub-triangles split in one round (0 = automatic)       */
+  int32_t leaf_size;       /* triangles per BVH leaf, 1..16 (default 4)                   */
+  int32_t block_size;      /* threads per block of the round kernels (default 128)        */
+  uint8_t bound_order[4];  /* cascade order, values 1..4 = u1..u4 (default 1,2,3,4)        */
+  int32_t n_bounds;        /* how many entries of bound_order are used, 1..4 (default 4)  */
+  int64_t max_rounds;      /* frontier rounds before HD_ERR_TIMEOUT (default 1e6)         */
+  int64_t max_frontier_bytes; /* device memory for frontier + vertex pool (0 = automatic) */
+} hd_options;
+
+typedef struct {
+  int64_t rounds;            /* frontier rounds after round 0                              */
+  int64_t splits;            /* sub-triangles split 1->4 (Section 4's B&B iterations)      */
+  int64_t queries;           /* nearest-triangle queries (vertices of A and midpoints)     */
+  int64_t pointtri_evals;    /* point-triangle distance evaluations (leaf tests + u3)      */
+  int64_t box_tests;         /* BVH child-box distance evaluations                         */
+  int64_t discards[6];       /* sub-triangles discarded, by the deciding bound:
+                                exact, u1, u2, u3, u4 (index 5 unused)                     */
+  int64_t retired;           /* sub-triangles kept but never split again: l <= U <= l + eps */
+  int64_t fp64_escalations;  /* MIXED: point-triangle tests redone in FP64 (slivers)        */
+  int64_t peak_frontier;     /* largest live frontier                                       */
+  int64_t pool_vertices;     /* vertices created (referenced vertices of A + 3 per split)  */
+  double eps_abs;            /* absolute tolerance used                                     */
+  double dA;                 /* bbox diagonal of A's referenced vertices                    */
+} hd_stats;
+
+typedef struct {
+  double lower, upper; /* l <= h(A,B) <= u (valid on HD_OK, HD_ERR_CAPACITY, HD_ERR_TIMEOUT) */
+  int32_t status;
+  hd_stats stats;
+} hd_result;
+
+/* Opaque: B, its bounding-volume hierarchy and per-triangle data, on one device. */
+typedef struct hd_bvh hd_bvh;
+
+/* Fill *opt with the defaults listed above. */
+void hd_options_default(hd_options* opt);
+
+/* Build the BVH of B (Section 4: an AABB hierarchy over B, built once and used for the
+ * distances D, nearest triangles I and closest points C of points of A).  GPU build:
+ * Morton codes of the triangle centroids, radix sort, binary radix tree (Karras 2012),
+ * bottom-up boxes rounded outward, leaves of up to opt->leaf_size triangles.
+ * On HD_OK *out owns device memory until hd_free_B(*out).  opt may be NULL. */
+int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** out);
+
+/* Release everything hd_build_B allocated.  NULL is allowed. */
+void hd_free_B(hd_bvh* bvh);
+
+/* Triangle count of B and whether its vertices were given as float64. */
+int64_t hd_bvh_num_faces(const hd_bvh* bvh);
+
+/* One-sided h(A, B) to tolerance tol (Sections 3.1 and 4): returns [lower, upper] in
+ * *out.  A is read according to A->on_device.  The frontier-parallel rounds run on the
+ * GPU (nearest queries through the BVH, atomic lower bound, the exact case and the
+ * u1..u4 cascade, compaction and 1->4 split); only the final bracket and statistics
+ * come back to the host.  opt may be NULL (defaults). */
+int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
+                 hd_result* out);
+
+/* npairs independent problems h(As[i], Bs[i]) with one tolerance; outs[i] receives each
+ * result.  The pairs share the stream and the device.  Returns the first non-OK status
+ * (HD_ERR_INVALID/HD_ERR_CUDA abort; per-pair CAPACITY/TIMEOUT/NUMERIC are reported in
+ * outs[i].status and the call still returns HD_OK). */
+int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
+                         const hd_options* opt, void* stream, hd_result* outs);
+
+/* Batched nearest-triangle queries (the D, I, C of Section 4) for n points:
+ * P (device, n x 3, element type ptype) -> dist (device, n doubles), idx (device, n
+ * int32: row of F_B), foot (device, n x 3 doubles: the closest point).  precision
+ * HD_FP64 computes in double; HD_MIXED returns a certified bracket instead:
+ * dist = an upper bound of d(p, B) realised by triangle idx, foot its closest point,
+ * and, if dist_lo is not NULL, dist_lo (device, n doubles) a lower bound of d(p, B).
+ * Asynchronous on `stream`. */
+int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,
+               double* dist, int32_t* idx, double* foot, double* dist_lo);
+
+/* UpperBound(T, l) of Section 4 for n triangles given by their vertices and the
+ * vertices' nearest-triangle data (as returned by hd_nearest in HD_FP64):
+ * T (device, n x 9 doubles: v1, v2, v3), Td (n x 3), TI (n x 3 int32), Tq (n x 9),
+ * all device memory.  Writes U (n doubles) and code (n int32: 0 exact case,
+ * 1..4 the bound that discarded T (U < l), 5 kept: U = min of the computed bounds).
+ * FP64 arithmetic.  Asynchronous on `stream`. */
+int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const int32_t* TI, const double* Tq,
+                    int64_t n, double l, const hd_options* opt, void* stream, double* U, int32_t* code);
+
+/* Name of a status code (static string). */
+const char* hd_status_str(int status);
+
+/* Text of the last HD_ERR_CUDA on this thread (static buffer, "" if none). */
+const char* hd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HD_H_ */
