@@ -1,0 +1,248 @@
+"""Python binding of the GB300 Hausdorff branch-and-bound library (``include/hd.h``).
+
+Argument marshalling only: every step of the computation runs in ``libhd.so``'s CUDA
+kernels.  Arrays may be NumPy (host) or PyTorch tensors (host or CUDA); CUDA tensors are
+passed as device pointers on torch's current stream.  There is no CPU fallback: if the
+library is not built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhd.so")
+
+HD_OK, HD_ERR_INVALID, HD_ERR_CAPACITY, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_ERR_CUDA = range(6)
+HD_F32, HD_F64 = 0, 1
+HD_TOL_ABS, HD_TOL_REL = 0, 1
+HD_FP64, HD_MIXED = 0, 1
+BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
+
+
+class HdMesh(C.Structure):
+    _fields_ = [("V", C.c_void_p), ("nV", C.c_int64), ("F", C.c_void_p), ("nF", C.c_int64), ("vtype", C.c_int32),
+                ("on_device", C.c_int32)]
+
+
+class HdOptions(C.Structure):
+    _fields_ = [("tol_mode", C.c_int32), ("precision", C.c_int32), ("max_face_factor", C.c_double),
+                ("frontier_chunk", C.c_int64), ("leaf_size", C.c_int32), ("block_size", C.c_int32),
+                ("bound_order", C.c_uint8 * 4), ("n_bounds", C.c_int32), ("max_rounds", C.c_int64),
+                ("max_frontier_bytes", C.c_int64)]
+
+
+class HdStats(C.Structure):
+    _fields_ = [("rounds", C.c_int64), ("splits", C.c_int64), ("queries", C.c_int64), ("pointtri_evals", C.c_int64),
+                ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
+                ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
+                ("eps_abs", C.c_double), ("dA", C.c_double)]
+
+
+class HdResult(C.Structure):
+    _fields_ = [("lower", C.c_double), ("upper", C.c_double), ("status", C.c_int32), ("stats", HdStats)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded ``libhd.so``.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2406_10357_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+        L.hd_options_default.argtypes = [C.POINTER(HdOptions)]
+        L.hd_options_default.restype = None
+        L.hd_build_B.argtypes = [C.POINTER(HdMesh), C.POINTER(HdOptions), vp, C.POINTER(vp)]
+        L.hd_free_B.argtypes = [vp]
+        L.hd_free_B.restype = None
+        L.hd_bvh_num_faces.argtypes = [vp]
+        L.hd_bvh_num_faces.restype = i64
+        L.hd_hausdorff.argtypes = [vp, C.POINTER(HdMesh), d, C.POINTER(HdOptions), vp, C.POINTER(HdResult)]
+        L.hd_hausdorff_batched.argtypes = [C.POINTER(vp), C.POINTER(HdMesh), i64, d, C.POINTER(HdOptions), vp,
+                                           C.POINTER(HdResult)]
+        L.hd_nearest.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
+        L.hd_upper_bounds.argtypes = [vp, vp, vp, vp, vp, i64, d, C.POINTER(HdOptions), vp, vp, vp]
+        L.hd_status_str.argtypes = [C.c_int]
+        L.hd_status_str.restype = C.c_char_p
+        L.hd_last_error.restype = C.c_char_p
+        for f in ("hd_build_B", "hd_hausdorff", "hd_hausdorff_batched", "hd_nearest", "hd_upper_bounds"):
+            getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class HdError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = f"{what}: {hd_status_str(status)}"
+        if status == HD_ERR_CUDA:
+            msg += f" ({lib().hd_last_error().decode()})"
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(rc: int, what: str):
+    if rc != HD_OK:
+        raise HdError(rc, what)
+
+
+def hd_status_str(status: int) -> str:
+    return lib().hd_status_str(status).decode()
+
+
+def hd_options_default(**kw) -> HdOptions:
+    """Defaults of ``hd_options_default``; keyword arguments override fields
+    (``bound_order`` may be a sequence of 1..4, which also sets ``n_bounds``)."""
+    o = HdOptions()
+    lib().hd_options_default(C.byref(o))
+    for k, v in kw.items():
+        if k == "bound_order":
+            v = list(v)
+            for i in range(4):
+                o.bound_order[i] = v[i] if i < len(v) else 0
+            o.n_bounds = len(v)
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def _is_torch(x) -> bool:
+    return hasattr(x, "data_ptr") and hasattr(x, "is_cuda")
+
+
+def _stream(on_device: bool, stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    if on_device:
+        import torch
+
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(0)
+
+
+def _mesh(V, F):
+    """HdMesh view of (V, F) plus the objects that must stay alive during the call."""
+    if _is_torch(V):
+        import torch
+
+        V = V.contiguous()
+        if V.dtype not in (torch.float32, torch.float64):
+            V = V.double()
+        F = F.to(device=V.device, dtype=torch.int32).contiguous()
+        m = HdMesh(V.data_ptr(), V.shape[0], F.data_ptr(), F.shape[0], HD_F64 if V.dtype == torch.float64 else HD_F32,
+                   1 if V.is_cuda else 0)
+        return m, (V, F), bool(V.is_cuda)
+    V = np.ascontiguousarray(V)
+    if V.dtype not in (np.float32, np.float64):
+        V = V.astype(np.float64)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    m = HdMesh(V.ctypes.data, V.shape[0], F.ctypes.data, F.shape[0], HD_F64 if V.dtype == np.float64 else HD_F32, 0)
+    return m, (V, F), False
+
+
+class Bvh:
+    """Owner of an ``hd_bvh*`` (freed with ``hd_free_B`` when collected)."""
+
+    def __init__(self, handle: int, nF: int):
+        self.handle = C.c_void_p(handle)
+        self.nF = nF
+
+    def __del__(self):
+        if getattr(self, "handle", None) and self.handle.value and _lib is not None:
+            _lib.hd_free_B(self.handle)
+            self.handle = C.c_void_p(0)
+
+
+def hd_build_B(V, F, opt: HdOptions | None = None, stream=None) -> Bvh:
+    """Build the BVH of B (host or device arrays)."""
+    m, keep, dev = _mesh(V, F)
+    out = C.c_void_p(0)
+    _check(lib().hd_build_B(C.byref(m), C.byref(opt) if opt else None, _stream(dev, stream), C.byref(out)),
+           "hd_build_B")
+    return Bvh(out.value, int(m.nF))
+
+
+def hd_free_B(bvh: Bvh):
+    if bvh.handle.value:
+        lib().hd_free_B(bvh.handle)
+        bvh.handle = C.c_void_p(0)
+
+
+def _result(r: HdResult) -> dict:
+    s = r.stats
+    return dict(lower=r.lower, upper=r.upper, status=r.status, status_str=hd_status_str(r.status),
+                stats=dict(rounds=s.rounds, splits=s.splits, queries=s.queries, pointtri_evals=s.pointtri_evals,
+                           box_tests=s.box_tests, discards={BOUND_NAMES[k]: s.discards[k] for k in range(6)},
+                           retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
+                           pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA))
+
+
+def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:
+    """h(A, B) bracket: dict(lower, upper, status, stats).  Raises on INVALID/CUDA errors;
+    CAPACITY/TIMEOUT/NUMERIC come back in ``status``."""
+    m, keep, dev = _mesh(VA, FA)
+    r = HdResult()
+    rc = lib().hd_hausdorff(bvh.handle, C.byref(m), float(tol), C.byref(opt) if opt else None, _stream(dev, stream),
+                            C.byref(r))
+    if rc in (HD_ERR_INVALID, HD_ERR_CUDA):
+        raise HdError(rc, "hd_hausdorff")
+    return _result(r)
+
+
+def hd_hausdorff_batched(bvhs, As, tol: float, opt: HdOptions | None = None, stream=None) -> list[dict]:
+    """Independent pairs h(As[i], Bs[i]); As is a list of (V, F)."""
+    n = len(bvhs)
+    handles = (C.c_void_p * n)(*[b.handle.value for b in bvhs])
+    meshes = (HdMesh * n)()
+    keep, dev = [], False
+    for i, (V, F) in enumerate(As):
+        m, k, d = _mesh(V, F)
+        meshes[i] = m
+        keep.append(k)
+        dev = dev or d
+    outs = (HdResult * n)()
+    _check(lib().hd_hausdorff_batched(handles, meshes, n, float(tol), C.byref(opt) if opt else None,
+                                      _stream(dev, stream), outs), "hd_hausdorff_batched")
+    return [_result(outs[i]) for i in range(n)]
+
+
+def hd_nearest(bvh: Bvh, P, precision: int = HD_FP64, stream=None):
+    """Nearest triangle of B for each row of P (a CUDA tensor, float32 or float64).
+    Returns CUDA tensors (dist, idx, foot, dist_lo); in HD_MIXED dist is a certified upper
+    bound and dist_lo a certified lower bound of d(p, B)."""
+    import torch
+
+    assert P.is_cuda
+    P = P.contiguous()
+    if P.dtype not in (torch.float32, torch.float64):
+        P = P.double()
+    n = P.shape[0]
+    dev = P.device
+    dist = torch.empty(n, dtype=torch.float64, device=dev)
+    dlo = torch.empty(n, dtype=torch.float64, device=dev)
+    idx = torch.empty(n, dtype=torch.int32, device=dev)
+    foot = torch.empty((n, 3), dtype=torch.float64, device=dev)
+    _check(lib().hd_nearest(bvh.handle, P.data_ptr(), HD_F64 if P.dtype == torch.float64 else HD_F32, n, precision,
+                            _stream(True, stream), dist.data_ptr(), idx.data_ptr(), foot.data_ptr(), dlo.data_ptr()),
+           "hd_nearest")
+    return dist, idx, foot, dlo
+
+
+def hd_upper_bounds(bvh: Bvh, T, Td, TI, Tq, l: float, opt: HdOptions | None = None, stream=None):
+    """UpperBound(T, l) in FP64 for n triangles (CUDA tensors): returns (U, code)."""
+    import torch
+
+    T, Td, Tq = (x.to(torch.float64).contiguous() for x in (T, Td, Tq))
+    TI = TI.to(torch.int32).contiguous()
+    n = T.shape[0]
+    U = torch.empty(n, dtype=torch.float64, device=T.device)
+    code = torch.empty(n, dtype=torch.int32, device=T.device)
+    _check(lib().hd_upper_bounds(bvh.handle, T.data_ptr(), Td.data_ptr(), TI.data_ptr(), Tq.data_ptr(), n, float(l),
+                                 C.byref(opt) if opt else None, _stream(True, stream), U.data_ptr(),
+                                 code.data_ptr()), "hd_upper_bounds")
+    return U, code

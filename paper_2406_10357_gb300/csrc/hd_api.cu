@@ -1,0 +1,307 @@
+// The C ABI of include/hd.h: options, validation, dispatch to the FP64 or certified FP32
+// branch-and-bound, and the step-level entry points used for parity checks.
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "hd_bnb.cuh"
+#include "hd_fp64.cuh"
+
+namespace hd {
+
+static thread_local char g_err[512] = "";
+
+int set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_err, sizeof g_err, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+  return HD_ERR_CUDA;
+}
+
+int resolve_options(const hd_options* in, Opts* o) {
+  hd_options d;
+  hd_options_default(&d);
+  const hd_options& x = in ? *in : d;
+  o->tol_mode = x.tol_mode;
+  o->precision = x.precision;
+  o->max_face_factor = x.max_face_factor;
+  o->frontier_chunk = x.frontier_chunk;
+  o->leaf_size = x.leaf_size;
+  o->block_size = x.block_size;
+  o->n_bounds = x.n_bounds;
+  o->max_rounds = x.max_rounds;
+  o->max_frontier_bytes = x.max_frontier_bytes;
+  memcpy(o->order, x.bound_order, 4);
+  if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
+  if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
+  if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;
+  if (o->leaf_size < 1 || o->leaf_size > 16) return HD_ERR_INVALID;
+  if (o->block_size < 32 || o->block_size > 1024 || o->block_size % 32) return HD_ERR_INVALID;
+  if (o->n_bounds < 1 || o->n_bounds > 4) return HD_ERR_INVALID;
+  for (int k = 0; k < o->n_bounds; ++k)
+    if (o->order[k] < 1 || o->order[k] > 4) return HD_ERR_INVALID;
+  if (o->max_rounds < 1 || o->frontier_chunk < 0 || o->max_frontier_bytes < 0) return HD_ERR_INVALID;
+  return HD_OK;
+}
+
+static int check_mesh(const hd_mesh* m) {
+  if (!m || !m->V || !m->F || m->nV <= 0 || m->nF <= 0) return HD_ERR_INVALID;
+  if (m->vtype != HD_F32 && m->vtype != HD_F64) return HD_ERR_INVALID;
+  if (m->nV > INT32_MAX / 2 || m->nF > INT32_MAX / 4) return HD_ERR_INVALID;
+  return HD_OK;
+}
+
+// The default stream-ordered pool keeps freed blocks, so the per-call work buffers are not
+// returned to the driver between calls.
+static void keep_pool_memory() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  static bool done[64] = {};
+  if (dev < 64 && !done[dev]) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    done[dev] = true;
+  }
+}
+
+int prepare_A(const RunIO& io, uint8_t* ref, double* dA, int64_t* n_ref) {
+  cudaStream_t s = io.s;
+  unsigned long long* box = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&box, 64, s));
+  unsigned long long init[8] = {~0ull, ~0ull, ~0ull, 0, 0, 0, 0, 0};
+  HD_TRY(cudaMemcpyAsync(box, init, 64, cudaMemcpyHostToDevice, s));
+  HD_TRY(cudaMemsetAsync(ref, 0, io.nVA, s));
+  int* bad = (int*)(box + 6);
+  k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
+  if (io.vtype == HD_F64)
+    k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
+  else
+    k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
+  HD_TRY_LAUNCH();
+  unsigned long long h[8];
+  HD_TRY(cudaMemcpyAsync(h, box, 64, cudaMemcpyDeviceToHost, s));
+  HD_TRY(cudaFreeAsync(box, s));
+  HD_TRY(cudaStreamSynchronize(s));
+  if (h[6] & 0xffffffffull) return HD_ERR_INVALID;
+  double v[6];
+  for (int k = 0; k < 6; ++k) {
+    unsigned long long u = h[k];
+    u = (u >> 63) ? (u & ~(1ull << 63)) : ~u;
+    memcpy(&v[k], &u, 8);
+  }
+  double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
+  *dA = sqrt(dx * dx + dy * dy + dz * dz);
+  *n_ref = 0;
+  return HD_OK;
+}
+
+int run_fp64(const RunIO& io) { return run_bnb<PolicyD>(io); }
+int run_mixed(const RunIO& io);
+
+template <class P, typename T>
+__global__ void k_points_in(const T* P_, int64_t n, typename P::Vtx* v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename P::Vtx x;
+  memset(&x, 0, sizeof x);
+  x.x = (double)P_[3 * i];
+  x.y = (double)P_[3 * i + 1];
+  x.z = (double)P_[3 * i + 2];
+  x.tri = -2;
+  x.hint = -1;
+  v[i] = x;
+}
+
+template <class P>
+__global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tri_vid, double* dist, int32_t* idx,
+                             double* foot, double* dlo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename P::Vtx x = v[i];
+  dist[i] = P::out_dist(x);
+  idx[i] = x.tri >= 0 ? tri_vid[x.tri].w : -1;
+  D3 f = P::out_foot(x);
+  foot[3 * i] = f.x;
+  foot[3 * i + 1] = f.y;
+  foot[3 * i + 2] = f.z;
+  if (dlo) dlo[i] = P::out_dlo(x);
+}
+
+template <class P>
+int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
+                   int32_t* idx, double* foot, double* dlo) {
+  typename P::Vtx* tmp = nullptr;
+  RunState* st = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&tmp, sizeof(typename P::Vtx) * n, s));
+  HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
+  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
+  if (ptype == HD_F64)
+    k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, tmp);
+  else
+    k_points_in<P, float><<<blocks_for(n, 256), 256, 0, s>>>((const float*)Pts, n, tmp);
+  k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), tmp, n, st);
+  k_points_out<P><<<blocks_for(n, 256), 256, 0, s>>>(tmp, n, B->tri_vid, dist, idx, foot, dlo);
+  HD_TRY_LAUNCH();
+  HD_TRY(cudaFreeAsync(tmp, s));
+  HD_TRY(cudaFreeAsync(st, s));
+  return HD_OK;
+}
+int nearest_points_mixed(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
+                         int32_t* idx, double* foot, double* dlo);
+
+__global__ void k_upper_bounds(BvhDev B, const int* inv, const double* T, const double* Td, const int32_t* TI,
+                               const double* Tq, int64_t n, double l, RunParams rp, double* U, int32_t* code) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  VI t[3];
+  for (int k = 0; k < 3; ++k) {
+    const double* v = T + 9 * i + 3 * k;
+    const double* q = Tq + 9 * i + 3 * k;
+    int I = TI[3 * i + k];
+    if (I < 0 || I >= B.nF) {  // not a triangle of B: no bound
+      U[i] = NAN;
+      code[i] = -1;
+      return;
+    }
+    t[k] = {{v[0], v[1], v[2]}, Td[3 * i + k], inv[I], {q[0], q[1], q[2]}};
+  }
+  unsigned long long ev = 0;
+  int c;
+  U[i] = upper_bound_d(B, t, l, rp.order, rp.n_bounds, c, ev);
+  code[i] = c;
+}
+
+}  // namespace hd
+
+using namespace hd;
+
+extern "C" {
+
+void hd_options_default(hd_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof *o);
+  o->tol_mode = HD_TOL_ABS;
+  o->precision = HD_FP64;
+  o->max_face_factor = 1e7;
+  o->frontier_chunk = 0;
+  o->leaf_size = 4;
+  o->block_size = 128;
+  o->bound_order[0] = 1;
+  o->bound_order[1] = 2;
+  o->bound_order[2] = 3;
+  o->bound_order[3] = 4;
+  o->n_bounds = 4;
+  o->max_rounds = 1000000;
+  o->max_frontier_bytes = 0;
+}
+
+const char* hd_status_str(int s) {
+  switch (s) {
+    case HD_OK: return "HD_OK";
+    case HD_ERR_INVALID: return "HD_ERR_INVALID";
+    case HD_ERR_CAPACITY: return "HD_ERR_CAPACITY";
+    case HD_ERR_NUMERIC: return "HD_ERR_NUMERIC";
+    case HD_ERR_TIMEOUT: return "HD_ERR_TIMEOUT";
+    case HD_ERR_CUDA: return "HD_ERR_CUDA";
+    default: return "HD_UNKNOWN";
+  }
+}
+
+const char* hd_last_error(void) { return g_err; }
+
+int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** out) {
+  if (!out) return HD_ERR_INVALID;
+  *out = nullptr;
+  Opts o;
+  if (resolve_options(opt, &o) != HD_OK || check_mesh(B) != HD_OK) return HD_ERR_INVALID;
+  keep_pool_memory();
+  return build_bvh(B, o, (cudaStream_t)stream, out);
+}
+
+void hd_free_B(hd_bvh* b) {
+  if (!b) return;
+  cudaFree(b->nodes);
+  cudaFree(b->tri32);
+  cudaFree(b->tri64);
+  cudaFree(b->tri_vid);
+  cudaFree(b->inv);
+  delete b;
+}
+
+int64_t hd_bvh_num_faces(const hd_bvh* b) { return b ? b->nF : 0; }
+
+int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
+                 hd_result* out) {
+  if (!out) return HD_ERR_INVALID;
+  memset(out, 0, sizeof *out);
+  out->status = HD_ERR_INVALID;
+  Opts o;
+  if (!B || !(tol > 0.0) || resolve_options(opt, &o) != HD_OK || check_mesh(A) != HD_OK) return HD_ERR_INVALID;
+  int dev = -1;
+  HD_TRY(cudaGetDevice(&dev));
+  if (dev != B->device) return HD_ERR_INVALID;
+  keep_pool_memory();
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vbytes = (size_t)A->nV * 3 * (A->vtype == HD_F64 ? 8 : 4);
+  const void* VA = A->V;
+  const int32_t* FA = A->F;
+  void* Vtmp = nullptr;
+  int32_t* Ftmp = nullptr;
+  if (!A->on_device) {
+    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, s));
+    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)A->nF * 12, s));
+    HD_TRY(cudaMemcpyAsync(Vtmp, A->V, vbytes, cudaMemcpyHostToDevice, s));
+    HD_TRY(cudaMemcpyAsync(Ftmp, A->F, (size_t)A->nF * 12, cudaMemcpyHostToDevice, s));
+    VA = Vtmp;
+    FA = Ftmp;
+  }
+  RunIO io{B, VA, A->vtype, A->nV, FA, A->nF, tol, &o, s, out};
+  int rc = o.precision == HD_FP64 ? run_fp64(io) : run_mixed(io);
+  if (Vtmp) cudaFreeAsync(Vtmp, s);
+  if (Ftmp) cudaFreeAsync(Ftmp, s);
+  if (rc != HD_OK) {
+    out->status = rc;
+    return rc;
+  }
+  return HD_OK;
+}
+
+int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
+                         const hd_options* opt, void* stream, hd_result* outs) {
+  if (!Bs || !As || !outs || npairs < 0) return HD_ERR_INVALID;
+  for (int64_t i = 0; i < npairs; ++i) {
+    int rc = hd_hausdorff(Bs[i], &As[i], tol, opt, stream, &outs[i]);
+    if (rc == HD_ERR_INVALID || rc == HD_ERR_CUDA) return rc;
+  }
+  return HD_OK;
+}
+
+int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,
+               double* dist, int32_t* idx, double* foot, double* dist_lo) {
+  if (!B || (n > 0 && (!P || !dist || !idx || !foot)) || n < 0) return HD_ERR_INVALID;
+  if ((ptype != HD_F32 && ptype != HD_F64) || (precision != HD_FP64 && precision != HD_MIXED)) return HD_ERR_INVALID;
+  if (n == 0) return HD_OK;
+  keep_pool_memory();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == HD_FP64) return nearest_points<PolicyD>(B, P, ptype, n, s, dist, idx, foot, dist_lo);
+  return nearest_points_mixed(B, P, ptype, n, s, dist, idx, foot, dist_lo);
+}
+
+int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const int32_t* TI, const double* Tq,
+                    int64_t n, double l, const hd_options* opt, void* stream, double* U, int32_t* code) {
+  Opts o;
+  if (!B || n < 0 || resolve_options(opt, &o) != HD_OK) return HD_ERR_INVALID;
+  if (n == 0) return HD_OK;
+  if (!T || !Td || !TI || !Tq || !U || !code) return HD_ERR_INVALID;
+  RunParams rp;
+  rp.eps = 0.0;
+  memcpy(rp.order, o.order, 4);
+  rp.n_bounds = o.n_bounds;
+  cudaStream_t s = (cudaStream_t)stream;
+  k_upper_bounds<<<blocks_for(n, 128), 128, 0, s>>>(bvh_dev(B), B->inv, T, Td, TI, Tq, n, l, rp, U, code);
+  HD_TRY_LAUNCH();
+  return HD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,334 @@
+// FP64 policy: every distance and bound in IEEE double with round-to-nearest, the
+// arithmetic of the paper's implementation (Section 4).
+#pragma once
+
+#include "hd_internal.cuh"
+
+namespace hd {
+
+constexpr int kStack = 64;
+
+// Nearest triangle of B to p by ordered depth-first traversal of the BVH: both child
+// boxes come with one node fetch, leaf children are tested at once, the nearer internal
+// child is entered and the farther one pushed with its box distance, which is re-checked
+// when popped.  `Test` gets a triangle range and may shrink the pruning radius it holds.
+template <class Test>
+__device__ inline void traverse(const BvhDev& B, D3 p, Test& test, Counters& c) {
+  int stack_node[kStack];
+  double stack_d[kStack];
+  int sp = 0;
+  int node = 0;
+  for (;;) {
+    const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
+    float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+    int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
+    double d0 = box_dist2(p, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
+    double d1 = box_dist2(p, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
+    c.boxes += 2;
+    if (ref.z > 0 && d0 < test.radius2()) test.range(ref.x, ref.z);
+    if (ref.w > 0 && d1 < test.radius2()) test.range(ref.y, ref.w);
+    double r2 = test.radius2();
+    bool g0 = ref.z == 0 && d0 < r2, g1 = ref.w == 0 && d1 < r2;
+    if (g0 && g1) {
+      int nn = ref.x, nf = ref.y;
+      double df = d1;
+      if (d1 < d0) {
+        nn = ref.y;
+        nf = ref.x;
+        df = d0;
+      }
+      if (sp < kStack) {
+        stack_node[sp] = nf;
+        stack_d[sp] = df;
+        ++sp;
+      } else {
+        c.err = 1;  // stack overflow: the far subtree is skipped and the error reported
+      }
+      node = nn;
+      continue;
+    }
+    if (g0) { node = ref.x; continue; }
+    if (g1) { node = ref.y; continue; }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (stack_d[sp] < test.radius2()) {
+        node = stack_node[sp];
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+}
+
+struct NearestD {
+  D3 p;
+  const double* tri64;
+  double best2 = INFINITY;
+  int best = -1;
+  D3 q = {0, 0, 0};
+  unsigned long long evals = 0;
+  __device__ double radius2() const { return best2; }
+  __device__ void test1(int j) {
+    D3 a, b, c;
+    load_tri64(tri64, j, a, b, c);
+    D3 x = closest_on_triangle(p, a, b, c);
+    D3 e = p - x;
+    double d2 = dot(e, e);
+    ++evals;
+    if (d2 < best2) {
+      best2 = d2;
+      best = j;
+      q = x;
+    }
+  }
+  __device__ void range(int first, int count) {
+    for (int j = first; j < first + count; ++j) test1(j);
+  }
+};
+
+__device__ inline double dist_to_tri64(const BvhDev& B, int j, D3 x) {
+  D3 a, b, c;
+  load_tri64(B.tri64, j, a, b, c);
+  return len(x - closest_on_triangle(x, a, b, c));
+}
+
+// ----------------------------------------------------------------------------- bounds (Section 3.2)
+
+struct VI {
+  D3 v;
+  double d;
+  int I;
+  D3 q;
+};
+
+// Eq. (uexact): the three vertices are nearest to one triangle S; h(T,S) = max_i |v_i - q_i|.
+__device__ inline double ub_exact(const VI t[3]) { return fmax(t[0].d, fmax(t[1].d, t[2].d)); }
+
+// Eq. (u1)
+__device__ inline double ub_u1(const VI t[3]) {
+  double u = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double e1 = len(t[i].v - t[(i + 1) % 3].v), e2 = len(t[i].v - t[(i + 2) % 3].v);
+    u = fmin(u, fmax(e1, e2) + t[i].d);
+  }
+  return u;
+}
+
+// Eq. (u2): g + max_i d_i with g = R if s - r > 2R, else half the longest edge.
+__device__ inline double ub_u2(const VI t[3]) {
+  double e1 = len(t[1].v - t[2].v), e2 = len(t[2].v - t[0].v), e3 = len(t[0].v - t[1].v);
+  double area = 0.5 * len(cross(t[1].v - t[0].v, t[2].v - t[0].v));
+  double g = 0.5 * fmax(e1, fmax(e2, e3));
+  if (area > 0.0) {
+    double R = e1 * e2 * e3 / (4.0 * area);
+    double s = 0.5 * (e1 + e2 + e3);
+    double r = area / s;
+    if (s - r > 2.0 * R) g = R;
+  }
+  return g + fmax(t[0].d, fmax(t[1].d, t[2].d));
+}
+
+// Shared edge of triangles f, g of B (equal vertex indices of their F_B rows): returns
+// true with the slots of the two shared vertices in f and the opposite slots in f and g.
+__device__ inline bool shared_edge(const BvhDev& B, int f, int g, int& fs0, int& fs1, int& fo, int& go) {
+  int4 a = __ldg(B.tri_vid + f), b = __ldg(B.tri_vid + g);
+  int av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
+  bool ash[3], bsh[3];
+  int nsh = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    ash[i] = (av[i] == bv[0] || av[i] == bv[1] || av[i] == bv[2]);
+    bsh[i] = (bv[i] == av[0] || bv[i] == av[1] || bv[i] == av[2]);
+  }
+  // distinct shared vertex indices of f
+  int sl[3], ns = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (!ash[i]) continue;
+    bool dup = false;
+    for (int k = 0; k < ns; ++k) dup |= av[sl[k]] == av[i];
+    if (!dup) sl[ns++] = i;
+  }
+  nsh = ns;
+  if (nsh != 2) return false;
+  fs0 = sl[0];
+  fs1 = sl[1];
+  fo = go = -1;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (av[i] != av[fs0] && av[i] != av[fs1]) fo = i;
+    if (bv[i] != av[fs0] && bv[i] != av[fs1]) go = i;
+  }
+  return fo >= 0 && go >= 0;
+}
+
+__device__ inline D3 tri_vertex(const BvhDev& B, int j, int slot) {
+  const double* t = B.tri64 + 9 * (size_t)j + 3 * slot;
+  return {t[0], t[1], t[2]};
+}
+
+// Kang et al. 2018 bound, Eqs. (Kang2018_case1) and (Kang2018_case2).
+__device__ inline double ub_u3(const BvhDev& B, const VI t[3], unsigned long long& evals) {
+  int lone = -1;
+  if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
+    if (t[1].I == t[2].I) lone = 0;
+    else if (t[0].I == t[2].I) lone = 1;
+    else if (t[0].I == t[1].I) lone = 2;
+  }
+  int fs0, fs1, fo, go;
+  if (lone >= 0 && shared_edge(B, t[lone].I, t[(lone + 1) % 3].I, fs0, fs1, fo, go)) {
+    const VI& v1 = t[lone];
+    const VI& v2 = t[(lone + 1) % 3];
+    const VI& v3 = t[(lone + 2) % 3];
+    int S1 = v1.I, S2 = v2.I;
+    D3 p0 = tri_vertex(B, S1, fs0), e = tri_vertex(B, S1, fs1) - p0;
+    D3 b1 = 0.5 * (v1.v + v2.v), b2 = 0.5 * (v1.v + v3.v);
+    double el = len(e);
+    if (el > 0.0) {
+      D3 eh = (1.0 / el) * e;
+      D3 a1 = tri_vertex(B, S1, fo) - p0, a2 = tri_vertex(B, S2, go) - p0;
+      D3 w1 = a1 - dot(a1, eh) * eh, w2 = a2 - dot(a2, eh) * eh;
+      double n1 = len(w1), n2 = len(w2);
+      if (n1 > 0.0 && n2 > 0.0) {
+        D3 nb = (1.0 / n1) * w1 - (1.0 / n2) * w2;
+        double s1 = dot(nb, v1.v - p0), s2 = dot(nb, v2.v - p0), s3 = dot(nb, v3.v - p0);
+        if (s1 >= 0.0 && s2 <= 0.0 && s3 <= 0.0 && s1 - s2 > 0.0 && s1 - s3 > 0.0) {
+          b1 = v1.v + (s1 / (s1 - s2)) * (v2.v - v1.v);
+          b2 = v1.v + (s1 / (s1 - s3)) * (v3.v - v1.v);
+        }
+      }
+    }
+    evals += 7;
+    double hR = fmax(dist_to_tri64(B, S1, v1.v), fmax(dist_to_tri64(B, S1, b1), dist_to_tri64(B, S1, b2)));
+    double hQ = fmax(fmax(dist_to_tri64(B, S2, v3.v), dist_to_tri64(B, S2, b2)),
+                     fmax(dist_to_tri64(B, S2, b1), dist_to_tri64(B, S2, v2.v)));
+    return fmax(hR, hQ);
+  }
+  D3 m[3], bc = (1.0 / 3.0) * (t[0].v + t[1].v + t[2].v);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) m[i] = 0.5 * (t[i].v + t[(i + 1) % 3].v);
+  double ut = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int S = t[i].I;
+    double h = fmax(fmax(dist_to_tri64(B, S, t[i].v), dist_to_tri64(B, S, m[i])),
+                    fmax(dist_to_tri64(B, S, bc), dist_to_tri64(B, S, m[(i + 2) % 3])));
+    ut = fmax(ut, h);
+  }
+  double best = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    double h = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) h = fmax(h, dist_to_tri64(B, t[i].I, t[j].v));
+    best = fmin(best, h);
+  }
+  evals += 21;
+  return fmin(ut, best);
+}
+
+// max over T of d(., {a, b}), attained at a vertex of T or where an edge of T crosses the
+// bisector plane of a and b (Section 3.2.4).
+__device__ inline double h_two_points(const VI t[3], D3 a, D3 b) {
+  double h = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) h = fmax(h, fmin(len(t[i].v - a), len(t[i].v - b)));
+  D3 n = b - a;
+  if (dot(n, n) == 0.0) return h;
+  D3 mid = 0.5 * (a + b);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    D3 x0 = t[i].v, x1 = t[(i + 1) % 3].v;
+    double c0 = dot(n, x0 - mid), c1 = dot(n, x1 - mid);
+    if (((c0 <= 0.0 && c1 >= 0.0) || (c0 >= 0.0 && c1 <= 0.0)) && c0 != c1) {
+      D3 x = x0 + (c0 / (c0 - c1)) * (x1 - x0);
+      h = fmax(h, fmin(len(x - a), len(x - b)));
+    }
+  }
+  return h;
+}
+
+// Eq. (bound_u4)
+__device__ inline double ub_u4(const VI t[3]) {
+  double l0 = len(t[0].v - t[1].v), l1 = len(t[1].v - t[2].v), l2 = len(t[2].v - t[0].v);
+  int k = 0;
+  double m = l0;
+  if (l1 < m) { k = 1; m = l1; }
+  if (l2 < m) k = 2;
+  D3 q2 = t[k].q, q3 = t[(k + 1) % 3].q, q1 = t[(k + 2) % 3].q;
+  return fmin(h_two_points(t, q1, q2), h_two_points(t, q1, q3));
+}
+
+// UpperBound(T, l) of Section 4.
+__device__ inline double upper_bound_d(const BvhDev& B, const VI t[3], double l, const uint8_t* order, int nb,
+                                       int& code, unsigned long long& evals) {
+  if (t[0].I == t[1].I && t[1].I == t[2].I) {
+    code = 0;
+    return ub_exact(t);
+  }
+  double U = INFINITY;
+  for (int k = 0; k < nb; ++k) {
+    double u;
+    switch (order[k]) {
+      case 1: u = ub_u1(t); break;
+      case 2: u = ub_u2(t); break;
+      case 3: u = ub_u3(B, t, evals); break;
+      default: u = ub_u4(t); break;
+    }
+    if (u < l) {
+      code = order[k];
+      return u;
+    }
+    U = fmin(U, u);
+  }
+  code = 5;
+  return U;
+}
+
+// ----------------------------------------------------------------------------- the policy
+
+struct PolicyD {
+  using Vtx = VtxD;
+  using Item = ItemD;
+  using UT = double;
+  static constexpr bool kFp64 = true;
+
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c) {
+    NearestD t;
+    t.p = {v.x, v.y, v.z};
+    t.tri64 = B.tri64;
+    if (v.hint >= 0) t.test1(v.hint);
+    traverse(B, t.p, t, c);
+    c.evals += t.evals;
+    v.tri = t.best;
+    v.d = sqrt(t.best2);
+    v.qx = t.q.x;
+    v.qy = t.q.y;
+    v.qz = t.q.z;
+  }
+  __device__ static double lower(const Vtx& v) { return v.d; }
+  __device__ static double out_dist(const Vtx& v) { return v.d; }
+  __device__ static double out_dlo(const Vtx& v) { return v.d; }
+  __device__ static D3 out_foot(const Vtx& v) { return {v.qx, v.qy, v.qz}; }
+  __device__ static void midpoint(const Vtx& a, const Vtx& b, Vtx& m) {
+    m.x = 0.5 * (a.x + b.x);
+    m.y = 0.5 * (a.y + b.y);
+    m.z = 0.5 * (a.z + b.z);
+    m.d = 0.0;
+    m.qx = m.qy = m.qz = 0.0;
+    m.tri = -2;
+    m.hint = a.tri;
+  }
+  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l,
+                                   const uint8_t* order, int nb, int& code, unsigned long long& evals) {
+    VI t[3] = {{{a.x, a.y, a.z}, a.d, a.tri, {a.qx, a.qy, a.qz}},
+               {{b.x, b.y, b.z}, b.d, b.tri, {b.qx, b.qy, b.qz}},
+               {{c.x, c.y, c.z}, c.d, c.tri, {c.qx, c.qy, c.qz}}};
+    return upper_bound_d(B, t, l, order, nb, code, evals);
+  }
+};
+
+}  // namespace hd

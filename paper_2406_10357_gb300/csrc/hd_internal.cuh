@@ -1,0 +1,232 @@
+// Internal types and device helpers shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hd.h"
+
+namespace hd {
+
+// ----------------------------------------------------------------------------- errors
+
+int set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+#define HD_TRY(call)                                                                  \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) return ::hd::set_cuda_error(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HD_TRY_LAUNCH() HD_TRY(cudaGetLastError())
+
+// ----------------------------------------------------------------------------- BVH layout
+
+// One traversal node, 64 bytes: the boxes of both children (so one node fetch gives both
+// child boxes), and for each child either an internal node index (count == 0), a leaf
+// range [ref, ref + count) of sorted triangles (count > 0), or nothing (count < 0).
+struct __align__(16) BvhNode {
+  float4 f0;  // c0.lo.x c0.lo.y c0.lo.z c0.hi.x
+  float4 f1;  // c0.hi.y c0.hi.z c1.lo.x c1.lo.y
+  float4 f2;  // c1.lo.z c1.hi.x c1.hi.y c1.hi.z
+  int4 ref;   // c0.ref c1.ref c0.count c1.count
+};
+static_assert(sizeof(BvhNode) == 64, "node is 64 B");
+
+}  // namespace hd
+
+// The handle behind hd_bvh*.  Triangles are stored in BVH (Morton) order.
+struct hd_bvh {
+  int device;
+  int64_t nF;
+  int leaf_size;
+  int input_f64;
+  int64_t n_nodes;
+  hd::BvhNode* nodes;  // n_nodes
+  float4* tri32;       // 3 per triangle: a.xyz|orig-index-bits, b.xyz|0, c.xyz|0 (RN of input)
+  double* tri64;       // 9 per triangle: a, b, c (exact input values)
+  int4* tri_vid;       // per triangle: the F_B row (vertex indices) and the original face index
+  int* inv;            // original face index -> sorted position
+  float eta;           // max distance between a float vertex of tri32 and its input value (0 for f32 input)
+};
+
+namespace hd {
+
+// ----------------------------------------------------------------------------- pool and frontier
+
+// A vertex of A or of a sub-triangle of A, with its nearest-triangle data (D, I, C of
+// Section 4).  Positions are double: midpoints of float or double inputs stay exact for
+// about 29 levels of subdivision.
+struct __align__(16) VtxD {  // HD_FP64
+  double x, y, z;
+  double d;           // |p - q|
+  double qx, qy, qz;  // closest point q on B
+  int tri;            // nearest triangle (sorted index); -1 = not referenced
+  int hint;           // triangle tried first by the query (warm start), -1 = none
+};
+static_assert(sizeof(VtxD) == 64, "VtxD is 64 B");
+
+struct __align__(16) VtxM {  // HD_MIXED
+  double x, y, z;
+  float qx, qy, qz;  // closest point q relative to the float position p32 = (float)p
+  float qerr;        // a point of triangle `tri` lies within qerr of p32 + (qx,qy,qz)
+  float dhi;         // >= d(p, S_tri) for the exact p (certified)
+  float dlo;         // <= d(p, B) for the exact p (certified)
+  int tri;
+  int hint;
+  float pad0, pad1;
+};
+static_assert(sizeof(VtxM) == 64, "VtxM is 64 B");
+
+struct ItemD {
+  int v[3];
+  int pad;
+  double U;
+};
+struct ItemM {
+  int v[3];
+  float U;
+};
+
+// Device-side state of one hd_hausdorff run.  All counters are updated with atomics.
+struct RunState {
+  unsigned long long l_bits;     // lower bound l (double bits; non-negative so ordered as uint64)
+  unsigned long long uret_bits;  // max U of retired sub-triangles (double bits)
+  unsigned long long umax_bits;  // max U over the next frontier (double bits)
+  int n_front;                   // items in the current frontier
+  int n_next;                    // items appended to the next frontier
+  int n_split;                   // items split this round
+  int n_pool;                    // vertices in the pool
+  int overflow;                  // next frontier or split list ran out of room
+  int err;                       // traversal stack overflow and similar
+  unsigned long long evals, box_tests, queries, retired, escalations;
+  unsigned long long discards[6];
+};
+
+// Device view of hd_bvh, passed to kernels by value.
+struct BvhDev {
+  const BvhNode* nodes;
+  const float4* tri32;
+  const double* tri64;
+  const int4* tri_vid;
+  int64_t nF;
+  float eta;
+};
+
+// Per-thread statistics, flushed with one atomic per warp.
+struct Counters {
+  unsigned long long evals = 0, boxes = 0, escalations = 0;
+  int err = 0;
+};
+
+// ----------------------------------------------------------------------------- small math
+
+struct D3 {
+  double x, y, z;
+};
+__host__ __device__ inline D3 d3(double x, double y, double z) { return {x, y, z}; }
+__host__ __device__ inline D3 operator+(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__host__ __device__ inline D3 operator-(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__host__ __device__ inline D3 operator*(double s, D3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__host__ __device__ inline double dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__host__ __device__ inline D3 cross(D3 a, D3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__host__ __device__ inline double len(D3 a) { return sqrt(dot(a, a)); }
+
+__device__ inline unsigned float_to_ordered(float f) {
+  unsigned u = __float_as_uint(f);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ inline float ordered_to_float(unsigned u) {
+  return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__device__ inline void atomic_max_nonneg(unsigned long long* addr, double v) {
+  atomicMax(addr, (unsigned long long)__double_as_longlong(v));
+}
+
+// Closest point of triangle (a, b, c) to p by Voronoi-region classification on the
+// barycentric dot products (Ericson, Real-Time Collision Detection, 2005, Sect. 5.1.5).
+// Divisions are guarded: a triangle whose face region has a non-positive denominator
+// (zero area) is handled as its three edges.
+__device__ inline D3 closest_on_segment(D3 p, D3 a, D3 b) {
+  D3 e = b - a;
+  double ee = dot(e, e);
+  double t = ee > 0.0 ? fmin(1.0, fmax(0.0, dot(p - a, e) / ee)) : 0.0;
+  return a + t * e;
+}
+
+__device__ inline D3 closest_on_triangle(D3 p, D3 a, D3 b, D3 c) {
+  D3 ab = b - a, ac = c - a, ap = p - a;
+  double d1 = dot(ab, ap), d2 = dot(ac, ap);
+  if (d1 <= 0.0 && d2 <= 0.0) return a;
+  D3 bp = p - b;
+  double d3v = dot(ab, bp), d4 = dot(ac, bp);
+  if (d3v >= 0.0 && d4 <= d3v) return b;
+  double vc = d1 * d4 - d3v * d2;
+  if (vc <= 0.0 && d1 >= 0.0 && d3v <= 0.0) {
+    double den = d1 - d3v;
+    return a + (den > 0.0 ? d1 / den : 0.0) * ab;
+  }
+  D3 cp = p - c;
+  double d5 = dot(ab, cp), d6 = dot(ac, cp);
+  if (d6 >= 0.0 && d5 <= d6) return c;
+  double vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.0 && d2 >= 0.0 && d6 <= 0.0) {
+    double den = d2 - d6;
+    return a + (den > 0.0 ? d2 / den : 0.0) * ac;
+  }
+  double va = d3v * d6 - d5 * d4;
+  if (va <= 0.0 && (d4 - d3v) >= 0.0 && (d5 - d6) >= 0.0) {
+    double den = (d4 - d3v) + (d5 - d6);
+    return b + (den > 0.0 ? (d4 - d3v) / den : 0.0) * (c - b);
+  }
+  double den = va + vb + vc;
+  if (!(den > 0.0)) {  // zero-area triangle: nearest of the three edges
+    D3 q0 = closest_on_segment(p, a, b), q1 = closest_on_segment(p, b, c), q2 = closest_on_segment(p, c, a);
+    double e0 = dot(p - q0, p - q0), e1 = dot(p - q1, p - q1), e2 = dot(p - q2, p - q2);
+    D3 q = q0;
+    if (e1 < e0) { q = q1; e0 = e1; }
+    if (e2 < e0) q = q2;
+    return q;
+  }
+  double v = vb / den, w = vc / den;
+  return a + v * ab + w * ac;
+}
+
+__device__ inline void load_tri64(const double* tri64, int i, D3& a, D3& b, D3& c) {
+  const double* t = tri64 + 9 * (size_t)i;
+  a = {t[0], t[1], t[2]};
+  b = {t[3], t[4], t[5]};
+  c = {t[6], t[7], t[8]};
+}
+
+// Squared distance from p to an axis-aligned box (0 inside).
+__device__ inline double box_dist2(D3 p, float lx, float ly, float lz, float hx, float hy, float hz) {
+  double dx = fmax(fmax((double)lx - p.x, p.x - (double)hx), 0.0);
+  double dy = fmax(fmax((double)ly - p.y, p.y - (double)hy), 0.0);
+  double dz = fmax(fmax((double)lz - p.z, p.z - (double)hz), 0.0);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+// ----------------------------------------------------------------------------- launch helpers
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+// Options after defaults and validation.
+struct Opts {
+  int tol_mode, precision, leaf_size, block_size, n_bounds;
+  double max_face_factor;
+  int64_t frontier_chunk, max_rounds, max_frontier_bytes;
+  uint8_t order[4];
+};
+int resolve_options(const hd_options* in, Opts* out);
+
+// Build-time helpers implemented in hd_lbvh.cu.
+int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out);
+
+}  // namespace hd

@@ -1,0 +1,472 @@
+// K1 -- GPU build of the bounding-volume hierarchy over B.
+//
+// The paper builds libigl's AABB tree over B once and uses it for all distance queries
+// (Section 4).  Here the hierarchy is a linear BVH built on the GPU:
+//   1. triangle centroids and their bounding box;
+//   2. 48-bit Morton codes (16 bits per axis) of the centroids;
+//   3. a stable LSD radix sort of (code, triangle) pairs, 8-bit digits;
+//   4. the binary radix tree of Karras (HPG 2012) over the sorted codes, ties broken by
+//      position;
+//   5. bottom-up boxes (float, rounded outward so they contain the exact triangles);
+//   6. traversal nodes: 64 B each, holding both child boxes; subtrees of at most
+//      leaf_size triangles become leaf ranges.
+#include <cstdio>
+#include <vector>
+
+#include "hd_internal.cuh"
+
+namespace hd {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------- 1-2: centroids, Morton codes
+
+template <typename T>
+__device__ inline D3 load_vertex(const T* V, int64_t i) {
+  return {(double)V[3 * i], (double)V[3 * i + 1], (double)V[3 * i + 2]};
+}
+
+template <typename T>
+__global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, double* tri_unsorted,
+                       unsigned* cbox /*6 ordered floats: min xyz (as ~max), max xyz*/, int* bad) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (f < nF) {
+    int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV) {
+      atomicExch(bad, 1);
+    } else {
+      D3 a = load_vertex(V, i0), b = load_vertex(V, i1), c = load_vertex(V, i2);
+      double* t = tri_unsorted + 9 * f;
+      t[0] = a.x; t[1] = a.y; t[2] = a.z;
+      t[3] = b.x; t[4] = b.y; t[5] = b.z;
+      t[6] = c.x; t[7] = c.y; t[8] = c.z;
+      bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
+                 isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
+      if (!fin) {
+        atomicExch(bad, 1);
+      } else {
+        D3 m = (1.0 / 3.0) * (a + b + c);
+        lo[0] = hi[0] = (float)m.x;
+        lo[1] = hi[1] = (float)m.y;
+        lo[2] = hi[2] = (float)m.z;
+      }
+    }
+  }
+  // block reduction of the centroid box, then one atomic per block and axis
+  for (int k = 0; k < 3; ++k) {
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+    }
+  }
+  if ((threadIdx.x & 31) == 0 && isfinite(lo[0])) {
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&cbox[k], float_to_ordered(lo[k]));
+      atomicMax(&cbox[3 + k], float_to_ordered(hi[k]));
+    }
+  }
+}
+
+__device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit of 48
+  uint64_t x = v & 0xffffu;
+  x = (x | (x << 16)) & 0x0000ff0000ffull;
+  x = (x | (x << 8)) & 0x00f00f00f00full;
+  x = (x | (x << 4)) & 0x0c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x249249249249ull;
+  return x;
+}
+
+__global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned* cbox, uint64_t* keys,
+                         uint32_t* vals) {
+  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (f >= nF) return;
+  const double* t = tri_unsorted + 9 * f;
+  uint32_t q[3];
+  for (int k = 0; k < 3; ++k) {
+    float lo = ordered_to_float(cbox[k]), hi = ordered_to_float(cbox[3 + k]);
+    double c = (t[k] + t[3 + k] + t[6 + k]) / 3.0;
+    double ext = (double)hi - (double)lo;
+    double u = ext > 0.0 ? (c - lo) / ext : 0.5;
+    u = fmin(fmax(u, 0.0), 1.0);
+    q[k] = (uint32_t)fmin(u * 65536.0, 65535.0);
+  }
+  keys[f] = (spread16(q[0]) << 2) | (spread16(q[1]) << 1) | spread16(q[2]);
+  vals[f] = (uint32_t)f;
+}
+
+// ---------------------------------------------------------------- 3: stable LSD radix sort
+
+constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32, RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // 4096 keys per block; warp w owns 512 consecutive keys
+
+__global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks) {
+  __shared__ unsigned cnt[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_TILE;
+  for (int k = threadIdx.x; k < RS_TILE; k += blockDim.x) {
+    int64_t i = base + k;
+    if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+}
+
+// exclusive scan of `n` counters in place, one block of 1024 threads
+__global__ void k_rs_scan(unsigned* a, int64_t n) {
+  __shared__ unsigned part[1024];
+  int64_t per = (n + 1023) / 1024;
+  int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
+  unsigned s = 0;
+  for (int64_t i = b; i < e; ++i) s += a[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan of the 1024 partial sums
+    unsigned v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int64_t i = b; i < e; ++i) {
+    unsigned v = a[i];
+    a[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
+                             int shift, const unsigned* hist, int nblocks) {
+  __shared__ unsigned wcnt[RS_WARPS][256];
+  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
+  __syncwarp();
+  const unsigned lt = (1u << lane) - 1u;
+  int64_t base = (int64_t)blockIdx.x * RS_TILE + w * (RS_TILE / RS_WARPS);
+  unsigned rank[RS_ROUNDS];
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    bool valid = i < n;
+    unsigned dig = valid ? (unsigned)((kin[i] >> shift) & 0xff) : 256u + lane;  // invalid lanes match only themselves
+    unsigned peers = __match_any_sync(0xffffffffu, dig);
+    unsigned before = __popc(peers & lt);
+    unsigned c = valid ? wcnt[w][dig] : 0;
+    __syncwarp();
+    if (valid && before == 0) wcnt[w][dig] = c + __popc(peers);
+    __syncwarp();
+    rank[r] = c + before;
+  }
+  __syncthreads();
+  // warp offsets within the block, per digit (exclusive over warps)
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    unsigned run = 0;
+    for (int k = 0; k < RS_WARPS; ++k) {
+      unsigned v = wcnt[k][d];
+      wcnt[k][d] = run;
+      run += v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + r * 32 + lane;
+    if (i < n) {
+      uint64_t key = kin[i];
+      unsigned dig = (unsigned)((key >> shift) & 0xff);
+      unsigned pos = hist[(int64_t)dig * nblocks + blockIdx.x] + wcnt[w][dig] + rank[r];
+      kout[pos] = key;
+      vout[pos] = vin[i];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 4: sorted triangles, leaf boxes
+
+__device__ inline float rd(double x) { return __double2float_rd(x); }
+__device__ inline float ru(double x) { return __double2float_ru(x); }
+
+__global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uint32_t* order, int64_t nF,
+                         double* tri64, float4* tri32, int4* tri_vid, int* inv, float4* leafbox /*2 per leaf*/,
+                         unsigned* eta_bits) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nF) return;
+  uint32_t f = order[i];
+  const double* s = tri_unsorted + 9 * (size_t)f;
+  double* t = tri64 + 9 * i;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  float eta = 0.0f;
+  float4 out[3];
+  for (int v = 0; v < 3; ++v) {
+    float c[3];
+    for (int k = 0; k < 3; ++k) {
+      double x = s[3 * v + k];
+      t[3 * v + k] = x;
+      lo[k] = fminf(lo[k], rd(x));
+      hi[k] = fmaxf(hi[k], ru(x));
+      c[k] = (float)x;
+    }
+    // distance between the float vertex and the input vertex, rounded up
+    double ex = s[3 * v] - c[0], ey = s[3 * v + 1] - c[1], ez = s[3 * v + 2] - c[2];
+    eta = fmaxf(eta, __double2float_ru(sqrt(ex * ex + ey * ey + ez * ez) * (1.0 + 1e-12)));
+    out[v] = make_float4(c[0], c[1], c[2], 0.0f);
+  }
+  out[0].w = __int_as_float((int)f);
+  tri32[3 * i] = out[0];
+  tri32[3 * i + 1] = out[1];
+  tri32[3 * i + 2] = out[2];
+  tri_vid[i] = make_int4(F[3 * f], F[3 * f + 1], F[3 * f + 2], (int)f);
+  inv[f] = (int)i;
+  leafbox[2 * i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+  leafbox[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+  if (eta > 0.0f) atomicMax(eta_bits, __float_as_uint(eta));
+}
+
+// ---------------------------------------------------------------- 5: Karras binary radix tree
+
+__device__ inline int delta(const uint64_t* k, int64_t n, int64_t i, int64_t j) {
+  if (j < 0 || j >= n) return -1;
+  uint64_t a = k[i], b = k[j];
+  if (a == b) return 64 + __clz((int)(uint32_t)(i ^ j));
+  return __clzll((long long)(a ^ b));
+}
+
+// Internal node i covers the sorted range [first, last]; its children are encoded as
+// c >= 0 internal, c < 0 leaf ~c.  Parents of internal nodes and leaves are recorded for
+// the bottom-up pass (-1 for the root).
+__global__ void k_karras(const uint64_t* keys, int64_t n, int* left, int* right, int* first, int* last,
+                         int* parent_int, int* parent_leaf) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  int d = delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1) >= 0 ? 1 : -1;
+  int dmin = delta(keys, n, i, i - d);
+  int64_t lmax = 2;
+  while (delta(keys, n, i, i + lmax * d) > dmin) lmax <<= 1;
+  int64_t l = 0;
+  for (int64_t t = lmax >> 1; t >= 1; t >>= 1)
+    if (delta(keys, n, i, i + (l + t) * d) > dmin) l += t;
+  int64_t j = i + l * d;
+  int dnode = delta(keys, n, i, j);
+  int64_t s = 0, t = l;
+  do {
+    t = (t + 1) >> 1;
+    if (delta(keys, n, i, i + (s + t) * d) > dnode) s += t;
+  } while (t > 1);
+  int64_t g = i + s * d + (d < 0 ? -1 : 0);
+  int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+  int cl = (lo == g) ? ~(int)g : (int)g;
+  int cr = (hi == g + 1) ? ~(int)(g + 1) : (int)(g + 1);
+  left[i] = cl;
+  right[i] = cr;
+  first[i] = (int)lo;
+  last[i] = (int)hi;
+  if (cl >= 0) parent_int[cl] = (int)i; else parent_leaf[~cl] = (int)i;
+  if (cr >= 0) parent_int[cr] = (int)i; else parent_leaf[~cr] = (int)i;
+  if (i == 0) parent_int[0] = -1;
+}
+
+__device__ inline void load_box(const float4* b, float lo[3], float hi[3]) {
+  float4 a = __ldcg(b), c = __ldcg(b + 1);
+  lo[0] = a.x; lo[1] = a.y; lo[2] = a.z;
+  hi[0] = c.x; hi[1] = c.y; hi[2] = c.z;
+}
+
+// Bottom-up boxes: the second child to arrive at a node computes its box.
+__global__ void k_refit(int64_t n, const int* left, const int* right, const int* parent_int,
+                        const int* parent_leaf, const float4* leafbox, float4* ibox, int* flags) {
+  int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (leaf >= n) return;
+  int node = parent_leaf[leaf];
+  while (node >= 0) {
+    __threadfence();
+    if (atomicAdd(&flags[node], 1) == 0) return;
+    __threadfence();
+    float lo[3], hi[3], lo2[3], hi2[3];
+    int cl = left[node], cr = right[node];
+    load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo, hi);
+    load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo2, hi2);
+    __stcg(ibox + 2 * node, make_float4(fminf(lo[0], lo2[0]), fminf(lo[1], lo2[1]), fminf(lo[2], lo2[2]), 0.f));
+    __stcg(ibox + 2 * node + 1,
+           make_float4(fmaxf(hi[0], hi2[0]), fmaxf(hi[1], hi2[1]), fmaxf(hi[2], hi2[2]), 0.f));
+    node = parent_int[node];
+  }
+}
+
+// ---------------------------------------------------------------- 6: traversal nodes
+
+__device__ inline void child_ref(int c, const int* first, const int* last, const float4* leafbox,
+                                 const float4* ibox, int L, int& ref, int& cnt, float lo[3], float hi[3]) {
+  if (c < 0) {
+    ref = ~c;
+    cnt = 1;
+    load_box(leafbox + 2 * (int64_t)(~c), lo, hi);
+    return;
+  }
+  int sz = last[c] - first[c] + 1;
+  load_box(ibox + 2 * (int64_t)c, lo, hi);
+  if (sz <= L) {
+    ref = first[c];
+    cnt = sz;
+  } else {
+    ref = c;
+    cnt = 0;
+  }
+}
+
+__global__ void k_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
+                       const float4* leafbox, const float4* ibox, BvhNode* nodes) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  if (last[i] - first[i] + 1 <= L) return;  // inside a leaf range: never visited
+  int r0, c0, r1, c1;
+  float lo0[3], hi0[3], lo1[3], hi1[3];
+  child_ref(left[i], first, last, leafbox, ibox, L, r0, c0, lo0, hi0);
+  child_ref(right[i], first, last, leafbox, ibox, L, r1, c1, lo1, hi1);
+  BvhNode nd;
+  nd.f0 = make_float4(lo0[0], lo0[1], lo0[2], hi0[0]);
+  nd.f1 = make_float4(hi0[1], hi0[2], lo1[0], lo1[1]);
+  nd.f2 = make_float4(lo1[2], hi1[0], hi1[1], hi1[2]);
+  nd.ref = make_int4(r0, r1, c0, c1);
+  nodes[i] = nd;
+}
+
+// Root for n <= leaf_size: one node whose first child is the whole range.
+__global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t i = 0; i < n; ++i) {
+    float a[3], b[3];
+    load_box(leafbox + 2 * i, a, b);
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], a[k]);
+      hi[k] = fmaxf(hi[k], b[k]);
+    }
+  }
+  BvhNode nd;
+  nd.f0 = make_float4(lo[0], lo[1], lo[2], hi[0]);
+  nd.f1 = make_float4(hi[1], hi[2], INFINITY, INFINITY);
+  nd.f2 = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
+  nd.ref = make_int4(0, 0, (int)n, -1);
+  nodes[0] = nd;
+}
+
+template <typename T>
+int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, unsigned* cbox, int* bad,
+                cudaStream_t s) {
+  k_prep<T><<<blocks_for(B->nF, kThreads), kThreads, 0, s>>>((const T*)V, B->nV, F, B->nF, tri_unsorted, cbox, bad);
+  HD_TRY_LAUNCH();
+  return HD_OK;
+}
+
+}  // namespace
+
+int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
+  const int64_t n = B->nF;
+  const size_t vbytes = (size_t)B->nV * 3 * (B->vtype == HD_F64 ? 8 : 4);
+  int dev = 0;
+  HD_TRY(cudaGetDevice(&dev));
+
+  // inputs on the device
+  const void* V = B->V;
+  const int32_t* F = B->F;
+  void* Vtmp = nullptr;
+  int32_t* Ftmp = nullptr;
+  if (!B->on_device) {
+    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, s));
+    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)n * 12, s));
+    HD_TRY(cudaMemcpyAsync(Vtmp, B->V, vbytes, cudaMemcpyHostToDevice, s));
+    HD_TRY(cudaMemcpyAsync(Ftmp, B->F, (size_t)n * 12, cudaMemcpyHostToDevice, s));
+    V = Vtmp;
+    F = Ftmp;
+  }
+
+  hd_bvh* h = new hd_bvh();
+  h->device = dev;
+  h->nF = n;
+  h->leaf_size = o.leaf_size;
+  h->input_f64 = B->vtype == HD_F64;
+  h->n_nodes = n > 1 ? n - 1 : 1;
+  HD_TRY(cudaMalloc((void**)&h->nodes, sizeof(BvhNode) * h->n_nodes));
+  HD_TRY(cudaMalloc((void**)&h->tri32, sizeof(float4) * 3 * n));
+  HD_TRY(cudaMalloc((void**)&h->tri64, sizeof(double) * 9 * n));
+  HD_TRY(cudaMalloc((void**)&h->tri_vid, sizeof(int4) * n));
+  HD_TRY(cudaMalloc((void**)&h->inv, sizeof(int) * n));
+
+  // scratch: one block, carved up
+  const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  size_t off = 0;
+  auto carve = [&](size_t bytes) {
+    size_t at = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  size_t o_tri = carve(sizeof(double) * 9 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
+         o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
+         o_ibox = carve(32 * n), o_int = carve(4 * 7 * n + 64), o_misc = carve(64);
+  char* scratch = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&scratch, off, s));
+  double* tri_unsorted = (double*)(scratch + o_tri);
+  uint64_t* k0 = (uint64_t*)(scratch + o_k0);
+  uint64_t* k1 = (uint64_t*)(scratch + o_k1);
+  uint32_t* v0 = (uint32_t*)(scratch + o_v0);
+  uint32_t* v1 = (uint32_t*)(scratch + o_v1);
+  unsigned* hist = (unsigned*)(scratch + o_hist);
+  float4* leafbox = (float4*)(scratch + o_leafbox);
+  float4* ibox = (float4*)(scratch + o_ibox);
+  int* ints = (int*)(scratch + o_int);
+  int *left = ints, *right = ints + n, *first = ints + 2 * n, *last = ints + 3 * n, *pint = ints + 4 * n,
+      *pleaf = ints + 5 * n, *flags = ints + 6 * n;
+  unsigned* misc = (unsigned*)(scratch + o_misc);  // [0..5] centroid box, [6] bad, [7] eta bits
+
+  unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
+  HD_TRY(cudaMemcpyAsync(misc, init, sizeof init, cudaMemcpyHostToDevice, s));
+  int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s)
+                              : launch_prep<float>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s);
+  if (rc != HD_OK) return rc;
+  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, n, misc, k0, v0);
+  HD_TRY_LAUNCH();
+
+  for (int shift = 0; shift < 48; shift += 8) {
+    k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+    k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
+    k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    HD_TRY_LAUNCH();
+    std::swap(k0, k1);
+    std::swap(v0, v1);
+  }
+
+  k_gather<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, F, v0, n, h->tri64, h->tri32, h->tri_vid, h->inv,
+                                                        leafbox, misc + 7);
+  HD_TRY_LAUNCH();
+  if (n > o.leaf_size) {
+    HD_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * n, s));
+    k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last, pint, pleaf);
+    k_refit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, left, right, pint, pleaf, leafbox, ibox, flags);
+    k_emit<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, leafbox, ibox,
+                                                            h->nodes);
+  } else {
+    k_root_leaf<<<1, 1, 0, s>>>(n, leafbox, h->nodes);
+  }
+  HD_TRY_LAUNCH();
+
+  unsigned flags_host[2] = {0, 0};
+  HD_TRY(cudaMemcpyAsync(flags_host, misc + 6, 8, cudaMemcpyDeviceToHost, s));
+  HD_TRY(cudaFreeAsync(scratch, s));
+  if (Vtmp) HD_TRY(cudaFreeAsync(Vtmp, s));
+  if (Ftmp) HD_TRY(cudaFreeAsync(Ftmp, s));
+  HD_TRY(cudaStreamSynchronize(s));
+  uint32_t eta_bits = flags_host[1];
+  float eta;
+  memcpy(&eta, &eta_bits, 4);
+  h->eta = eta;
+  if (flags_host[0]) {
+    hd_free_B(h);
+    return HD_ERR_INVALID;
+  }
+  *out = h;
+  return HD_OK;
+}
+
+}  // namespace hd

@@ -1,0 +1,63 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/hd.h declares.  No GPU work is launched here."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def hd():
+    from paper_2406_10357_gb300 import build
+
+    build.build()
+    import paper_2406_10357_gb300 as hd
+
+    hd.lib()
+    return hd
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "hd.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hd_[A-Za-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(hd):
+    names = declared_symbols()
+    assert {"hd_build_B", "hd_hausdorff", "hd_hausdorff_batched", "hd_free_B", "hd_status_str"} <= set(names)
+    L = C.CDLL(hd.LIB_PATH)
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_struct_layouts_match_header(hd):
+    # sizes of the ABI structs as laid out by a C compiler for this header
+    assert C.sizeof(hd.HdMesh) == 40
+    assert C.sizeof(hd.HdOptions) == 56
+    assert C.sizeof(hd.HdStats) == 8 * 17
+    assert C.sizeof(hd.HdResult) == 24 + 8 * 17
+
+
+def test_options_default_and_status_strings(hd):
+    o = hd.hd_options_default()
+    assert o.tol_mode == hd.HD_TOL_ABS and o.precision == hd.HD_FP64
+    assert o.max_face_factor == 1e7 and list(o.bound_order) == [1, 2, 3, 4] and o.n_bounds == 4
+    assert o.leaf_size == 4 and o.block_size == 128
+    assert hd.hd_status_str(hd.HD_ERR_CAPACITY) == "HD_ERR_CAPACITY"
+    assert hd.hd_status_str(99) == "HD_UNKNOWN"
+
+
+def test_invalid_arguments_rejected_before_any_launch(hd):
+    L = hd.lib()
+    r = hd.HdResult()
+    assert L.hd_hausdorff(None, None, 1e-3, None, None, C.byref(r)) == hd.HD_ERR_INVALID
+    out = C.c_void_p(0)
+    assert L.hd_build_B(None, None, None, C.byref(out)) == hd.HD_ERR_INVALID
+    m = hd.HdMesh(0, 0, 0, 0, 0, 0)
+    assert L.hd_build_B(C.byref(m), None, None, C.byref(out)) == hd.HD_ERR_INVALID
+    bad = hd.hd_options_default(leaf_size=40)
+    assert L.hd_build_B(C.byref(m), C.byref(bad), None, C.byref(out)) == hd.HD_ERR_INVALID

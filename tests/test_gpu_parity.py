@@ -1,0 +1,238 @@
+"""CUDA path against the FP64 oracle, through the C ABI.
+
+Per-query parity (HD_FP64): the distance of each point to B matches the oracle's brute
+force to 1e-6 relative (the tolerance the workloads are specified with); nearest indices
+may differ only where two triangles tie, so the distance to the returned triangle is
+checked instead of the index.  Bracket parity: the GPU bracket [l, u] and the oracle's
+both contain h, so they must intersect, and both gaps are within eps.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+REL = 1e-6
+
+
+@pytest.fixture(scope="module")
+def hd():
+    from paper_2406_10357_gb300 import build
+
+    build.build()
+    import paper_2406_10357_gb300 as hd
+
+    return hd
+
+
+def _dA(V, F):
+    R = np.asarray(V, float)[np.unique(np.asarray(F).ravel())]
+    return float(np.linalg.norm(R.max(0) - R.min(0)))
+
+
+def _pts_parity(hd, orc, bvh, VB, FB, P, precision):
+    Pt = torch.from_numpy(np.ascontiguousarray(P, dtype=np.float64)).cuda()
+    d, idx, foot, dlo = hd.hd_nearest(bvh, Pt, precision)
+    torch.cuda.synchronize()
+    d, idx, foot, dlo = d.cpu().numpy(), idx.cpu().numpy(), foot.cpu().numpy(), dlo.cpu().numpy()
+    do, io, qo = orc.nearest(P, VB, FB)
+    scale = max(1e-12 * _dA(VB, FB), 1e-300)
+    err = np.abs(d - do) / np.maximum(do, scale)
+    assert np.all(idx >= 0) and np.all(idx < len(FB))
+    # the returned foot lies on the returned triangle: its oracle distance to that triangle is ~0
+    for i in np.random.default_rng(0).choice(len(P), size=min(50, len(P)), replace=False):
+        f = FB[idx[i]]
+        dd, _ = orc.point_triangle(foot[i], *np.asarray(VB, float)[f])
+        assert dd <= 1e-9 * max(1.0, d[i])
+        assert abs(np.linalg.norm(P[i] - foot[i]) - d[i]) <= 1e-9 * max(1.0, d[i])
+    return err, d, dlo, do
+
+
+@pytest.mark.parametrize("k,scale,npts", [(1, 1.0, 400), (2, 0.05, 2000), (3, 0.02, 2000), (5, 0.01, 2000)])
+def test_nearest_fp64_matches_bruteforce(hd, orc, k, scale, npts):
+    p = mg.workload(k, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    rng = np.random.default_rng(k)
+    V = np.asarray(p.VA, float)
+    P = np.concatenate([V[rng.choice(len(V), size=min(npts, len(V)), replace=False)],
+                        V.mean(0) + rng.normal(size=(200, 3)) * V.std(0) * 1.5])
+    err, *_ = _pts_parity(hd, orc, bvh, p.VB, p.FB, P, hd.HD_FP64)
+    assert err.max() <= REL, err.max()
+
+
+@pytest.mark.parametrize("leaf", [1, 4, 16])
+def test_nearest_every_leaf_size_and_tiny_B(hd, orc, leaf):
+    rng = np.random.default_rng(leaf)
+    for nB in (1, 2, 3, 5, 17, 100):
+        VB = rng.normal(size=(3 * nB, 3))
+        FB = np.arange(3 * nB, dtype=np.int32).reshape(nB, 3)
+        bvh = hd.hd_build_B(VB, FB, hd.hd_options_default(leaf_size=leaf))
+        P = rng.normal(size=(300, 3)) * 2
+        err, *_ = _pts_parity(hd, orc, bvh, VB, FB, P, hd.HD_FP64)
+        assert err.max() <= REL
+
+
+def test_nearest_full_size_workload2_sampled(hd, orc):
+    """The benchmark's workload at full size: 2000 sampled vertices of A against brute force."""
+    p = mg.workload(2)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    rng = np.random.default_rng(2)
+    P = np.asarray(p.VA, float)[rng.choice(len(p.VA), size=2000, replace=False)]
+    err, *_ = _pts_parity(hd, orc, bvh, p.VB, p.FB, P, hd.HD_FP64)
+    assert err.max() <= REL
+
+
+def test_upper_bounds_match_oracle(hd, orc):
+    """UpperBound(T, l) on the GPU against the oracle for identical vertex data."""
+    p = mg.workload(1)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    rng = np.random.default_rng(5)
+    V = np.asarray(p.VA, float)
+    n = 600
+    # sub-triangles of A's faces at random barycentric positions and sizes
+    f = rng.integers(0, len(p.FA), n)
+    W = rng.dirichlet([1, 1, 1], size=(n, 3))
+    s = rng.choice([1.0, 0.3, 0.05, 0.01], size=n)[:, None, None]
+    c = rng.dirichlet([1, 1, 1], size=n)[:, None, :]
+    W = c + s * (W - c)
+    T = np.einsum("nkj,njd->nkd", W, V[p.FA[f]])
+    d, I, q = orc.nearest(T.reshape(-1, 3), p.VB, p.FB)
+    d, I, q = d.reshape(n, 3), I.reshape(n, 3), q.reshape(n, 3, 3)
+    l0 = float(np.quantile(d, 0.8))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    U, code = hd.hd_upper_bounds(bvh, t(T.reshape(n, 9)), t(d), t(I.astype(np.int32)), t(q.reshape(n, 9)), l0)
+    U, code = U.cpu().numpy(), code.cpu().numpy()
+    names = {"exact": 0, "u1": 1, "u2": 2, "u3": 3, "u4": 4, "kept": 5}
+    for i in range(n):
+        Uo, co = orc.upper_bound(T[i], d[i], I[i], q[i], p.VB, p.FB, l0)
+        assert abs(U[i] - Uo) <= 1e-9 * max(1.0, Uo), (i, U[i], Uo)
+        if abs(Uo - l0) > 1e-9:
+            assert code[i] == names[co], (i, code[i], co)
+
+
+def _load_golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _load_golden(), ids=lambda c: c["name"])
+def test_closed_form_pairs_gpu(hd, case):
+    VA, FA = np.array(case["VA"], float), np.array(case["FA"], np.int32)
+    VB, FB = np.array(case["VB"], float), np.array(case["FB"], np.int32)
+    bvh = hd.hd_build_B(VB, FB)
+    r = hd.hd_hausdorff(bvh, VA, FA, case["tol"])
+    assert r["status"] == hd.HD_OK, r
+    assert r["lower"] <= case["h"] + 1e-12 and case["h"] <= r["upper"] + 1e-12
+    assert r["upper"] - r["lower"] <= case["tol"]
+
+
+def _bracket_parity(hd, orc, p, precision=None, tight=True, opt=None):
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    o = opt or hd.hd_options_default(tol_mode=p.tol_mode)
+    if precision is not None:
+        o.precision = precision
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, o)
+    ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    eps = p.tol * (_dA(p.VA, p.FA) if p.tol_mode else 1.0)
+    assert r["status"] == hd.HD_OK, r
+    assert ro["status"] == orc.OK
+    assert r["upper"] - r["lower"] <= eps * (1 + 1e-12)
+    assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + 1e-12 * eps
+    if tight:
+        rt = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol / 100, p.tol_mode)
+        assert r["lower"] <= rt["upper"] + 1e-12 and rt["lower"] <= r["upper"] + 1e-12
+    return r, ro
+
+
+def test_bracket_workload1_fp64(hd, orc):
+    r, ro = _bracket_parity(hd, orc, mg.workload(1))
+    assert r["stats"]["splits"] > 0
+
+
+@pytest.mark.parametrize("k,scale", [(2, 0.02), (2, 0.1), (3, 0.01), (5, 0.005)])
+def test_bracket_reduced_workloads_fp64(hd, orc, k, scale):
+    _bracket_parity(hd, orc, mg.workload(k, scale), tight=(k != 3))
+
+
+def test_bracket_all_bound_orders_fp64(hd, orc):
+    import itertools
+
+    p = mg.workload(1)
+    ref = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, 1e-6, 0)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    for kk in range(1, 5):
+        for order in itertools.permutations((1, 2, 3, 4), kk):
+            o = hd.hd_options_default(bound_order=order, max_face_factor=2000)
+            r = hd.hd_hausdorff(bvh, p.VA, p.FA, 1e-4, o)
+            assert r["status"] in (hd.HD_OK, hd.HD_ERR_CAPACITY), (order, r)
+            assert max(r["lower"], ref["lower"]) <= min(r["upper"], ref["upper"]) + 1e-12, order
+
+
+def test_full_size_workload2_fp64_properties(hd, orc):
+    """The benchmark's workload at full size: the bracket is within eps and holds the
+    oracle's distances of 3000 sampled vertices (each d(v, B) <= h <= u, and l is the
+    maximum over all vertices, so l >= each sample)."""
+    p = mg.workload(2)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode))
+    eps = p.tol * _dA(p.VA, p.FA)
+    assert r["status"] == hd.HD_OK and r["upper"] - r["lower"] <= eps
+    rng = np.random.default_rng(9)
+    P = np.asarray(p.VA, float)[rng.choice(len(p.VA), size=3000, replace=False)]
+    do, _, _ = orc.nearest(P, p.VB, p.FB)
+    assert do.max() <= r["lower"] * (1 + REL) and do.max() <= r["upper"]
+
+
+def test_invalid_inputs_gpu(hd):
+    V = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    F = np.array([[0, 1, 2]], np.int32)
+    bvh = hd.hd_build_B(V, F)
+    with pytest.raises(hd.HdError):
+        hd.hd_hausdorff(bvh, V, np.array([[0, 1, 3]], np.int32), 1e-3)
+    Vn = V.copy()
+    Vn[2, 2] = np.nan
+    with pytest.raises(hd.HdError):
+        hd.hd_hausdorff(bvh, Vn, F, 1e-3)
+    with pytest.raises(hd.HdError):
+        hd.hd_build_B(Vn, F)
+    with pytest.raises(hd.HdError):
+        hd.hd_hausdorff(bvh, V, F, 0.0)
+
+
+def test_capacity_returns_valid_bracket(hd, orc):
+    p = mg.workload(1)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    ref = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, 1e-7, 0)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, 1e-7, hd.hd_options_default(max_face_factor=1.5))
+    assert r["status"] == hd.HD_ERR_CAPACITY
+    assert r["lower"] <= ref["upper"] + 1e-12 and ref["lower"] <= r["upper"] + 1e-12
+
+
+def test_identical_meshes_gpu(hd):
+    V, F = mg.icosphere(2)
+    bvh = hd.hd_build_B(V, F)
+    r = hd.hd_hausdorff(bvh, V, F, 1e-3)
+    assert r["status"] == hd.HD_OK and 0 <= r["lower"] <= 1e-12 and r["upper"] <= 1e-3
+
+
+def test_device_inputs_and_streams(hd):
+    """Device tensors on a side stream give the same bracket as host arrays."""
+    p = mg.workload(1)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r1 = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        VA = torch.from_numpy(p.VA).cuda()
+        FA = torch.from_numpy(p.FA).cuda()
+        r2 = hd.hd_hausdorff(bvh, VA, FA, p.tol)
+    assert r1["lower"] == r2["lower"] and abs(r1["upper"] - r2["upper"]) <= p.tol
