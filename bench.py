@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark: certified h(A, B) queries per second on one GB300.
+
+Workload (one pair per step and per rank): A = torus R=1, r=0.3 on a 400 x 250 grid
+(200,000 triangles, vertex normal noise sigma 1e-3), B = the same torus re-triangulated
+on a 224 x 112 grid with 0.3-cell jitter (50,176 triangles), tol = 1e-5 x bbox diagonal of
+A; float32 vertices, seeded synthetic data.  A step is the whole hot path: BVH build of B,
+round 0 (vertex queries, lower bound, bounds of every face) and every frontier round to
+convergence.  Inputs are resident in HBM; L2 is flushed (256 MiB write) between timed
+steps; steps are timed with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
+
+Under torchrun (N > 1) every rank runs its own replica of the pair (independent units, no
+collective on the data path); the value is all ranks' pairs / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import meshgen as mg  # noqa: E402
+
+METRIC = "certified h(A,B) queries/s"
+UNIT = "pairs/s"
+WORKLOAD = 2
+# CPU-baseline sample: the oracle on 1/16 of A's faces (a band of the torus) against all of B
+SLICES = 16
+# flops per unit, counted from the kernel source (see the design notes): one point-triangle
+# closest-point evaluation (Voronoi-region method, face-region path) and one child-box test
+FLOPS_PER_LEAF_TEST = 80
+FLOPS_PER_BOX_TEST = 17
+BYTES_PER_NODE = 64
+# device->host bytes per step besides results: build flags (8), bbox of A (64) and one
+# RunState (144 B) per round plus round 0
+RUNSTATE_BYTES = 144
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-arm", action="store_true")
+    return ap.parse_args()
+
+
+def workload_desc(p):
+    return (f"{p.name}: torus pair, A {len(p.FA):,} triangles (400x250 grid, normal noise 1e-3), "
+            f"B {len(p.FB):,} triangles (224x112 grid, 0.3-cell jitter), tol 1e-5 x bbox diagonal of A")
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_sample(p, k: int, eps_abs: float):
+    """Oracle on slice k of A's faces (1/SLICES of them) against all of B; returns seconds."""
+    import oracle
+
+    n = len(p.FA)
+    a, b = k * n // SLICES, (k + 1) * n // SLICES
+    t = time.perf_counter()
+    r = oracle.hausdorff(p.VA, p.FA[a:b], p.VB, p.FB, eps_abs, 0)
+    dt = time.perf_counter() - t
+    return dt, r
+
+
+def cpu_baseline(p, eps_abs, slices=(0, SLICES // 2)):
+    import oracle
+
+    oracle.build()
+    t = 0.0
+    for k in slices:
+        dt, _ = oracle_sample(p, k, eps_abs)
+        t += dt
+    frac = len(slices) / SLICES
+    return dict(value=frac / t, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"FP64 oracle (brute-force distances, best-first queue) on {len(slices)} slices of 1/{SLICES} "
+                       f"of A's faces each against all of B at the same absolute eps; {t:.2f} s for "
+                       f"{frac:.4f} of the pair, scaled to pairs/s")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    p = mg.workload(WORKLOAD)
+    VA = p.VA.astype(np.float64)
+    eps_abs = p.tol * float(np.linalg.norm(VA.max(0) - VA.min(0)))
+    for w in range(args.warmup):
+        oracle_sample(p, w % SLICES, eps_abs)
+    ts = []
+    for k in range(args.steps):
+        dt, _ = oracle_sample(p, k % SLICES, eps_abs)
+        ts.append(dt)
+    total = sum(ts)
+    value = args.steps / SLICES / total
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=workload_desc(p), sample=f"each step: 1/{SLICES} of A's faces (rotating bands)"),
+                cpu_baseline=dict(value=value, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                                  sample=f"each step is 1/{SLICES} of A's faces against all of B; value scaled to "
+                                         "whole pairs per second"),
+                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.rows, self.proc = [], None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        if not sm:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0)
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx) if mx else None, reasons=reasons,
+                    samples=len(sm))
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2406_10357_gb300", "csrc")
+    for f in sorted(os.listdir(src)):
+        h.update(open(os.path.join(src, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kind: str, precision: str):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
+    taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if "=" in line and not line.startswith("#"):
+            k, v = line.strip().split("=", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_digest") != source_digest() or kv.get(f"{kind}.{precision}.bytes_per_launch") is None:
+        return None
+    return float(kv[f"{kind}.{precision}.bytes_per_launch"])
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def run_ours(args):
+    import torch
+
+    import paper_2406_10357_gb300 as hd
+    from paper_2406_10357_gb300 import build as hb
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if rank == 0 or not hb.up_to_date():
+        hb.build()
+    if dist:
+        dist.barrier()
+
+    p = mg.workload(WORKLOAD)
+    VA = torch.from_numpy(p.VA).to(dev)
+    FA = torch.from_numpy(p.FA).to(dev)
+    VB = torch.from_numpy(p.VB).to(dev)
+    FB = torch.from_numpy(p.FB).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    prec = hd.HD_MIXED if args.precision == "mixed" else hd.HD_FP64
+    opt = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=prec)
+
+    def step(o):
+        bvh = hd.hd_build_B(VB, FB)
+        r = hd.hd_hausdorff(bvh, VA, FA, p.tol, o)
+        if r["status"] != hd.HD_OK:
+            raise RuntimeError(f"step failed: {r}")
+        return r
+
+    def timed(o, k):
+        ts, rs = [], []
+        for _ in range(k):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rs.append(step(o))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return ts, rs
+
+    for _ in range(args.warmup):
+        step(opt)
+    hd.hd_trace_read(reset=True)
+    hd.hd_trace_enable(True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ts, rs = timed(opt, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    hd.hd_trace_enable(False)
+    trace = hd.hd_trace_read(reset=True)
+
+    total_ms = sum(ts)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # mixed vs FP64 at the same tol (same workload, fewer steps)
+    fp64 = None
+    if not args.no_fp64_arm and prec == hd.HD_MIXED:
+        o64 = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64)
+        step(o64)
+        k64 = max(3, args.steps // 4)
+        t64, r64 = timed(o64, k64)
+        fp64 = dict(value=k64 / (sum(t64) / 1e3), ms_per_step=sum(t64) / k64, lower=r64[-1]["lower"],
+                    upper=r64[-1]["upper"])
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    e2e_ts, e2e_r = [], None
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bvh = hd.hd_build_B(p.VB, p.FB)
+        e2e_r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, opt)
+        lo, up = e2e_r["lower"], e2e_r["upper"]  # result already on the host
+        e2e_ts.append(time.perf_counter() - t0)
+    e2e_total = sum(e2e_ts)
+    if dist:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    h2d = p.VA.nbytes + p.FA.nbytes + p.VB.nbytes + p.FB.nbytes
+    d2h = 8 + 64 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
+
+    # roofline of the dominant kernel kind, from the trace of the timed steps
+    stats = [r["stats"] for r in rs]
+    leaf = sum(s["leaf_tests"] for s in stats)
+    boxes = sum(s["box_tests"] for s in stats)
+    evals = sum(s["pointtri_evals"] for s in stats)
+    dom = max(("query", "bound", "select", "build", "prep"), key=lambda k: trace[k]["ms"])
+    q = trace["query"]
+    peaks, src = measured_peaks()
+    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if prec == hd.HD_MIXED:
+        peak_tf = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12  # FP32 lanes x FMA x max SM clock
+        peak_note = f"FP32: 152 SMs x 128 lanes x 2 flops x {clock_mhz:.0f} MHz (derived, {src} clock)"
+    else:
+        peak_tf = 1.25  # FP64 nominal for GB300 (the pool's profiling recipe)
+        peak_note = "FP64 nominal 1.25 TFLOP/s"
+    q_flops = FLOPS_PER_LEAF_TEST * leaf + FLOPS_PER_BOX_TEST * boxes
+    achieved = q_flops / (q["ms"] / 1e3) / 1e12 if q["ms"] > 0 else 0.0
+    roof = dict(kernel="k_query (nearest-triangle traversal)", dominant_kind=dom, bound="alu",
+                achieved=achieved, peak=peak_tf, unit="TFLOP/s", frac=achieved / peak_tf,
+                traffic=profiled_traffic("query", args.precision), peak_note=peak_note,
+                algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x leaf tests + {FLOPS_PER_BOX_TEST} flops x box tests",
+                launches=q["launches"], ms_per_launch=q["ms"] / max(1, q["launches"]),
+                l2_bytes_per_launch=(BYTES_PER_NODE * boxes / 2 + 48 * leaf) / max(1, q["launches"]),
+                share={k: round(trace[k]["ms"] / max(1e-9, sum(v["ms"] for v in trace.values())), 4) for k in trace})
+
+    # kernel launches in the timed region: build (24, or 22 when B fits one leaf), A's
+    # validation (2), pool init (1), round-0 query and bound (2), 4 per frontier round
+    nb = len(p.FB)
+    build_k = 24 if nb > 4 else 22
+    launches = sum(build_k + 5 + 4 * s["rounds"] for s in stats)
+
+    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32" if prec == hd.HD_MIXED else "f64", data="synthetic",
+                config=dict(workload=workload_desc(p), precision=args.precision, l2="flushed between steps (256 MiB write)",
+                            parallelism="replicas" if world > 1 else "single"),
+                pointtri_evals_per_s=world * evals / (total_ms / 1e3),
+                result=dict(lower=rs[-1]["lower"], upper=rs[-1]["upper"], eps_abs=rs[-1]["stats"]["eps_abs"],
+                            rounds=rs[-1]["stats"]["rounds"], splits=rs[-1]["stats"]["splits"]),
+                roofline=roof, e2e=dict(value=world * len(e2e_ts) / e2e_total, unit=UNIT, h2d_bytes_per_step=h2d,
+                                        d2h_bytes_per_step=d2h),
+                gpu_launches=launches, clocks=clk, fp64_arm=fp64)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        VAd = p.VA.astype(np.float64)
+        line["cpu_baseline"] = cpu_baseline(p, p.tol * float(np.linalg.norm(VAd.max(0) - VAd.min(0))))
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

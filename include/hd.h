@@ -81,9 +81,10 @@ typedef struct {
   int64_t splits;            /* sub-triangles split 1->4 (Section 4's B&B iterations)      */
   int64_t queries;           /* nearest-triangle queries (vertices of A and midpoints)     */
   int64_t pointtri_evals;    /* point-triangle distance evaluations (leaf tests + u3)      */
-  int64_t box_tests;         /* BVH child-box distance evaluations                         */
-  int64_t discards[6];       /* sub-triangles discarded, by the deciding bound:
-                                exact, u1, u2, u3, u4 (index 5 unused)                     */
+  int64_t leaf_tests;        /* ... of which in the BVH traversal (leaf triangles tested)  */
+  int64_t box_tests;         /* BVH child-box distance evaluations (2 per node visited)    */
+  int64_t discards[6];       /* sub-triangles discarded, by the deciding bound: exact, u1,
+                                u2, u3, u4; [5] = discarded later because l grew past U    */
   int64_t retired;           /* sub-triangles kept but never split again: l <= U <= l + eps */
   int64_t fp64_escalations;  /* MIXED: point-triangle tests redone in FP64 (slivers)        */
   int64_t peak_frontier;     /* largest live frontier                                       */
@@ -150,6 +151,25 @@ int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t
  * FP64 arithmetic.  Asynchronous on `stream`. */
 int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const int32_t* TI, const double* Tq,
                     int64_t n, double l, const hd_options* opt, void* stream, double* U, int32_t* code);
+
+/* Kernel timing trace.  While enabled (process-wide), the library records a CUDA event
+ * pair on the launching stream around each of its kernels and accumulates, per kind,
+ * the number of launches and their total device time in milliseconds.  Each pair costs a
+ * few microseconds of host time.  Kinds: the whole BVH build of one hd_build_B call
+ * (counted as one launch), the nearest-triangle traversal, UpperBound of faces and
+ * children, select/split/compaction, and validation/pool set-up. */
+enum { HD_K_BUILD = 0, HD_K_QUERY = 1, HD_K_BOUND = 2, HD_K_SELECT = 3, HD_K_PREP = 4, HD_K_KINDS = 5 };
+typedef struct {
+  int64_t launches[8];
+  double ms[8];
+} hd_trace;
+
+/* Turn the trace on (1) or off (0). */
+void hd_trace_enable(int on);
+
+/* Copy the accumulated trace into *out (waits for the recorded events); reset != 0
+ * clears it afterwards. */
+int hd_trace_read(hd_trace* out, int reset);
 
 /* Name of a status code (static string). */
 const char* hd_status_str(int status);

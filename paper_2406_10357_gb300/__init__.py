@@ -36,13 +36,21 @@ class HdOptions(C.Structure):
 
 class HdStats(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("splits", C.c_int64), ("queries", C.c_int64), ("pointtri_evals", C.c_int64),
-                ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
+                ("leaf_tests", C.c_int64), ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
                 ("eps_abs", C.c_double), ("dA", C.c_double)]
 
 
 class HdResult(C.Structure):
     _fields_ = [("lower", C.c_double), ("upper", C.c_double), ("status", C.c_int32), ("stats", HdStats)]
+
+
+class HdTrace(C.Structure):
+    _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
+
+
+HD_K_BUILD, HD_K_QUERY, HD_K_BOUND, HD_K_SELECT, HD_K_PREP = range(5)
+KERNEL_KINDS = ("build", "query", "bound", "select", "prep")
 
 
 _lib = None
@@ -68,6 +76,10 @@ def lib():
                                            C.POINTER(HdResult)]
         L.hd_nearest.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
         L.hd_upper_bounds.argtypes = [vp, vp, vp, vp, vp, i64, d, C.POINTER(HdOptions), vp, vp, vp]
+        L.hd_trace_enable.argtypes = [C.c_int]
+        L.hd_trace_enable.restype = None
+        L.hd_trace_read.argtypes = [C.POINTER(HdTrace), C.c_int]
+        L.hd_trace_read.restype = C.c_int
         L.hd_status_str.argtypes = [C.c_int]
         L.hd_status_str.restype = C.c_char_p
         L.hd_last_error.restype = C.c_char_p
@@ -173,10 +185,22 @@ def hd_free_B(bvh: Bvh):
         bvh.handle = C.c_void_p(0)
 
 
+def hd_trace_enable(on: bool = True):
+    """Record CUDA events around the library's kernels (per kind: launches, total ms)."""
+    lib().hd_trace_enable(1 if on else 0)
+
+
+def hd_trace_read(reset: bool = False) -> dict:
+    t = HdTrace()
+    _check(lib().hd_trace_read(C.byref(t), 1 if reset else 0), "hd_trace_read")
+    return {KERNEL_KINDS[k]: dict(launches=t.launches[k], ms=t.ms[k]) for k in range(len(KERNEL_KINDS))}
+
+
 def _result(r: HdResult) -> dict:
     s = r.stats
     return dict(lower=r.lower, upper=r.upper, status=r.status, status_str=hd_status_str(r.status),
                 stats=dict(rounds=s.rounds, splits=s.splits, queries=s.queries, pointtri_evals=s.pointtri_evals,
+                           leaf_tests=s.leaf_tests,
                            box_tests=s.box_tests, discards={BOUND_NAMES[k]: s.discards[k] for k in range(6)},
                            retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
                            pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA))

@@ -2,6 +2,7 @@
 // branch-and-bound, and the step-level entry points used for parity checks.
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hd_bnb.cuh"
@@ -14,6 +15,67 @@ static thread_local char g_err[512] = "";
 int set_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
   snprintf(g_err, sizeof g_err, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
   return HD_ERR_CUDA;
+}
+
+// ----------------------------------------------------------------------------- kernel trace
+
+namespace {
+struct Pending {
+  int kind;
+  cudaEvent_t a, b;
+};
+struct Trace {
+  std::mutex m;
+  bool on = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  int64_t launches[8] = {};
+  double ms[8] = {};
+  cudaEvent_t get() {
+    if (!free_events.empty()) {
+      cudaEvent_t e = free_events.back();
+      free_events.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  void resolve() {  // caller holds m
+    for (auto& p : pending) {
+      float t = 0.f;
+      if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) {
+        launches[p.kind] += 1;
+        ms[p.kind] += t;
+      }
+      free_events.push_back(p.a);
+      free_events.push_back(p.b);
+    }
+    pending.clear();
+  }
+};
+Trace& trace() {
+  static Trace* t = new Trace();  // never destroyed: events may outlive static destruction order
+  return *t;
+}
+}  // namespace
+
+TraceScope::TraceScope(int k, cudaStream_t st) : kind(k), s(st) {
+  Trace& t = trace();
+  std::lock_guard<std::mutex> g(t.m);
+  if (!t.on) return;
+  a = t.get();
+  b = t.get();
+  if (a) cudaEventRecord(a, s);
+}
+
+TraceScope::~TraceScope() {
+  if (!a || !b) return;
+  Trace& t = trace();
+  std::lock_guard<std::mutex> g(t.m);
+  cudaEventRecord(b, s);
+  t.pending.push_back({kind, a, b});
+  if (t.pending.size() > 4096) t.resolve();
 }
 
 int resolve_options(const hd_options* in, Opts* o) {
@@ -65,7 +127,7 @@ static void keep_pool_memory() {
   }
 }
 
-int prepare_A(const RunIO& io, uint8_t* ref, double* dA, int64_t* n_ref) {
+int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax) {
   cudaStream_t s = io.s;
   unsigned long long* box = nullptr;
   HD_TRY(cudaMallocAsync((void**)&box, 64, s));
@@ -73,11 +135,14 @@ int prepare_A(const RunIO& io, uint8_t* ref, double* dA, int64_t* n_ref) {
   HD_TRY(cudaMemcpyAsync(box, init, 64, cudaMemcpyHostToDevice, s));
   HD_TRY(cudaMemsetAsync(ref, 0, io.nVA, s));
   int* bad = (int*)(box + 6);
-  k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
-  if (io.vtype == HD_F64)
-    k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
-  else
-    k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
+  {
+    TraceScope tr(HD_K_PREP, s);
+    k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
+    if (io.vtype == HD_F64)
+      k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
+    else
+      k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
+  }
   HD_TRY_LAUNCH();
   unsigned long long h[8];
   HD_TRY(cudaMemcpyAsync(h, box, 64, cudaMemcpyDeviceToHost, s));
@@ -92,60 +157,17 @@ int prepare_A(const RunIO& io, uint8_t* ref, double* dA, int64_t* n_ref) {
   }
   double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
   *dA = sqrt(dx * dx + dy * dy + dz * dz);
-  *n_ref = 0;
+  *amax = 0.0;
+  for (int k = 0; k < 6; ++k) *amax = fmax(*amax, fabs(v[k]));
   return HD_OK;
 }
 
 int run_fp64(const RunIO& io) { return run_bnb<PolicyD>(io); }
 int run_mixed(const RunIO& io);
 
-template <class P, typename T>
-__global__ void k_points_in(const T* P_, int64_t n, typename P::Vtx* v) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  typename P::Vtx x;
-  memset(&x, 0, sizeof x);
-  x.x = (double)P_[3 * i];
-  x.y = (double)P_[3 * i + 1];
-  x.z = (double)P_[3 * i + 2];
-  x.tri = -2;
-  x.hint = -1;
-  v[i] = x;
-}
-
-template <class P>
-__global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tri_vid, double* dist, int32_t* idx,
-                             double* foot, double* dlo) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  typename P::Vtx x = v[i];
-  dist[i] = P::out_dist(x);
-  idx[i] = x.tri >= 0 ? tri_vid[x.tri].w : -1;
-  D3 f = P::out_foot(x);
-  foot[3 * i] = f.x;
-  foot[3 * i + 1] = f.y;
-  foot[3 * i + 2] = f.z;
-  if (dlo) dlo[i] = P::out_dlo(x);
-}
-
-template <class P>
-int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
-                   int32_t* idx, double* foot, double* dlo) {
-  typename P::Vtx* tmp = nullptr;
-  RunState* st = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&tmp, sizeof(typename P::Vtx) * n, s));
-  HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
-  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
-  if (ptype == HD_F64)
-    k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, tmp);
-  else
-    k_points_in<P, float><<<blocks_for(n, 256), 256, 0, s>>>((const float*)Pts, n, tmp);
-  k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), tmp, n, st);
-  k_points_out<P><<<blocks_for(n, 256), 256, 0, s>>>(tmp, n, B->tri_vid, dist, idx, foot, dlo);
-  HD_TRY_LAUNCH();
-  HD_TRY(cudaFreeAsync(tmp, s));
-  HD_TRY(cudaFreeAsync(st, s));
-  return HD_OK;
+int nearest_points_fp64(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
+                        int32_t* idx, double* foot, double* dlo) {
+  return nearest_points<PolicyD>(B, Pts, ptype, n, s, dist, idx, foot, dlo);
 }
 int nearest_points_mixed(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                          int32_t* idx, double* foot, double* dlo);
@@ -209,6 +231,28 @@ const char* hd_status_str(int s) {
 }
 
 const char* hd_last_error(void) { return g_err; }
+
+void hd_trace_enable(int on) {
+  Trace& t = trace();
+  std::lock_guard<std::mutex> g(t.m);
+  t.on = on != 0;
+}
+
+int hd_trace_read(hd_trace* out, int reset) {
+  if (!out) return HD_ERR_INVALID;
+  Trace& t = trace();
+  std::lock_guard<std::mutex> g(t.m);
+  t.resolve();
+  for (int k = 0; k < 8; ++k) {
+    out->launches[k] = t.launches[k];
+    out->ms[k] = t.ms[k];
+  }
+  if (reset) {
+    memset(t.launches, 0, sizeof t.launches);
+    memset(t.ms, 0, sizeof t.ms);
+  }
+  return HD_OK;
+}
 
 int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** out) {
   if (!out) return HD_ERR_INVALID;
@@ -284,7 +328,7 @@ int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t
   if (n == 0) return HD_OK;
   keep_pool_memory();
   cudaStream_t s = (cudaStream_t)stream;
-  if (precision == HD_FP64) return nearest_points<PolicyD>(B, P, ptype, n, s, dist, idx, foot, dist_lo);
+  if (precision == HD_FP64) return nearest_points_fp64(B, P, ptype, n, s, dist, idx, foot, dist_lo);
   return nearest_points_mixed(B, P, ptype, n, s, dist, idx, foot, dist_lo);
 }
 
@@ -296,6 +340,7 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
   if (!T || !Td || !TI || !Tq || !U || !code) return HD_ERR_INVALID;
   RunParams rp;
   rp.eps = 0.0;
+  rp.slack = 0.0;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   cudaStream_t s = (cudaStream_t)stream;

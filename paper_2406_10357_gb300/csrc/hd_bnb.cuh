@@ -25,12 +25,6 @@
 
 namespace hd {
 
-struct RunParams {
-  double eps;  // absolute tolerance
-  uint8_t order[4];
-  int n_bounds;
-};
-
 __device__ inline unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -42,10 +36,13 @@ __device__ inline double warp_max(double v) {
 
 // Flush per-thread counters with one atomic per warp.  Every lane of the warp must call it.
 __device__ inline void flush_counters(RunState* st, const Counters& c) {
-  unsigned long long e = warp_sum(c.evals), b = warp_sum(c.boxes);
+  unsigned long long e = warp_sum(c.evals), b = warp_sum(c.boxes), lf = warp_sum(c.leaf),
+                     x = warp_sum(c.escalations);
   if ((threadIdx.x & 31) == 0) {
-    if (e) atomicAdd(&st->evals, e);
+    if (e + lf) atomicAdd(&st->evals, e + lf);
+    if (lf) atomicAdd(&st->leaf_tests, lf);
     if (b) atomicAdd(&st->box_tests, b);
+    if (x) atomicAdd(&st->escalations, x);
   }
   if (c.err) atomicExch(&st->err, 1);
 }
@@ -71,19 +68,30 @@ __device__ inline unsigned long long double_to_ordered(double d) {
 template <typename T>
 static __global__ void k_check_bbox(const T* VA, int64_t nVA, const uint8_t* ref, unsigned long long* box, int* bad) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nVA) return;
-  double x = VA[3 * i], y = VA[3 * i + 1], z = VA[3 * i + 2];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
-    atomicExch(bad, 1);
-    return;
+  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
+  if (i < nVA) {
+    double x = VA[3 * i], y = VA[3 * i + 1], z = VA[3 * i + 2];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
+      atomicExch(bad, 1);
+    } else if (ref[i]) {
+      lo[0] = hi[0] = double_to_ordered(x);
+      lo[1] = hi[1] = double_to_ordered(y);
+      lo[2] = hi[2] = double_to_ordered(z);
+    }
   }
-  if (!ref[i]) return;
-  atomicMin(&box[0], double_to_ordered(x));
-  atomicMin(&box[1], double_to_ordered(y));
-  atomicMin(&box[2], double_to_ordered(z));
-  atomicMax(&box[3], double_to_ordered(x));
-  atomicMax(&box[4], double_to_ordered(y));
-  atomicMax(&box[5], double_to_ordered(z));
+  // warp reduction first: one atomic per warp and bound instead of one per vertex
+  for (int k = 0; k < 3; ++k)
+    for (int o = 16; o > 0; o >>= 1) {
+      unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[k], o), b = __shfl_xor_sync(0xffffffffu, hi[k], o);
+      lo[k] = a < lo[k] ? a : lo[k];
+      hi[k] = b > hi[k] ? b : hi[k];
+    }
+  if ((threadIdx.x & 31) == 0 && hi[0] != 0) {
+    for (int k = 0; k < 3; ++k) {
+      atomicMin(&box[k], lo[k]);
+      atomicMax(&box[3 + k], hi[k]);
+    }
+  }
 }
 
 template <class P, typename T>
@@ -92,9 +100,7 @@ __global__ void k_init_pool(const T* VA, int64_t nVA, const uint8_t* ref, typena
   if (i >= nVA) return;
   typename P::Vtx v;
   memset(&v, 0, sizeof v);
-  v.x = (double)VA[3 * i];
-  v.y = (double)VA[3 * i + 1];
-  v.z = (double)VA[3 * i + 2];
+  P::set_pos(v, (double)VA[3 * i], (double)VA[3 * i + 1], (double)VA[3 * i + 2]);
   v.tri = ref[i] ? -2 : -1;
   v.hint = -1;
   pool[i] = v;
@@ -104,7 +110,7 @@ __global__ void k_init_pool(const T* VA, int64_t nVA, const uint8_t* ref, typena
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.
 template <class P>
 __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
-                        RunState* st) {
+                        RunState* st, double slack) {
   int count = cap;
   if (count_ptr) count = min(*count_ptr * mult, cap);
   Counters c;
@@ -118,7 +124,7 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
       if (v.tri != -1) {
         P::query(B, v, c);
         pool[beg + t] = v;
-        lmax = fmax(lmax, P::lower(v));
+        lmax = fmax(lmax, P::lower(v) - slack);
         ++nq;
       }
     }
@@ -170,7 +176,7 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
     it.v[1] = FA[3 * f + 1];
     it.v[2] = FA[3 * f + 2];
     int code;
-    it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp.order, rp.n_bounds, code, c.evals);
+    it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
     classify<P>(st, it, l, rp.eps, code, next, next_cap);
   }
   flush_counters(st, c);
@@ -237,8 +243,7 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
       else if (k == 2) { it.v[0] = m31; it.v[1] = m23; it.v[2] = par.z; }
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
-      it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp.order, rp.n_bounds, code,
-                            c.evals);
+      it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
       classify<P>(st, it, l, rp.eps, code, next, next_cap);
     }
   }
@@ -293,7 +298,7 @@ inline double bits_to_double(unsigned long long b) {
 }
 
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
-int prepare_A(const RunIO& io, uint8_t* ref, double* dA, int64_t* n_ref);
+int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax);
 
 template <class P>
 int run_bnb(const RunIO& io) {
@@ -307,8 +312,8 @@ int run_bnb(const RunIO& io) {
   uint8_t* ref = nullptr;
   HD_TRY(cudaMallocAsync((void**)&ref, std::max<int64_t>(io.nVA, 1), s));
   double dA = 0.0;
-  int64_t n_ref = 0;
-  int rc = prepare_A(io, ref, &dA, &n_ref);
+  double amax = 0.0;
+  int rc = prepare_A(io, ref, &dA, &amax);
   if (rc != HD_OK) {
     cudaFreeAsync(ref, s);
     return rc;
@@ -341,6 +346,7 @@ int run_bnb(const RunIO& io) {
   BvhDev B = bvh_dev(io.B);
   RunParams rp;
   rp.eps = eps;
+  rp.slack = P::slack(amax);
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   const int bs = o.block_size;
@@ -353,14 +359,24 @@ int run_bnb(const RunIO& io) {
   const unsigned max_grid = (unsigned)dev_sms * 16;
 
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
-  if (io.vtype == HD_F64)
-    k_init_pool<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, pool);
-  else
-    k_init_pool<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, pool);
+  {
+    TraceScope tr(HD_K_PREP, s);
+    if (io.vtype == HD_F64)
+      k_init_pool<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, pool);
+    else
+      k_init_pool<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, pool);
+  }
   HD_TRY_LAUNCH();
-  k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, pool, 0, nullptr, 1, (int)io.nVA, st);
+  {
+    TraceScope tr(HD_K_QUERY, s);
+    k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, pool, 0, nullptr, 1, (int)io.nVA, st,
+                                                                       rp.slack);
+  }
   HD_TRY_LAUNCH();
-  k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, pool, io.FA, io.nFA, st, rp, front[1], (int)front_cap);
+  {
+    TraceScope tr(HD_K_BOUND, s);
+    k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, pool, io.FA, io.nFA, st, rp, front[1], (int)front_cap);
+  }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
   HD_TRY(cudaStreamSynchronize(s));
@@ -386,14 +402,23 @@ int run_bnb(const RunIO& io) {
       status = HD_ERR_CAPACITY;
       break;
     }
-    k_round_reset<<<1, 1, 0, s>>>(st, (int)n_front);
-    k_select<P><<<blocks_for(n_front, 256), 256, 0, s>>>(front[cur], (int)n_front, st, rp, (int)K, split_par, pool,
-                                                         (int)n_pool, front[cur ^ 1], (int)front_cap);
-    unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
-    k_query<P><<<gq, bs, 0, s>>>(B, pool, (int)n_pool, &st->n_split, 3, (int)(3 * K), st);
-    unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
-    k_bound_children<P><<<gb, bs, 0, s>>>(B, pool, split_par, (int)K, (int)n_pool, st, rp, front[cur ^ 1],
-                                          (int)front_cap);
+    {
+      TraceScope tr(HD_K_SELECT, s);
+      k_round_reset<<<1, 1, 0, s>>>(st, (int)n_front);
+      k_select<P><<<blocks_for(n_front, 256), 256, 0, s>>>(front[cur], (int)n_front, st, rp, (int)K, split_par,
+                                                           pool, (int)n_pool, front[cur ^ 1], (int)front_cap);
+    }
+    {
+      TraceScope tr(HD_K_QUERY, s);
+      unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
+      k_query<P><<<gq, bs, 0, s>>>(B, pool, (int)n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack);
+    }
+    {
+      TraceScope tr(HD_K_BOUND, s);
+      unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
+      k_bound_children<P><<<gb, bs, 0, s>>>(B, pool, split_par, (int)K, (int)n_pool, st, rp, front[cur ^ 1],
+                                            (int)front_cap);
+    }
     HD_TRY_LAUNCH();
     HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     HD_TRY(cudaStreamSynchronize(s));
@@ -426,6 +451,7 @@ int run_bnb(const RunIO& io) {
   S.splits = splits;
   S.queries = (int64_t)hst->queries;
   S.pointtri_evals = (int64_t)hst->evals;
+  S.leaf_tests = (int64_t)hst->leaf_tests;
   S.box_tests = (int64_t)hst->box_tests;
   for (int k = 0; k < 6; ++k) S.discards[k] = (int64_t)hst->discards[k];
   S.retired = (int64_t)hst->retired;
@@ -439,6 +465,59 @@ int run_bnb(const RunIO& io) {
   cudaFreeAsync(split_par, s);
   cudaFreeAsync(st, s);
   cudaFreeAsync(ref, s);
+  return HD_OK;
+}
+
+// ----------------------------------------------------------------------------- point queries
+
+template <class P, typename T>
+__global__ void k_points_in(const T* P_, int64_t n, typename P::Vtx* v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename P::Vtx x;
+  memset(&x, 0, sizeof x);
+  P::set_pos(x, (double)P_[3 * i], (double)P_[3 * i + 1], (double)P_[3 * i + 2]);
+  x.tri = -2;
+  x.hint = -1;
+  v[i] = x;
+}
+
+template <class P>
+__global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tri_vid, double* dist, int32_t* idx,
+                             double* foot, double* dlo) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename P::Vtx x = v[i];
+  dist[i] = P::out_dist(x);
+  idx[i] = x.tri >= 0 ? tri_vid[x.tri].w : -1;
+  D3 f = P::out_foot(x);
+  foot[3 * i] = f.x;
+  foot[3 * i + 1] = f.y;
+  foot[3 * i + 2] = f.z;
+  if (dlo) dlo[i] = P::out_dlo(x);
+}
+
+// hd_nearest: nearest triangle of B for n external points (P as float or double rows).
+template <class P>
+int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
+                   int32_t* idx, double* foot, double* dlo) {
+  typename P::Vtx* tmp = nullptr;
+  RunState* st = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&tmp, sizeof(typename P::Vtx) * n, s));
+  HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
+  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
+  if (ptype == HD_F64)
+    k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, tmp);
+  else
+    k_points_in<P, float><<<blocks_for(n, 256), 256, 0, s>>>((const float*)Pts, n, tmp);
+  {
+    TraceScope tr(HD_K_QUERY, s);
+    k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), tmp, n, st);
+  }
+  k_points_out<P><<<blocks_for(n, 256), 256, 0, s>>>(tmp, n, B->tri_vid, dist, idx, foot, dlo);
+  HD_TRY_LAUNCH();
+  HD_TRY(cudaFreeAsync(tmp, s));
+  HD_TRY(cudaFreeAsync(st, s));
   return HD_OK;
 }
 

@@ -302,7 +302,7 @@ struct PolicyD {
     t.tri64 = B.tri64;
     if (v.hint >= 0) t.test1(v.hint);
     traverse(B, t.p, t, c);
-    c.evals += t.evals;
+    c.leaf += t.evals;
     v.tri = t.best;
     v.d = sqrt(t.best2);
     v.qx = t.q.x;
@@ -313,6 +313,12 @@ struct PolicyD {
   __device__ static double out_dist(const Vtx& v) { return v.d; }
   __device__ static double out_dlo(const Vtx& v) { return v.d; }
   __device__ static D3 out_foot(const Vtx& v) { return {v.qx, v.qy, v.qz}; }
+  static double slack(double) { return 0.0; }
+  __device__ static void set_pos(Vtx& v, double x, double y, double z) {
+    v.x = x;
+    v.y = y;
+    v.z = z;
+  }
   __device__ static void midpoint(const Vtx& a, const Vtx& b, Vtx& m) {
     m.x = 0.5 * (a.x + b.x);
     m.y = 0.5 * (a.y + b.y);
@@ -323,11 +329,11 @@ struct PolicyD {
     m.hint = a.tri;
   }
   __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l,
-                                   const uint8_t* order, int nb, int& code, unsigned long long& evals) {
+                                   const RunParams& rp, int& code, Counters& cnt) {
     VI t[3] = {{{a.x, a.y, a.z}, a.d, a.tri, {a.qx, a.qy, a.qz}},
                {{b.x, b.y, b.z}, b.d, b.tri, {b.qx, b.qy, b.qz}},
                {{c.x, c.y, c.z}, c.d, c.tri, {c.qx, c.qy, c.qz}}};
-    return upper_bound_d(B, t, l, order, nb, code, evals);
+    return upper_bound_d(B, t, l, rp.order, rp.n_bounds, code, cnt.evals);
   }
 };
 

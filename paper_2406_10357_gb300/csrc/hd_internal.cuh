@@ -67,11 +67,12 @@ struct __align__(16) VtxD {  // HD_FP64
 static_assert(sizeof(VtxD) == 64, "VtxD is 64 B");
 
 struct __align__(16) VtxM {  // HD_MIXED
-  double x, y, z;
-  float qx, qy, qz;  // closest point q relative to the float position p32 = (float)p
-  float qerr;        // a point of triangle `tri` lies within qerr of p32 + (qx,qy,qz)
-  float dhi;         // >= d(p, S_tri) for the exact p (certified)
-  float dlo;         // <= d(p, B) for the exact p (certified)
+  float hx, hy, hz;  // position p = h + l: h the nearest float, l the float residual
+  float lx, ly, lz;
+  float qx, qy, qz;  // closest point q relative to p
+  float qerr;        // a point of triangle `tri` lies within qerr of p + (qx,qy,qz)
+  float dhi;         // >= d(p, S_tri) (certified)
+  float dlo;         // <= d(p, B) (certified)
   int tri;
   int hint;
   float pad0, pad1;
@@ -99,7 +100,7 @@ struct RunState {
   int n_pool;                    // vertices in the pool
   int overflow;                  // next frontier or split list ran out of room
   int err;                       // traversal stack overflow and similar
-  unsigned long long evals, box_tests, queries, retired, escalations;
+  unsigned long long evals, box_tests, queries, retired, escalations, leaf_tests;
   unsigned long long discards[6];
 };
 
@@ -113,9 +114,18 @@ struct BvhDev {
   float eta;
 };
 
+// Per-run constants of the round kernels.
+struct RunParams {
+  double eps;    // absolute tolerance
+  double slack;  // added to upper bounds, subtracted from lower bounds (MIXED: representation
+                 // error of subdivided vertices as float pairs; 0 in FP64)
+  uint8_t order[4];
+  int n_bounds;
+};
+
 // Per-thread statistics, flushed with one atomic per warp.
 struct Counters {
-  unsigned long long evals = 0, boxes = 0, escalations = 0;
+  unsigned long long evals = 0, boxes = 0, escalations = 0, leaf = 0;
   int err = 0;
 };
 
@@ -225,6 +235,15 @@ struct Opts {
   uint8_t order[4];
 };
 int resolve_options(const hd_options* in, Opts* out);
+
+// Kernel timing trace (hd_trace_enable): an event pair around a launch when enabled.
+struct TraceScope {
+  TraceScope(int kind, cudaStream_t s);
+  ~TraceScope();
+  int kind;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr, b = nullptr;
+};
 
 // Build-time helpers implemented in hd_lbvh.cu.
 int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out);

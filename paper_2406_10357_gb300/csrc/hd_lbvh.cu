@@ -420,6 +420,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
       *pleaf = ints + 5 * n, *flags = ints + 6 * n;
   unsigned* misc = (unsigned*)(scratch + o_misc);  // [0..5] centroid box, [6] bad, [7] eta bits
 
+  TraceScope trace_build(HD_K_BUILD, s);  // the whole build counts as one launch
   unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
   HD_TRY(cudaMemcpyAsync(misc, init, sizeof init, cudaMemcpyHostToDevice, s));
   int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s)

@@ -1,0 +1,530 @@
+// Certified FP32 policy (HD_MIXED).
+//
+// Distances and bounds run in float with directed rounding where a bound needs it, so that
+// every lower bound stays below and every upper bound above the exact value:
+//
+//  * Positions of sub-triangle vertices are pairs of floats h + l (l holds the rounding
+//    residual of the exact midpoint), and every geometric difference is taken locally,
+//    (x - h) - l, so rounding errors scale with local sizes (distances, triangle sizes),
+//    not with the coordinates.
+//  * Point-triangle distance: the closest point is found on the local triangle by
+//    Voronoi-region classification (Ericson 2005) with barycentric weights clamped into
+//    the simplex, so it is a point of the triangle up to a few units of rounding; its
+//    length plus an a-priori error term (48 u M, M the local magnitude, u = 2^-24) is an
+//    upper bound.  The lower bound is a support-function certificate: for any n with
+//    |n| <= 1, d(p, S) >= min over the vertices X of S of n.(X - p), evaluated with
+//    downward rounding; n points to the computed closest point, which makes it tight
+//    whenever the classification was right.  If the certificate is loose (near-degenerate
+//    sliver, where the barycentric test is ill-conditioned), the test is redone in FP64.
+//  * Box distances for pruning are lower bounds (downward rounding); pruning compares
+//    them with the best certified upper bound, so the minimum of the tested lower bounds
+//    is a lower bound of d(p, B).
+//  * Bounds of Section 3.2 take certified vertex distances (upper bounds), edge lengths
+//    rounded up, the circumradius only with the area rounded down, and the split points of
+//    u3 with their representation error added.  u4 runs in FP64 with a relative margin.
+#pragma once
+
+#include "hd_fp64.cuh"
+#include "hd_internal.cuh"
+
+namespace hd {
+
+constexpr float kU = 5.9604644775390625e-08f;  // 2^-24
+
+struct F3 {
+  float x, y, z;
+};
+__device__ inline F3 f3(float x, float y, float z) { return {x, y, z}; }
+__device__ inline F3 operator+(F3 a, F3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ inline F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ inline float dotf(F3 a, F3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+__device__ inline float amax3(F3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
+__device__ inline float norm_ru(F3 a) {
+  return __fsqrt_ru(__fmaf_ru(a.x, a.x, __fmaf_ru(a.y, a.y, __fmul_ru(a.z, a.z))));
+}
+__device__ inline float norm_rd(F3 a) {
+  return __fsqrt_rd(__fmaf_rd(a.x, a.x, __fmaf_rd(a.y, a.y, __fmul_rd(a.z, a.z))));
+}
+
+// A point as the unevaluated sum h + l of two float triples.
+struct FFP {
+  F3 h, l;
+};
+
+// x - p for a float point x, taken locally: (x - h) - l.
+__device__ inline F3 local_off(float4 x, const FFP& p) {
+  return {(x.x - p.h.x) - p.l.x, (x.y - p.h.y) - p.l.y, (x.z - p.h.z) - p.l.z};
+}
+
+// Barycentric weights (v, w) of the point of triangle (A, B, C) closest to the origin,
+// Voronoi-region classification, clamped so that v, w >= 0 and v + w <= 1 exactly.
+__device__ inline void closest_bary(F3 A, F3 B, F3 C, float& v, float& w) {
+  F3 ab = B - A, ac = C - A;
+  float d1 = -dotf(ab, A), d2 = -dotf(ac, A);
+  v = 0.f;
+  w = 0.f;
+  if (d1 <= 0.f && d2 <= 0.f) return;
+  float d3 = -dotf(ab, B), d4 = -dotf(ac, B);
+  if (d3 >= 0.f && d4 <= d3) {
+    v = 1.f;
+    return;
+  }
+  float vc = d1 * d4 - d3 * d2;
+  if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
+    float den = d1 - d3;
+    v = den > 0.f ? fminf(fmaxf(d1 / den, 0.f), 1.f) : 0.f;
+    return;
+  }
+  float d5 = -dotf(ab, C), d6 = -dotf(ac, C);
+  if (d6 >= 0.f && d5 <= d6) {
+    w = 1.f;
+    return;
+  }
+  float vb = d5 * d2 - d1 * d6;
+  if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
+    float den = d2 - d6;
+    w = den > 0.f ? fminf(fmaxf(d2 / den, 0.f), 1.f) : 0.f;
+    return;
+  }
+  float va = d3 * d6 - d5 * d4;
+  if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
+    float den = (d4 - d3) + (d5 - d6);
+    float t = den > 0.f ? fminf(fmaxf((d4 - d3) / den, 0.f), 1.f) : 0.f;
+    v = __fsub_rd(1.f, t);
+    w = t;
+    return;
+  }
+  float den = va + vb + vc;
+  if (den > 0.f) {
+    float inv = 1.f / den;
+    v = fminf(fmaxf(vb * inv, 0.f), 1.f);
+    w = fmaxf(vc * inv, 0.f);
+  } else {  // zero area: best of the three edges
+    float best = INFINITY;
+    F3 e[3] = {ab, C - B, A - C};
+    F3 o[3] = {A, B, C};
+    for (int k = 0; k < 3; ++k) {
+      float ee = dotf(e[k], e[k]);
+      float t = ee > 0.f ? fminf(fmaxf(-dotf(o[k], e[k]) / ee, 0.f), 1.f) : 0.f;
+      F3 q = {fmaf(t, e[k].x, o[k].x), fmaf(t, e[k].y, o[k].y), fmaf(t, e[k].z, o[k].z)};
+      float dq = dotf(q, q);
+      if (dq < best) {
+        best = dq;
+        if (k == 0) { v = t; w = 0.f; }
+        else if (k == 1) { v = __fsub_rd(1.f, t); w = t; }
+        else { v = 0.f; w = __fsub_rd(1.f, t); }
+      }
+    }
+  }
+  w = fminf(w, __fsub_rd(1.f, v));
+}
+
+struct PtOut {
+  float hi;    // >= d(p, S)
+  float lo;    // <= d(p, S)
+  F3 q;        // closest point relative to p
+  float qerr;  // a point of S lies within qerr of p + q
+  bool esc;    // redone in FP64
+};
+
+// Certified distance from p = h + l to the float triangle (a, b, c).
+__device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bool want_lo, PtOut& o) {
+  F3 A = local_off(a4, P), B = local_off(b4, P), C = local_off(c4, P);
+  float M = fmaxf(fmaxf(amax3(A), amax3(B)), fmaxf(amax3(C), amax3(P.l)));
+  float v, w;
+  closest_bary(A, B, C, v, w);
+  F3 E1 = B - A, E2 = C - A;
+  F3 Q = {fmaf(w, E2.x, fmaf(v, E1.x, A.x)), fmaf(w, E2.y, fmaf(v, E1.y, A.y)), fmaf(w, E2.z, fmaf(v, E1.z, A.z))};
+  float nq = norm_ru(Q);
+  o.hi = __fadd_ru(nq, __fmul_ru(48.f * kU, M));
+  o.q = Q;
+  o.qerr = __fmul_ru(40.f * kU, M);
+  o.esc = false;
+  o.lo = 0.f;
+  if (!want_lo) return;
+  float lo = 0.f;
+  if (nq > 0.f) {
+    float s = __frcp_rd(nq);
+    F3 n = {__fmul_rz(Q.x, s), __fmul_rz(Q.y, s), __fmul_rz(Q.z, s)};  // |n| <= 1
+    float da = __fmaf_rd(n.x, A.x, __fmaf_rd(n.y, A.y, __fmul_rd(n.z, A.z)));
+    float db = __fmaf_rd(n.x, B.x, __fmaf_rd(n.y, B.y, __fmul_rd(n.z, B.z)));
+    float dc = __fmaf_rd(n.x, C.x, __fmaf_rd(n.y, C.y, __fmul_rd(n.z, C.z)));
+    lo = fmaxf(__fsub_rd(fminf(da, fminf(db, dc)), __fmul_ru(6.f * kU, M)), 0.f);
+  }
+  o.lo = lo;
+  // a loose certificate means the classification was ill-conditioned: redo in FP64
+  if (__fsub_rd(nq, lo) > __fmul_ru(256.f * kU, M)) {
+    D3 p = {(double)P.h.x + (double)P.l.x, (double)P.h.y + (double)P.l.y, (double)P.h.z + (double)P.l.z};
+    D3 a = {a4.x, a4.y, a4.z}, b = {b4.x, b4.y, b4.z}, c = {c4.x, c4.y, c4.z};
+    D3 q = closest_on_triangle(p, a, b, c) - p;
+    double d = len(q);
+    // covers the double rounding of these few operations, done in absolute coordinates
+    double m = 1e-12 * ((double)M + d + fmax(fabs(p.x), fmax(fabs(p.y), fabs(p.z)))) + 1e-30;
+    double lo64 = 0.0;
+    if (d > 0.0) {
+      D3 n = (1.0 / d) * q;
+      lo64 = fmin(dot(n, a - p), fmin(dot(n, b - p), dot(n, c - p))) - m;
+    }
+    o.esc = true;
+    o.lo = fmaxf(o.lo, __double2float_rd(fmax(lo64, 0.0)));
+    float hi64 = __double2float_ru(d + m);
+    if (hi64 < o.hi) {
+      o.hi = hi64;
+      o.q = {(float)q.x, (float)q.y, (float)q.z};
+      // float rounding of q plus the double margin
+      o.qerr = __double2float_ru(3e-7 * (fabs(q.x) + fabs(q.y) + fabs(q.z)) + m);
+    }
+  }
+}
+
+// Lower bound of |p - box|^2 (downward rounding).
+__device__ inline float box_lo2(const FFP& P, float lx, float ly, float lz, float hx, float hy, float hz) {
+  float gx = fmaxf(fmaxf(__fsub_rd(__fsub_rd(lx, P.h.x), P.l.x), __fadd_rd(__fsub_rd(P.h.x, hx), P.l.x)), 0.f);
+  float gy = fmaxf(fmaxf(__fsub_rd(__fsub_rd(ly, P.h.y), P.l.y), __fadd_rd(__fsub_rd(P.h.y, hy), P.l.y)), 0.f);
+  float gz = fmaxf(fmaxf(__fsub_rd(__fsub_rd(lz, P.h.z), P.l.z), __fadd_rd(__fsub_rd(P.h.z, hz), P.l.z)), 0.f);
+  return __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
+}
+
+struct NearestM {
+  FFP P;
+  const float4* tri32;
+  float best_hi = INFINITY;
+  float dlo = INFINITY;
+  int best = -1;
+  F3 q = {0.f, 0.f, 0.f};
+  float qerr = 0.f;
+  unsigned long long evals = 0, esc = 0;
+  __device__ float radius2() const { return __fmul_ru(best_hi, best_hi); }
+  __device__ void test1(int j) {
+    const float4* t = tri32 + 3 * (size_t)j;
+    PtOut o;
+    pt_cert(P, __ldg(t), __ldg(t + 1), __ldg(t + 2), true, o);
+    ++evals;
+    esc += o.esc;
+    dlo = fminf(dlo, o.lo);
+    if (o.hi < best_hi) {
+      best_hi = o.hi;
+      best = j;
+      q = o.q;
+      qerr = o.qerr;
+    }
+  }
+  __device__ void range(int first, int count) {
+    for (int j = first; j < first + count; ++j) test1(j);
+  }
+};
+
+// Ordered depth-first traversal as in the FP64 path, with certified float box bounds.
+__device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c) {
+  int stack_node[kStack];
+  float stack_d[kStack];
+  int sp = 0;
+  int node = 0;
+  for (;;) {
+    const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
+    float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+    int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
+    float d0 = box_lo2(t.P, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
+    float d1 = box_lo2(t.P, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
+    c.boxes += 2;
+    if (ref.z > 0 && d0 <= t.radius2()) t.range(ref.x, ref.z);
+    if (ref.w > 0 && d1 <= t.radius2()) t.range(ref.y, ref.w);
+    float r2 = t.radius2();
+    bool g0 = ref.z == 0 && d0 <= r2, g1 = ref.w == 0 && d1 <= r2;
+    if (g0 && g1) {
+      int nn = ref.x, nf = ref.y;
+      float df = d1;
+      if (d1 < d0) {
+        nn = ref.y;
+        nf = ref.x;
+        df = d0;
+      }
+      if (sp < kStack) {
+        stack_node[sp] = nf;
+        stack_d[sp] = df;
+        ++sp;
+      } else {
+        c.err = 1;
+      }
+      node = nn;
+      continue;
+    }
+    if (g0) { node = ref.x; continue; }
+    if (g1) { node = ref.y; continue; }
+    bool found = false;
+    while (sp > 0) {
+      --sp;
+      if (stack_d[sp] <= t.radius2()) {
+        node = stack_node[sp];
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+}
+
+// ----------------------------------------------------------------------------- bounds
+
+struct VM {  // one vertex of T in the cascade
+  FFP p;
+  float dhi;
+  int I;
+  F3 q;  // closest point relative to p
+  float qerr;
+};
+
+// Certified edge vector p_j - p_i (components carry a relative error of about 2u).
+__device__ inline F3 edge(const VM& a, const VM& b) { return (b.p.h - a.p.h) + (b.p.l - a.p.l); }
+__device__ inline float len_hi(F3 e) { return __fmul_ru(norm_ru(e), 1.f + 4.f * kU); }
+__device__ inline float len_lo(F3 e) { return __fmul_rd(norm_rd(e), 1.f - 4.f * kU); }
+
+// u1, Eq. (u1), with edge lengths rounded up
+__device__ inline float ubm_u1(const VM t[3]) {
+  float u = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float e1 = len_hi(edge(t[i], t[(i + 1) % 3])), e2 = len_hi(edge(t[i], t[(i + 2) % 3]));
+    u = fminf(u, __fadd_ru(fmaxf(e1, e2), t[i].dhi));
+  }
+  return u;
+}
+
+// u2, Eq. (u2): g is half the longest edge when T is certainly obtuse (longest edge squared,
+// rounded down, above the sum of the other two squared, rounded up), else the circumradius
+// with the area rounded down.  Acute <=> s - r > 2R, so this is the paper's g wherever the
+// sign of the test is certain, and the circumradius (always a valid g) elsewhere.
+__device__ inline float ubm_u2(const VM t[3]) {
+  F3 e[3] = {edge(t[1], t[2]), edge(t[2], t[0]), edge(t[0], t[1])};
+  float hi[3], lo[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    hi[i] = len_hi(e[i]);
+    lo[i] = len_lo(e[i]);
+  }
+  int k = 0;
+  if (hi[1] > hi[k]) k = 1;
+  if (hi[2] > hi[k]) k = 2;
+  int i1 = (k + 1) % 3, i2 = (k + 2) % 3;
+  float g;
+  if (__fmul_rd(lo[k], lo[k]) > __fmaf_ru(hi[i1], hi[i1], __fmul_ru(hi[i2], hi[i2]))) {
+    g = __fmul_ru(0.5f, hi[k]);
+  } else {
+    F3 a = e[2], b = {-e[1].x, -e[1].y, -e[1].z};  // v2 - v1 and v3 - v1
+    F3 cr = {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+    float err = __fmul_ru(__fmul_ru(32.f * kU, amax3(a)), amax3(b));
+    float c2 = __fsub_rd(norm_rd(cr), err);  // lower bound of 2|T|
+    g = c2 > 0.f ? __fdiv_ru(__fmul_ru(__fmul_ru(hi[0], hi[1]), hi[2]), __fmul_rd(2.f, c2)) : INFINITY;
+  }
+  return __fadd_ru(g, fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi)));
+}
+
+__device__ inline float dist_hi(const BvhDev& B, int j, const FFP& x, float beta) {
+  const float4* t = B.tri32 + 3 * (size_t)j;
+  PtOut o;
+  pt_cert(x, __ldg(t), __ldg(t + 1), __ldg(t + 2), false, o);
+  return __fadd_ru(o.hi, beta);
+}
+
+// Point base + s * e (s in [0, 1]) as a float pair, with its representation error.
+__device__ inline FFP along(const VM& base, F3 e, float s, float& beta) {
+  FFP x;
+  x.h = base.p.h;
+  x.l = {fmaf(s, e.x, base.p.l.x), fmaf(s, e.y, base.p.l.y), fmaf(s, e.z, base.p.l.z)};
+  beta = __fmul_ru(8.f * kU, fmaxf(amax3(e), amax3(base.p.l)));
+  return x;
+}
+
+// u3 (Kang et al. 2018), Eqs. (Kang2018_case1) and (Kang2018_case2).
+__device__ inline float ubm_u3(const BvhDev& B, const VM t[3], unsigned long long& evals) {
+  int lone = -1;
+  if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
+    if (t[1].I == t[2].I) lone = 0;
+    else if (t[0].I == t[2].I) lone = 1;
+    else if (t[0].I == t[1].I) lone = 2;
+  }
+  int fs0, fs1, fo, go;
+  if (lone >= 0 && shared_edge(B, t[lone].I, t[(lone + 1) % 3].I, fs0, fs1, fo, go)) {
+    const VM& v1 = t[lone];
+    const VM& v2 = t[(lone + 1) % 3];
+    const VM& v3 = t[(lone + 2) % 3];
+    int S1 = v1.I, S2 = v2.I;
+    F3 e12 = edge(v1, v2), e13 = edge(v1, v3);
+    // split parameters: the bisecting plane of the two supporting half-planes (any value
+    // in [0, 1] gives a valid split; this choice only affects tightness)
+    float s2 = 0.5f, s3 = 0.5f;
+    const float4* T1 = B.tri32 + 3 * (size_t)S1;
+    const float4* T2 = B.tri32 + 3 * (size_t)S2;
+    float4 P0 = __ldg(T1 + fs0), P1 = __ldg(T1 + fs1), O1 = __ldg(T1 + fo), O2 = __ldg(T2 + go);
+    F3 p0 = {P0.x, P0.y, P0.z}, ed = F3{P1.x, P1.y, P1.z} - p0;
+    float el = sqrtf(dotf(ed, ed));
+    if (el > 0.f) {
+      F3 eh = {ed.x / el, ed.y / el, ed.z / el};
+      F3 a1 = F3{O1.x, O1.y, O1.z} - p0, a2 = F3{O2.x, O2.y, O2.z} - p0;
+      float k1 = dotf(a1, eh), k2 = dotf(a2, eh);
+      F3 w1 = {a1.x - k1 * eh.x, a1.y - k1 * eh.y, a1.z - k1 * eh.z};
+      F3 w2 = {a2.x - k2 * eh.x, a2.y - k2 * eh.y, a2.z - k2 * eh.z};
+      float n1 = sqrtf(dotf(w1, w1)), n2 = sqrtf(dotf(w2, w2));
+      if (n1 > 0.f && n2 > 0.f) {
+        F3 nb = {w1.x / n1 - w2.x / n2, w1.y / n1 - w2.y / n2, w1.z / n1 - w2.z / n2};
+        F3 r1 = (v1.p.h - p0) + v1.p.l;
+        float sv1 = dotf(nb, r1), sv2 = sv1 + dotf(nb, e12), sv3 = sv1 + dotf(nb, e13);
+        if (sv1 >= 0.f && sv2 <= 0.f && sv3 <= 0.f && sv1 - sv2 > 0.f && sv1 - sv3 > 0.f) {
+          s2 = fminf(fmaxf(sv1 / (sv1 - sv2), 0.f), 1.f);
+          s3 = fminf(fmaxf(sv1 / (sv1 - sv3), 0.f), 1.f);
+        }
+      }
+    }
+    float be1, be2;
+    FFP b1 = along(v1, e12, s2, be1), b2 = along(v1, e13, s3, be2);
+    evals += 4;
+    float hR = fmaxf(v1.dhi, fmaxf(dist_hi(B, S1, b1, be1), dist_hi(B, S1, b2, be2)));
+    float hQ = fmaxf(fmaxf(v3.I == S2 ? v3.dhi : dist_hi(B, S2, v3.p, 0.f), dist_hi(B, S2, b2, be2)),
+                     fmaxf(dist_hi(B, S2, b1, be1), v2.dhi));
+    return fmaxf(hR, hQ);
+  }
+  // case 2: quadrilaterals (v_i, m_i, b, m_{i-1}) against S_i, then min with h(T, S_i)
+  F3 e01 = edge(t[0], t[1]), e02 = edge(t[0], t[2]), e12 = edge(t[1], t[2]);
+  float bm[3];
+  FFP m[3];
+  m[0] = along(t[0], e01, 0.5f, bm[0]);
+  m[1] = along(t[1], e12, 0.5f, bm[1]);
+  m[2] = along(t[0], e02, 0.5f, bm[2]);  // m3 on v3v1
+  F3 sum = e01 + e02;
+  float bb;
+  FFP bc = along(t[0], sum, 1.f / 3.f, bb);
+  bb = __fmul_ru(16.f * kU, fmaxf(amax3(e01), fmaxf(amax3(e02), amax3(t[0].p.l))));
+  float ut = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    int S = t[i].I;
+    float h = fmaxf(fmaxf(t[i].dhi, dist_hi(B, S, m[i], bm[i])),
+                    fmaxf(dist_hi(B, S, bc, bb), dist_hi(B, S, m[(i + 2) % 3], bm[(i + 2) % 3])));
+    ut = fmaxf(ut, h);
+  }
+  float best = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float h = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) h = fmaxf(h, j == i ? t[j].dhi : dist_hi(B, t[i].I, t[j].p, 0.f));
+    best = fminf(best, h);
+  }
+  evals += 15;
+  return fminf(ut, best);
+}
+
+// u4, Eq. (bound_u4), in FP64 on the float-pair vertices and footpoints, plus the footpoint
+// error radii and a relative margin for the double rounding.
+__device__ inline float ubm_u4(const VM t[3], double slack) {
+  VI d[3];
+  float qe = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    D3 v = {(double)t[i].p.h.x + (double)t[i].p.l.x, (double)t[i].p.h.y + (double)t[i].p.l.y,
+            (double)t[i].p.h.z + (double)t[i].p.l.z};
+    d[i].v = v;
+    d[i].q = v + D3{(double)t[i].q.x, (double)t[i].q.y, (double)t[i].q.z};
+    d[i].d = 0.0;
+    d[i].I = t[i].I;
+    qe = fmaxf(qe, t[i].qerr);
+  }
+  double u = ub_u4(d);
+  return __fadd_ru(__double2float_ru(u + 2.0 * slack + 1e-12 * u), qe);
+}
+
+__device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], double l, const RunParams& rp, int& code,
+                                      Counters& c) {
+  float U;
+  if (t[0].I == t[1].I && t[1].I == t[2].I) {
+    code = 0;
+    U = fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi));
+  } else {
+    U = INFINITY;
+    code = 5;
+    for (int k = 0; k < rp.n_bounds; ++k) {
+      float u;
+      switch (rp.order[k]) {
+        case 1: u = ubm_u1(t); break;
+        case 2: u = ubm_u2(t); break;
+        case 3: u = ubm_u3(B, t, c.evals); break;
+        default: u = ubm_u4(t, rp.slack); break;
+      }
+      U = fminf(U, u);
+      if ((double)u < l) {
+        code = rp.order[k];
+        U = u;
+        break;
+      }
+    }
+  }
+  return __fadd_ru(U, __double2float_ru(rp.slack));
+}
+
+// ----------------------------------------------------------------------------- the policy
+
+struct PolicyM {
+  using Vtx = VtxM;
+  using Item = ItemM;
+  using UT = float;
+  static constexpr bool kFp64 = false;
+
+  // 2^-40 of the largest coordinate: covers the float-pair representation of subdivided
+  // vertices (2^-48 relative per level, at most 60 levels) and the double rounding of u4
+  static double slack(double amax) { return ldexp(amax, -40); }
+
+  __device__ static FFP pos(const Vtx& v) { return {{v.hx, v.hy, v.hz}, {v.lx, v.ly, v.lz}}; }
+
+  __device__ static void set_pos(Vtx& v, double x, double y, double z) {
+    v.hx = (float)x;
+    v.hy = (float)y;
+    v.hz = (float)z;
+    v.lx = (float)(x - (double)v.hx);
+    v.ly = (float)(y - (double)v.hy);
+    v.lz = (float)(z - (double)v.hz);
+  }
+
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c) {
+    NearestM t;
+    t.P = pos(v);
+    t.tri32 = B.tri32;
+    if (v.hint >= 0) t.test1(v.hint);
+    traverse_m(B, t, c);
+    c.leaf += t.evals;
+    c.escalations += t.esc;
+    v.tri = t.best;
+    v.dhi = __fadd_ru(t.best_hi, B.eta);
+    v.dlo = fmaxf(__fsub_rd(fminf(t.dlo, t.best_hi), B.eta), 0.f);
+    v.qx = t.q.x;
+    v.qy = t.q.y;
+    v.qz = t.q.z;
+    v.qerr = __fadd_ru(t.qerr, B.eta);
+  }
+  __device__ static double lower(const Vtx& v) { return v.dlo; }
+  __device__ static double out_dist(const Vtx& v) { return v.dhi; }
+  __device__ static double out_dlo(const Vtx& v) { return v.dlo; }
+  __device__ static D3 out_foot(const Vtx& v) {
+    return {(double)v.hx + (double)v.lx + (double)v.qx, (double)v.hy + (double)v.ly + (double)v.qy,
+            (double)v.hz + (double)v.lz + (double)v.qz};
+  }
+  __device__ static void midpoint(const Vtx& a, const Vtx& b, Vtx& m) {
+    double x = 0.5 * (((double)a.hx + (double)a.lx) + ((double)b.hx + (double)b.lx));
+    double y = 0.5 * (((double)a.hy + (double)a.ly) + ((double)b.hy + (double)b.ly));
+    double z = 0.5 * (((double)a.hz + (double)a.lz) + ((double)b.hz + (double)b.lz));
+    set_pos(m, x, y, z);
+    m.qx = m.qy = m.qz = 0.f;
+    m.qerr = m.dhi = m.dlo = 0.f;
+    m.tri = -2;
+    m.hint = a.tri;
+    m.pad0 = m.pad1 = 0.f;
+  }
+  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l,
+                                   const RunParams& rp, int& code, Counters& cnt) {
+    VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
+               {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
+               {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
+    return upper_bound_m(B, t, l, rp, code, cnt);
+  }
+};
+
+}  // namespace hd

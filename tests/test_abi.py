@@ -38,8 +38,9 @@ def test_struct_layouts_match_header(hd):
     # sizes of the ABI structs as laid out by a C compiler for this header
     assert C.sizeof(hd.HdMesh) == 40
     assert C.sizeof(hd.HdOptions) == 56
-    assert C.sizeof(hd.HdStats) == 8 * 17
-    assert C.sizeof(hd.HdResult) == 24 + 8 * 17
+    assert C.sizeof(hd.HdStats) == 8 * 18
+    assert C.sizeof(hd.HdResult) == 24 + 8 * 18
+    assert C.sizeof(hd.HdTrace) == 128
 
 
 def test_options_default_and_status_strings(hd):

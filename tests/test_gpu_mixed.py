@@ -1,0 +1,162 @@
+"""The certified FP32 path (HD_MIXED) against the FP64 oracle, through the C ABI.
+
+Certification: for every query the returned interval [dist_lo, dist] must contain the
+oracle's distance (which is exact to ~1e-16 relative; 1e-12 relative is allowed for it),
+and every MIXED bracket [l, u] must contain h (closed forms) or intersect the oracle's.
+Tightness: the intervals must be narrow (the bound is a few float roundings of the local
+magnitude, far below the workloads' tolerances).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
+ORACLE_REL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def hd():
+    from paper_2406_10357_gb300 import build
+
+    build.build()
+    import paper_2406_10357_gb300 as hd
+
+    return hd
+
+
+def _dA(V, F):
+    R = np.asarray(V, float)[np.unique(np.asarray(F).ravel())]
+    return float(np.linalg.norm(R.max(0) - R.min(0)))
+
+
+def _check_certified(hd, orc, VB, FB, P, tight_abs):
+    bvh = hd.hd_build_B(VB, FB)
+    Pt = torch.from_numpy(np.ascontiguousarray(P)).cuda()
+    hi, idx, foot, lo = (x.cpu().numpy() for x in hd.hd_nearest(bvh, Pt, hd.HD_MIXED))
+    do, _, _ = orc.nearest(np.asarray(P, float), np.asarray(VB, float), FB)
+    slack = ORACLE_REL * np.maximum(1.0, do)
+    assert np.all(lo <= do + slack), np.max(lo - do)
+    assert np.all(hi >= do - slack), np.max(do - hi)
+    assert np.all(idx >= 0)
+    gap = hi - lo
+    assert np.max(gap) <= tight_abs, (np.max(gap), np.argmax(gap))
+    # the returned triangle realises the upper bound
+    VBd = np.asarray(VB, float)
+    for i in np.random.default_rng(1).choice(len(P), size=min(40, len(P)), replace=False):
+        d_idx, _ = orc.point_triangle(np.asarray(P[i], float), *VBd[FB[idx[i]]])
+        assert d_idx <= hi[i] + slack[i]
+    return gap
+
+
+@pytest.mark.parametrize("k,scale", [(1, 1.0), (2, 0.05), (3, 0.02), (5, 0.01)])
+def test_nearest_mixed_is_certified(hd, orc, k, scale):
+    p = mg.workload(k, scale)
+    rng = np.random.default_rng(10 + k)
+    V = np.asarray(p.VA, float)
+    P = np.concatenate([V[rng.choice(len(V), size=min(3000, len(V)), replace=False)],
+                        V.mean(0) + rng.normal(size=(500, 3)) * V.std(0) * 1.5]).astype(np.float32)
+    _check_certified(hd, orc, p.VB, p.FB, P, tight_abs=1e-6)
+
+
+def test_nearest_mixed_full_size_workload2_sampled(hd, orc):
+    p = mg.workload(2)
+    rng = np.random.default_rng(21)
+    P = p.VA[rng.choice(len(p.VA), size=3000, replace=False)]
+    gap = _check_certified(hd, orc, p.VB, p.FB, P, tight_abs=1e-6)
+    assert np.median(gap) < 1e-7
+
+
+@pytest.mark.parametrize("aspect", [1e2, 1e4, 1e6])
+def test_nearest_mixed_slivers_and_degenerate(hd, orc, aspect):
+    """Slivers, zero-area and repeated-vertex triangles in B; points near their edges."""
+    rng = np.random.default_rng(int(aspect))
+    n = 400
+    a = rng.normal(size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    side = np.cross(d, rng.normal(size=(n, 3)))
+    side /= np.linalg.norm(side, axis=1, keepdims=True)
+    L = np.linalg.norm(d, axis=1, keepdims=True)
+    c = a + 0.37 * d + side * L / aspect
+    T = np.stack([a, a + d, c], 1)
+    T[::17, 2] = T[::17, 0]          # repeated vertex
+    T[::23, 2] = 0.5 * (T[::23, 0] + T[::23, 1])  # collinear
+    VB = T.reshape(-1, 3).astype(np.float32)
+    FB = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    P = np.concatenate([
+        (VB[0::3] + 0.5 * (VB[1::3] - VB[0::3]) + rng.normal(size=(n, 3)) * 1e-3),
+        (VB[2::3] + rng.normal(size=(n, 3)) * 1e-4),
+        rng.normal(size=(n, 3)) * 2,
+    ]).astype(np.float32)
+    gap = _check_certified(hd, orc, VB, FB, P, tight_abs=1e-5)
+    assert np.median(gap) < 1e-6
+
+
+def test_nearest_mixed_double_input_B(hd, orc):
+    """B given in float64 (not representable in float): the float copy's error is covered."""
+    p = mg.workload(1)
+    VB = np.asarray(p.VB, float) * (1 + 1e-9) + 1e-9
+    rng = np.random.default_rng(3)
+    P = rng.normal(size=(2000, 3)) * 1.1
+    _check_certified(hd, orc, VB, p.FB, P, tight_abs=2e-6)
+
+
+def _load_golden():
+    with open(GOLDEN) as f:
+        return json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _load_golden(), ids=lambda c: c["name"])
+def test_closed_form_pairs_mixed(hd, case):
+    VA, FA = np.array(case["VA"], float), np.array(case["FA"], np.int32)
+    VB, FB = np.array(case["VB"], float), np.array(case["FB"], np.int32)
+    bvh = hd.hd_build_B(VB, FB)
+    r = hd.hd_hausdorff(bvh, VA, FA, case["tol"], hd.hd_options_default(precision=hd.HD_MIXED))
+    assert r["status"] == hd.HD_OK, r
+    assert r["lower"] <= case["h"] and case["h"] <= r["upper"]
+    assert r["upper"] - r["lower"] <= case["tol"]
+
+
+@pytest.mark.parametrize("k,scale", [(1, 1.0), (2, 0.02), (2, 0.1), (3, 0.01), (5, 0.005)])
+def test_bracket_mixed_vs_oracle(hd, orc, k, scale):
+    p = mg.workload(k, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode, precision=hd.HD_MIXED))
+    ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    eps = p.tol * (_dA(p.VA, p.FA) if p.tol_mode else 1.0)
+    assert r["status"] == hd.HD_OK, r
+    assert r["upper"] - r["lower"] <= eps
+    assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + ORACLE_REL * ro["upper"]
+    # MIXED and FP64 GPU brackets intersect too
+    r64 = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode))
+    assert max(r["lower"], r64["lower"]) <= min(r["upper"], r64["upper"]) + ORACLE_REL * r64["upper"]
+
+
+def test_full_size_workload2_mixed_properties(hd, orc):
+    p = mg.workload(2)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode, precision=hd.HD_MIXED))
+    eps = p.tol * _dA(p.VA, p.FA)
+    assert r["status"] == hd.HD_OK and r["upper"] - r["lower"] <= eps
+    rng = np.random.default_rng(19)
+    P = np.asarray(p.VA, float)[rng.choice(len(p.VA), size=3000, replace=False)]
+    do, _, _ = orc.nearest(P, p.VB, p.FB)
+    assert do.max() <= r["upper"]
+    r64 = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode))
+    assert max(r["lower"], r64["lower"]) <= min(r["upper"], r64["upper"])
+
+
+def test_identical_meshes_mixed(hd):
+    V, F = mg.icosphere(2)
+    bvh = hd.hd_build_B(V, F)
+    r = hd.hd_hausdorff(bvh, V, F, 1e-3, hd.hd_options_default(precision=hd.HD_MIXED))
+    assert r["status"] == hd.HD_OK and 0 <= r["lower"] <= 1e-6 and r["upper"] <= 1e-3 + 1e-6
