@@ -109,7 +109,8 @@ void hd_options_default(hd_options* opt);
  * distances D, nearest triangles I and closest points C of points of A).  GPU build:
  * Morton codes of the triangle centroids, radix sort, binary radix tree (Karras 2012),
  * bottom-up boxes rounded outward, leaves of up to opt->leaf_size triangles.
- * On HD_OK *out owns device memory until hd_free_B(*out).  opt may be NULL. */
+ * B may have at most 2^27 - 1 triangles.  On HD_OK *out owns device memory until
+ * hd_free_B(*out).  opt may be NULL. */
 int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** out);
 
 /* Release everything hd_build_B allocated.  NULL is allowed. */

@@ -259,6 +259,7 @@ int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** o
   *out = nullptr;
   Opts o;
   if (resolve_options(opt, &o) != HD_OK || check_mesh(B) != HD_OK) return HD_ERR_INVALID;
+  if (B->nF >= (int64_t)1 << 27) return HD_ERR_INVALID;  // traversal stack entries pack 27-bit indices
   keep_pool_memory();
   return build_bvh(B, o, (cudaStream_t)stream, out);
 }

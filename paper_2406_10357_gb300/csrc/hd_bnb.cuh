@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "hd_fp64.cuh"
 #include "hd_internal.cuh"
 
 namespace hd {
@@ -119,14 +120,16 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
     bool active = t < count;
     if (__all_sync(0xffffffffu, !active)) break;
-    if (active) {
-      typename P::Vtx v = pool[beg + t];
-      if (v.tri != -1) {
-        P::query(B, v, c);
-        pool[beg + t] = v;
-        lmax = fmax(lmax, P::lower(v) - slack);
-        ++nq;
-      }
+    // every lane of the warp enters the query (the MIXED traversal votes across the warp);
+    // lanes without a vertex to query take part as already finished
+    typename P::Vtx v;
+    if (active) v = pool[beg + t];
+    bool q = active && v.tri != -1;
+    P::query(B, v, c, q);
+    if (q) {
+      pool[beg + t] = v;
+      lmax = fmax(lmax, P::lower(v) - slack);
+      ++nq;
     }
   }
   lmax = warp_max(lmax);
@@ -186,7 +189,8 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
 // rest (three midpoints each into the pool at mbase), carry the others over.
 template <class P>
 __global__ void k_select(const typename P::Item* front, int n_front, RunState* st, RunParams rp, int K,
-                         int4* split_par, typename P::Vtx* pool, int mbase, typename P::Item* next, int next_cap) {
+                         int4* split_par, typename P::Vtx* pool, int mbase, typename P::Item* next, int next_cap,
+                         typename P::Item* promo, int promo_cap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_front) return;
   double l = load_l(st);
@@ -201,10 +205,20 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
     atomicAdd(&st->retired, 1ull);
     return;
   }
+  typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
+  if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
+    int j = atomicAdd(&st->n_promote, 1);
+    if (j < promo_cap) {
+      promo[j] = it;
+      atomic_max_nonneg(&st->upro_bits, U);
+    } else {
+      atomicExch(&st->overflow, 1);
+    }
+    return;
+  }
   int s = atomicAdd(&st->n_split, 1);
   if (s < K) {
     split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], 0);
-    typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
     P::midpoint(a, b, m);
     pool[mbase + 3 * s] = m;
     P::midpoint(b, c, m);
@@ -265,11 +279,10 @@ __global__ void k_query_points(BvhDev B, typename P::Vtx* tmp, int64_t n, RunSta
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
     bool active = t < n;
     if (__all_sync(0xffffffffu, !active)) break;
-    if (active) {
-      typename P::Vtx v = tmp[t];
-      P::query(B, v, c);
-      tmp[t] = v;
-    }
+    typename P::Vtx v;
+    if (active) v = tmp[t];
+    P::query(B, v, c, active);  // whole warp enters (see k_query)
+    if (active) tmp[t] = v;
   }
   flush_counters(st, c);
 }
@@ -300,10 +313,190 @@ inline double bits_to_double(unsigned long long b) {
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
 int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax);
 
+// Buffers of one policy's frontier loop.
 template <class P>
-int run_bnb(const RunIO& io) {
+struct Rounds {
+  typename P::Vtx* pool = nullptr;
+  typename P::Item* front[2] = {nullptr, nullptr};
+  typename P::Item* promo = nullptr;  // items handed to the FP64 phase (MIXED only)
+  int4* split_par = nullptr;
+  int64_t pool_cap = 0, front_cap = 0, chunk = 0, promo_cap = 0;
+  int64_t n_pool = 0, n_front = 0;
+  int cur = 1;  // front[cur] holds the current frontier
+};
+
+struct Totals {
+  int64_t rounds = 0, splits = 0, peak = 0;
+  double u_run = INFINITY;
+};
+
+template <class P>
+int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_front, bool promo, cudaStream_t s) {
   using Vtx = typename P::Vtx;
   using Item = typename P::Item;
+  int64_t budget = o.max_frontier_bytes > 0 ? o.max_frontier_bytes : (int64_t)2 << 30;
+  R.pool_cap = std::min<int64_t>(std::max<int64_t>(min_pool + 3, (int64_t)(0.6 * budget) / (int64_t)sizeof(Vtx)),
+                                 INT32_MAX / 2);
+  R.front_cap = std::min<int64_t>(
+      std::max<int64_t>(min_front + 4, (int64_t)((promo ? 0.1 : 0.15) * budget) / (int64_t)sizeof(Item)), INT32_MAX / 4);
+  R.chunk = o.frontier_chunk > 0 ? o.frontier_chunk : std::max<int64_t>(R.front_cap / 4, 1024);
+  R.chunk = std::min<int64_t>(R.chunk, R.front_cap);
+  R.promo_cap = promo ? R.front_cap : 0;
+  HD_TRY(cudaMallocAsync((void**)&R.pool, sizeof(Vtx) * R.pool_cap, s));
+  HD_TRY(cudaMallocAsync((void**)&R.front[0], sizeof(Item) * R.front_cap, s));
+  HD_TRY(cudaMallocAsync((void**)&R.front[1], sizeof(Item) * R.front_cap, s));
+  HD_TRY(cudaMallocAsync((void**)&R.split_par, sizeof(int4) * R.chunk, s));
+  if (promo) HD_TRY(cudaMallocAsync((void**)&R.promo, sizeof(Item) * R.promo_cap, s));
+  return HD_OK;
+}
+
+template <class P>
+void free_rounds(Rounds<P>& R, cudaStream_t s) {
+  cudaFreeAsync(R.pool, s);
+  cudaFreeAsync(R.front[0], s);
+  cudaFreeAsync(R.front[1], s);
+  cudaFreeAsync(R.split_par, s);
+  if (R.promo) cudaFreeAsync(R.promo, s);
+}
+
+inline double round_upper(const RunState* h, int64_t n_front) {
+  double u = std::max(bits_to_double(h->l_bits), bits_to_double(h->uret_bits));
+  if (n_front) u = std::max(u, bits_to_double(h->umax_bits));
+  if (h->n_promote) u = std::max(u, bits_to_double(h->upro_bits));
+  return u;
+}
+
+// Frontier rounds of policy P until the frontier is empty, the capacity or round limit is
+// reached, or an error is flagged.  *status receives HD_OK/CAPACITY/TIMEOUT/NUMERIC.
+template <class P>
+int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, RunState* hst, const RunParams& rp, Totals& T,
+                int* status) {
+  const Opts& o = *io.o;
+  cudaStream_t s = io.s;
+  BvhDev B = bvh_dev(io.B);
+  const int bs = o.block_size;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned max_grid = (unsigned)sms * 16;
+  const double face_cap = o.max_face_factor * (double)io.nFA;
+  while (*status == HD_OK && R.n_front > 0) {
+    if (T.rounds >= o.max_rounds) {
+      *status = HD_ERR_TIMEOUT;
+      break;
+    }
+    int64_t K = std::min<int64_t>(R.chunk, (R.pool_cap - R.n_pool) / 3);
+    K = std::min<int64_t>(K, (R.front_cap - R.n_front) / 3);
+    double cap_left = std::floor((face_cap - (double)io.nFA) / 4.0) - (double)T.splits;
+    K = std::min<int64_t>(K, (int64_t)std::max(0.0, std::min(cap_left, 9.0e18)));
+    if (K <= 0) {
+      *status = HD_ERR_CAPACITY;
+      break;
+    }
+    {
+      TraceScope tr(HD_K_SELECT, s);
+      k_round_reset<<<1, 1, 0, s>>>(st, (int)R.n_front);
+      k_select<P><<<blocks_for(R.n_front, 256), 256, 0, s>>>(R.front[R.cur], (int)R.n_front, st, rp, (int)K,
+                                                             R.split_par, R.pool, (int)R.n_pool, R.front[R.cur ^ 1],
+                                                             (int)R.front_cap, R.promo, (int)R.promo_cap);
+    }
+    {
+      TraceScope tr(HD_K_QUERY, s);
+      unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
+      k_query<P><<<gq, bs, 0, s>>>(B, R.pool, (int)R.n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack);
+    }
+    {
+      TraceScope tr(HD_K_BOUND, s);
+      unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
+      k_bound_children<P><<<gb, bs, 0, s>>>(B, R.pool, R.split_par, (int)K, (int)R.n_pool, st, rp,
+                                            R.front[R.cur ^ 1], (int)R.front_cap);
+    }
+    HD_TRY_LAUNCH();
+    HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaStreamSynchronize(s));
+    int64_t S = std::min<int64_t>(hst->n_split, K);
+    ++T.rounds;
+    T.splits += S;
+    R.n_pool += 3 * S;
+    R.cur ^= 1;
+    R.n_front = hst->n_next;
+    T.peak = std::max(T.peak, R.n_front);
+    T.u_run = std::min(T.u_run, round_upper(hst, R.n_front));
+    if (hst->overflow) *status = HD_ERR_CAPACITY;
+    if (hst->err) *status = HD_ERR_NUMERIC;
+  }
+  return HD_OK;
+}
+
+// Promoted MIXED items: their vertices at exact positions in an FP64 pool, and index triples.
+template <class P>
+__global__ void k_promote_init(const typename P::Item* promo, int n, const typename P::Vtx* pool, VtxD* poolD,
+                               int32_t* tris) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  typename P::Item it = promo[i];
+  for (int k = 0; k < 3; ++k) {
+    typename P::Vtx v = pool[it.v[k]];
+    D3 x = P::exact_pos(v);
+    VtxD d;
+    memset(&d, 0, sizeof d);
+    d.x = x.x;
+    d.y = x.y;
+    d.z = x.z;
+    d.tri = -2;
+    d.hint = v.tri;
+    poolD[3 * i + k] = d;
+    tris[3 * i + k] = 3 * i + k;
+  }
+}
+
+// Final certification (a7): sub-triangles whose gap the FP32 error radius cannot resolve are
+// re-queried and bounded in FP64 (with the same slack margin) and refined to the end there.
+template <class P>
+int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, RunState* hst, const RunParams& rp,
+                   Totals& T, int* status) {
+  cudaStream_t s = io.s;
+  const Opts& o = *io.o;
+  BvhDev B = bvh_dev(io.B);
+  Rounds<PolicyD> D;
+  int rc = alloc_rounds<PolicyD>(D, o, 3 * n_pro, n_pro, false, s);
+  if (rc != HD_OK) return rc;
+  int32_t* tris = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&tris, sizeof(int32_t) * 3 * n_pro, s));
+  {
+    TraceScope tr(HD_K_PREP, s);
+    k_promote_init<P><<<blocks_for(n_pro, 256), 256, 0, s>>>(RM.promo, (int)n_pro, RM.pool, D.pool, tris);
+    k_round_reset<<<1, 1, 0, s>>>(st, 0);
+  }
+  HD_TRY_LAUNCH();
+  HD_TRY(cudaMemsetAsync(&st->upro_bits, 0, sizeof(unsigned long long), s));
+  HD_TRY(cudaMemsetAsync(&st->n_promote, 0, sizeof(int), s));
+  {
+    TraceScope tr(HD_K_QUERY, s);
+    k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, 0, nullptr, 1,
+                                                                                 (int)(3 * n_pro), st, rp.slack);
+  }
+  {
+    TraceScope tr(HD_K_BOUND, s);
+    k_bound_faces<PolicyD><<<blocks_for(n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, tris, n_pro, st, rp,
+                                                                                   D.front[1], (int)D.front_cap);
+  }
+  HD_TRY_LAUNCH();
+  HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+  HD_TRY(cudaStreamSynchronize(s));
+  D.n_pool = 3 * n_pro;
+  D.n_front = hst->n_next;
+  D.cur = 1;
+  T.u_run = std::min(T.u_run, round_upper(hst, D.n_front));
+  if (hst->overflow) *status = HD_ERR_CAPACITY;
+  rc = loop_rounds<PolicyD>(io, D, st, hst, rp, T, status);
+  cudaFreeAsync(tris, s);
+  free_rounds(D, s);
+  return rc;
+}
+
+template <class P>
+int run_bnb(const RunIO& io) {
   const Opts& o = *io.o;
   cudaStream_t s = io.s;
   hd_result& res = *io.out;
@@ -322,22 +515,10 @@ int run_bnb(const RunIO& io) {
   res.stats.dA = dA;
   res.stats.eps_abs = eps;
 
-  // memory: vertex pool, two frontier buffers, split list
-  int64_t budget = o.max_frontier_bytes > 0 ? o.max_frontier_bytes : (int64_t)2 << 30;
-  int64_t pool_cap = std::max<int64_t>(io.nVA + 3, (int64_t)(0.6 * budget) / (int64_t)sizeof(Vtx));
-  int64_t front_cap = std::max<int64_t>(io.nFA + 4, (int64_t)(0.15 * budget) / (int64_t)sizeof(Item));
-  pool_cap = std::min<int64_t>(pool_cap, INT32_MAX / 2);
-  front_cap = std::min<int64_t>(front_cap, INT32_MAX / 4);
-  int64_t chunk = o.frontier_chunk > 0 ? o.frontier_chunk : std::max<int64_t>(front_cap / 4, 1024);
-  chunk = std::min<int64_t>(chunk, front_cap);
-  Vtx* pool = nullptr;
-  Item* front[2] = {nullptr, nullptr};
-  int4* split_par = nullptr;
+  Rounds<P> R;
+  rc = alloc_rounds<P>(R, o, io.nVA, io.nFA, !P::kFp64, s);
+  if (rc != HD_OK) return rc;
   RunState* st = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&pool, sizeof(Vtx) * pool_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&front[0], sizeof(Item) * front_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&front[1], sizeof(Item) * front_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&split_par, sizeof(int4) * chunk, s));
   HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
   static thread_local RunState* hst = nullptr;  // pinned read-back buffer, kept for the thread's lifetime
@@ -350,119 +531,72 @@ int run_bnb(const RunIO& io) {
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   const int bs = o.block_size;
-  int dev_sms = 152;
-  {
-    int dev;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const unsigned max_grid = (unsigned)dev_sms * 16;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const unsigned max_grid = (unsigned)sms * 16;
 
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
   {
     TraceScope tr(HD_K_PREP, s);
     if (io.vtype == HD_F64)
-      k_init_pool<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, pool);
+      k_init_pool<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, R.pool);
     else
-      k_init_pool<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, pool);
+      k_init_pool<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, R.pool);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, pool, 0, nullptr, 1, (int)io.nVA, st,
+    k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
                                                                        rp.slack);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_BOUND, s);
-    k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, pool, io.FA, io.nFA, st, rp, front[1], (int)front_cap);
+    k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
+                                                           (int)R.front_cap);
   }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
   HD_TRY(cudaStreamSynchronize(s));
 
-  int cur = 1;
-  int64_t n_front = hst->n_next, n_pool = io.nVA, splits = 0, rounds = 0, peak = n_front;
+  Totals T;
+  R.cur = 1;
+  R.n_pool = io.nVA;
+  R.n_front = hst->n_next;
+  T.peak = R.n_front;
+  T.u_run = round_upper(hst, R.n_front);
+  int status = hst->overflow ? HD_ERR_CAPACITY : HD_OK;
+  rc = loop_rounds<P>(io, R, st, hst, rp, T, &status);
+  int64_t n_pro = hst->n_promote;
+  if (rc == HD_OK && status == HD_OK && n_pro > 0)
+    rc = finish_in_fp64<P>(io, R, std::min<int64_t>(n_pro, R.promo_cap), st, hst, rp, T, &status);
+  if (rc != HD_OK) return rc;
+
   double l = bits_to_double(hst->l_bits);
-  double u_run = std::max(l, std::max(bits_to_double(hst->uret_bits), n_front ? bits_to_double(hst->umax_bits) : 0.0));
-  const double face_cap = o.max_face_factor * (double)io.nFA;
-  int status = HD_OK;
-  if (hst->overflow) status = HD_ERR_CAPACITY;
-
-  while (status == HD_OK && n_front > 0) {
-    if (rounds >= o.max_rounds) {
-      status = HD_ERR_TIMEOUT;
-      break;
-    }
-    int64_t K = std::min<int64_t>(chunk, (pool_cap - n_pool) / 3);
-    K = std::min<int64_t>(K, (front_cap - n_front) / 3);
-    double cap_left = std::floor((face_cap - (double)io.nFA) / 4.0) - (double)splits;
-    K = std::min<int64_t>(K, (int64_t)std::max(0.0, std::min(cap_left, 9.0e18)));
-    if (K <= 0) {
-      status = HD_ERR_CAPACITY;
-      break;
-    }
-    {
-      TraceScope tr(HD_K_SELECT, s);
-      k_round_reset<<<1, 1, 0, s>>>(st, (int)n_front);
-      k_select<P><<<blocks_for(n_front, 256), 256, 0, s>>>(front[cur], (int)n_front, st, rp, (int)K, split_par,
-                                                           pool, (int)n_pool, front[cur ^ 1], (int)front_cap);
-    }
-    {
-      TraceScope tr(HD_K_QUERY, s);
-      unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
-      k_query<P><<<gq, bs, 0, s>>>(B, pool, (int)n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack);
-    }
-    {
-      TraceScope tr(HD_K_BOUND, s);
-      unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
-      k_bound_children<P><<<gb, bs, 0, s>>>(B, pool, split_par, (int)K, (int)n_pool, st, rp, front[cur ^ 1],
-                                            (int)front_cap);
-    }
-    HD_TRY_LAUNCH();
-    HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
-    HD_TRY(cudaStreamSynchronize(s));
-    int64_t S = std::min<int64_t>(hst->n_split, K);
-    ++rounds;
-    splits += S;
-    n_pool += 3 * S;
-    cur ^= 1;
-    n_front = hst->n_next;
-    peak = std::max(peak, n_front);
-    l = bits_to_double(hst->l_bits);
-    double u_round = std::max(l, std::max(bits_to_double(hst->uret_bits), n_front ? bits_to_double(hst->umax_bits) : 0.0));
-    u_run = std::min(u_run, u_round);
-    if (hst->overflow) status = HD_ERR_CAPACITY;
-    if (hst->err) status = HD_ERR_NUMERIC;
-  }
-
-  l = bits_to_double(hst->l_bits);
   double uret = bits_to_double(hst->uret_bits);
   if (status == HD_OK) {
     // frontier empty: everything was discarded or retired
-    u_run = std::min(u_run, std::max(l, uret));
-    if (uret < l && hst->retired == 0 && P::kFp64) status = HD_ERR_NUMERIC;
+    T.u_run = std::min(T.u_run, std::max(l, uret));
+    if (P::kFp64 && uret < l) status = HD_ERR_NUMERIC;
   }
   res.lower = l;
-  res.upper = std::max(l, u_run);
+  res.upper = std::max(l, T.u_run);
   res.status = status;
   hd_stats& S = res.stats;
-  S.rounds = rounds;
-  S.splits = splits;
+  S.rounds = T.rounds;
+  S.splits = T.splits;
   S.queries = (int64_t)hst->queries;
   S.pointtri_evals = (int64_t)hst->evals;
   S.leaf_tests = (int64_t)hst->leaf_tests;
   S.box_tests = (int64_t)hst->box_tests;
   for (int k = 0; k < 6; ++k) S.discards[k] = (int64_t)hst->discards[k];
   S.retired = (int64_t)hst->retired;
-  S.fp64_escalations = (int64_t)hst->escalations;
-  S.peak_frontier = peak;
-  S.pool_vertices = n_pool;
+  S.fp64_escalations = (int64_t)hst->escalations + n_pro;
+  S.peak_frontier = T.peak;
+  S.pool_vertices = R.n_pool;
 
-  cudaFreeAsync(pool, s);
-  cudaFreeAsync(front[0], s);
-  cudaFreeAsync(front[1], s);
-  cudaFreeAsync(split_par, s);
+  free_rounds(R, s);
   cudaFreeAsync(st, s);
   cudaFreeAsync(ref, s);
   return HD_OK;

@@ -296,7 +296,8 @@ struct PolicyD {
   using UT = double;
   static constexpr bool kFp64 = true;
 
-  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c) {
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active) {
+    if (!active) return;  // no warp-collective operations below
     NearestD t;
     t.p = {v.x, v.y, v.z};
     t.tri64 = B.tri64;
@@ -314,6 +315,8 @@ struct PolicyD {
   __device__ static double out_dlo(const Vtx& v) { return v.d; }
   __device__ static D3 out_foot(const Vtx& v) { return {v.qx, v.qy, v.qz}; }
   static double slack(double) { return 0.0; }
+  __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
+  __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {
     v.x = x;
     v.y = y;
@@ -333,7 +336,10 @@ struct PolicyD {
     VI t[3] = {{{a.x, a.y, a.z}, a.d, a.tri, {a.qx, a.qy, a.qz}},
                {{b.x, b.y, b.z}, b.d, b.tri, {b.qx, b.qy, b.qz}},
                {{c.x, c.y, c.z}, c.d, c.tri, {c.qx, c.qy, c.qz}}};
-    return upper_bound_d(B, t, l, rp.order, rp.n_bounds, code, cnt.evals);
+    // slack is 0 in a pure FP64 run; in the certification phase of a MIXED run it is the
+    // margin that covers the double rounding
+    double U = upper_bound_d(B, t, l - rp.slack, rp.order, rp.n_bounds, code, cnt.evals);
+    return U + rp.slack;
   }
 };
 

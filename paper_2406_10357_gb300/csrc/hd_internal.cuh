@@ -100,6 +100,8 @@ struct RunState {
   int n_pool;                    // vertices in the pool
   int overflow;                  // next frontier or split list ran out of room
   int err;                       // traversal stack overflow and similar
+  int n_promote;                 // MIXED items handed to the FP64 phase
+  unsigned long long upro_bits;  // max U of those items (double bits)
   unsigned long long evals, box_tests, queries, retired, escalations, leaf_tests;
   unsigned long long discards[6];
 };
@@ -167,8 +169,22 @@ __device__ inline D3 closest_on_segment(D3 p, D3 a, D3 b) {
   return a + t * e;
 }
 
+__device__ inline D3 closest_on_edges(D3 p, D3 a, D3 b, D3 c) {
+  D3 q0 = closest_on_segment(p, a, b), q1 = closest_on_segment(p, b, c), q2 = closest_on_segment(p, c, a);
+  double e0 = dot(p - q0, p - q0), e1 = dot(p - q1, p - q1), e2 = dot(p - q2, p - q2);
+  D3 q = q0;
+  if (e1 < e0) { q = q1; e0 = e1; }
+  if (e2 < e0) q = q2;
+  return q;
+}
+
 __device__ inline D3 closest_on_triangle(D3 p, D3 a, D3 b, D3 c) {
   D3 ab = b - a, ac = c - a, ap = p - a;
+  // Degenerate (coincident or collinear vertices) and extreme slivers first: the region tests
+  // below assume a proper triangle (with a zero-length edge the edge test can fire spuriously),
+  // and such a triangle is, to rounding, its three edges.
+  double aa = dot(ab, ab), cc = dot(ac, ac), bc = dot(ab, ac);
+  if (!(aa * cc - bc * bc > 1e-10 * aa * cc)) return closest_on_edges(p, a, b, c);
   double d1 = dot(ab, ap), d2 = dot(ac, ap);
   if (d1 <= 0.0 && d2 <= 0.0) return a;
   D3 bp = p - b;
@@ -192,17 +208,20 @@ __device__ inline D3 closest_on_triangle(D3 p, D3 a, D3 b, D3 c) {
     double den = (d4 - d3v) + (d5 - d6);
     return b + (den > 0.0 ? (d4 - d3v) / den : 0.0) * (c - b);
   }
+  // face region; den = |ab x ac|^2 (Lagrange), so den / (|ab|^2 |ac|^2) = sin^2 of the angle at a
   double den = va + vb + vc;
-  if (!(den > 0.0)) {  // zero-area triangle: nearest of the three edges
-    D3 q0 = closest_on_segment(p, a, b), q1 = closest_on_segment(p, b, c), q2 = closest_on_segment(p, c, a);
-    double e0 = dot(p - q0, p - q0), e1 = dot(p - q1, p - q1), e2 = dot(p - q2, p - q2);
-    D3 q = q0;
-    if (e1 < e0) { q = q1; e0 = e1; }
-    if (e2 < e0) q = q2;
-    return q;
+  D3 q = a;
+  double e = INFINITY;
+  if (den > 0.0) {
+    double v = fmin(fmax(vb / den, 0.0), 1.0);
+    double w = fmin(fmax(vc / den, 0.0), 1.0 - v);
+    q = a + v * ab + w * ac;  // a point of the triangle even when the weights were rounded badly
+    if (den > 1e-10 * dot(ab, ab) * dot(ac, ac)) return q;
+    e = dot(p - q, p - q);
   }
-  double v = vb / den, w = vc / den;
-  return a + v * ab + w * ac;
+  // ill-conditioned face weights: compare with the three edges (all candidates are on the triangle)
+  D3 qe = closest_on_edges(p, a, b, c);
+  return dot(p - qe, p - qe) < e ? qe : q;
 }
 
 __device__ inline void load_tri64(const double* tri64, int i, D3& a, D3& b, D3& c) {

@@ -99,10 +99,13 @@ __global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned*
 
 // ---------------------------------------------------------------- 3: stable LSD radix sort
 
-constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32, RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // 4096 keys per block; warp w owns 512 consecutive keys
+// A block sorts a tile of RS_THREADS * ROUNDS keys; warp w owns ROUNDS * 32 consecutive keys.
+// Small inputs use 4 rounds (1024-key tiles) so that more blocks share the work.
+constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32;
 
+template <int ROUNDS>
 __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks) {
+  constexpr int RS_TILE = RS_THREADS * ROUNDS;
   __shared__ unsigned cnt[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
   __syncthreads();
@@ -138,17 +141,19 @@ __global__ void k_rs_scan(unsigned* a, int64_t n) {
   }
 }
 
+template <int ROUNDS>
 __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
                              int shift, const unsigned* hist, int nblocks) {
+  constexpr int RS_TILE = RS_THREADS * ROUNDS;
   __shared__ unsigned wcnt[RS_WARPS][256];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
   int64_t base = (int64_t)blockIdx.x * RS_TILE + w * (RS_TILE / RS_WARPS);
-  unsigned rank[RS_ROUNDS];
+  unsigned rank[ROUNDS];
 #pragma unroll
-  for (int r = 0; r < RS_ROUNDS; ++r) {
+  for (int r = 0; r < ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     bool valid = i < n;
     unsigned dig = valid ? (unsigned)((kin[i] >> shift) & 0xff) : 256u + lane;  // invalid lanes match only themselves
@@ -172,7 +177,7 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < RS_ROUNDS; ++r) {
+  for (int r = 0; r < ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     if (i < n) {
       uint64_t key = kin[i];
@@ -395,7 +400,9 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   HD_TRY(cudaMalloc((void**)&h->inv, sizeof(int) * n));
 
   // scratch: one block, carved up
-  const int nblk = (int)((n + RS_TILE - 1) / RS_TILE);
+  const int rs_rounds = n < (1 << 20) ? 4 : 16;
+  const int64_t rs_tile = (int64_t)RS_THREADS * rs_rounds;
+  const int nblk = (int)((n + rs_tile - 1) / rs_tile);
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     size_t at = off;
@@ -430,9 +437,11 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   HD_TRY_LAUNCH();
 
   for (int shift = 0; shift < 48; shift += 8) {
-    k_rs_hist<<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+    if (rs_rounds == 4) k_rs_hist<4><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+    else k_rs_hist<16><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
     k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
-    k_rs_scatter<<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    if (rs_rounds == 4) k_rs_scatter<4><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    else k_rs_scatter<16><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
     HD_TRY_LAUNCH();
     std::swap(k0, k1);
     std::swap(v0, v1);

@@ -39,12 +39,15 @@ __device__ inline F3 operator+(F3 a, F3 b) { return {a.x + b.x, a.y + b.y, a.z +
 __device__ inline F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ inline float dotf(F3 a, F3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
 __device__ inline float amax3(F3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y), fabsf(a.z))); }
-__device__ inline float norm_ru(F3 a) {
-  return __fsqrt_ru(__fmaf_ru(a.x, a.x, __fmaf_ru(a.y, a.y, __fmul_ru(a.z, a.z))));
-}
-__device__ inline float norm_rd(F3 a) {
-  return __fsqrt_rd(__fmaf_rd(a.x, a.x, __fmaf_rd(a.y, a.y, __fmul_rd(a.z, a.z))));
-}
+// Square root and quotient with outward rounding: the correctly rounded (round-to-nearest)
+// result is within half an ulp, so one multiplication by 1 +- 2^-23, rounded outward, bounds
+// the exact value.
+__device__ inline float sqrt_up(float x) { return __fmul_ru(__fsqrt_rn(x), 1.f + 2.f * kU); }
+__device__ inline float sqrt_dn(float x) { return __fmul_rd(__fsqrt_rn(x), 1.f - 2.f * kU); }
+__device__ inline float div_up(float a, float b) { return __fmul_ru(__fdiv_rn(a, b), 1.f + 2.f * kU); }
+__device__ inline float div_dn(float a, float b) { return __fmul_rz(__fdiv_rn(a, b), 1.f - 2.f * kU); }
+__device__ inline float norm_ru(F3 a) { return sqrt_up(__fmaf_ru(a.x, a.x, __fmaf_ru(a.y, a.y, __fmul_ru(a.z, a.z)))); }
+__device__ inline float norm_rd(F3 a) { return sqrt_dn(__fmaf_rd(a.x, a.x, __fmaf_rd(a.y, a.y, __fmul_rd(a.z, a.z)))); }
 
 // A point as the unevaluated sum h + l of two float triples.
 struct FFP {
@@ -58,33 +61,61 @@ __device__ inline F3 local_off(float4 x, const FFP& p) {
 
 // Barycentric weights (v, w) of the point of triangle (A, B, C) closest to the origin,
 // Voronoi-region classification, clamped so that v, w >= 0 and v + w <= 1 exactly.
-__device__ inline void closest_bary(F3 A, F3 B, F3 C, float& v, float& w) {
+// Returns the region: 0 face, 1 edge AB, 2 edge AC, 3 edge BC, 4 vertex (A, B or C).
+// Degenerate triangles and extreme slivers (|AB x AC|^2 below 1e-5 |AB|^2 |AC|^2, where the
+// region tests are ill-conditioned or, with a zero-length edge, wrong) take the nearest of
+// the three edges.
+__device__ inline int closest_edge_bary(F3 A, F3 B, F3 C, float& v, float& w) {
+  F3 e[3] = {B - A, C - B, A - C};
+  F3 o[3] = {A, B, C};
+  float best = INFINITY;
+  int region = 1;
+  for (int k = 0; k < 3; ++k) {
+    float ee = dotf(e[k], e[k]);
+    float t = ee > 0.f ? fminf(fmaxf(-dotf(o[k], e[k]) / ee, 0.f), 1.f) : 0.f;
+    F3 q = {fmaf(t, e[k].x, o[k].x), fmaf(t, e[k].y, o[k].y), fmaf(t, e[k].z, o[k].z)};
+    float dq = dotf(q, q);
+    if (dq < best) {
+      best = dq;
+      int r = (t == 0.f || t == 1.f) ? 4 : (k == 0 ? 1 : (k == 1 ? 3 : 2));
+      region = r;
+      if (k == 0) { v = t; w = 0.f; }
+      else if (k == 1) { v = __fsub_rd(1.f, t); w = t; }
+      else { v = 0.f; w = __fsub_rd(1.f, t); }
+    }
+  }
+  return region;
+}
+
+__device__ inline int closest_bary(F3 A, F3 B, F3 C, float& v, float& w) {
   F3 ab = B - A, ac = C - A;
-  float d1 = -dotf(ab, A), d2 = -dotf(ac, A);
   v = 0.f;
   w = 0.f;
-  if (d1 <= 0.f && d2 <= 0.f) return;
+  float aa = dotf(ab, ab), cc = dotf(ac, ac), bc = dotf(ab, ac);
+  if (!(aa * cc - bc * bc > 1e-5f * aa * cc)) return closest_edge_bary(A, B, C, v, w);
+  float d1 = -dotf(ab, A), d2 = -dotf(ac, A);
+  if (d1 <= 0.f && d2 <= 0.f) return 4;
   float d3 = -dotf(ab, B), d4 = -dotf(ac, B);
   if (d3 >= 0.f && d4 <= d3) {
     v = 1.f;
-    return;
+    return 4;
   }
   float vc = d1 * d4 - d3 * d2;
   if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
     float den = d1 - d3;
     v = den > 0.f ? fminf(fmaxf(d1 / den, 0.f), 1.f) : 0.f;
-    return;
+    return 1;
   }
   float d5 = -dotf(ab, C), d6 = -dotf(ac, C);
   if (d6 >= 0.f && d5 <= d6) {
     w = 1.f;
-    return;
+    return 4;
   }
   float vb = d5 * d2 - d1 * d6;
   if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
     float den = d2 - d6;
     w = den > 0.f ? fminf(fmaxf(d2 / den, 0.f), 1.f) : 0.f;
-    return;
+    return 2;
   }
   float va = d3 * d6 - d5 * d4;
   if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
@@ -92,31 +123,14 @@ __device__ inline void closest_bary(F3 A, F3 B, F3 C, float& v, float& w) {
     float t = den > 0.f ? fminf(fmaxf((d4 - d3) / den, 0.f), 1.f) : 0.f;
     v = __fsub_rd(1.f, t);
     w = t;
-    return;
+    return 3;
   }
   float den = va + vb + vc;
-  if (den > 0.f) {
-    float inv = 1.f / den;
-    v = fminf(fmaxf(vb * inv, 0.f), 1.f);
-    w = fmaxf(vc * inv, 0.f);
-  } else {  // zero area: best of the three edges
-    float best = INFINITY;
-    F3 e[3] = {ab, C - B, A - C};
-    F3 o[3] = {A, B, C};
-    for (int k = 0; k < 3; ++k) {
-      float ee = dotf(e[k], e[k]);
-      float t = ee > 0.f ? fminf(fmaxf(-dotf(o[k], e[k]) / ee, 0.f), 1.f) : 0.f;
-      F3 q = {fmaf(t, e[k].x, o[k].x), fmaf(t, e[k].y, o[k].y), fmaf(t, e[k].z, o[k].z)};
-      float dq = dotf(q, q);
-      if (dq < best) {
-        best = dq;
-        if (k == 0) { v = t; w = 0.f; }
-        else if (k == 1) { v = __fsub_rd(1.f, t); w = t; }
-        else { v = 0.f; w = __fsub_rd(1.f, t); }
-      }
-    }
-  }
-  w = fminf(w, __fsub_rd(1.f, v));
+  if (!(den > 0.f)) return closest_edge_bary(A, B, C, v, w);
+  float inv = 1.f / den;
+  v = fminf(fmaxf(vb * inv, 0.f), 1.f);
+  w = fminf(fmaxf(vc * inv, 0.f), __fsub_rd(1.f, v));
+  return 0;
 }
 
 struct PtOut {
@@ -127,12 +141,29 @@ struct PtOut {
   bool esc;    // redone in FP64
 };
 
+// min over the vertices of n . X, rounded down, for |n| <= 1 (support-function lower bound)
+__device__ inline float support_rd(F3 n, F3 A, F3 B, F3 C) {
+  float da = __fmaf_rd(n.x, A.x, __fmaf_rd(n.y, A.y, __fmul_rd(n.z, A.z)));
+  float db = __fmaf_rd(n.x, B.x, __fmaf_rd(n.y, B.y, __fmul_rd(n.z, B.z)));
+  float dc = __fmaf_rd(n.x, C.x, __fmaf_rd(n.y, C.y, __fmul_rd(n.z, C.z)));
+  return fminf(da, fminf(db, dc));
+}
+
+// n scaled so that |n| <= 1 (rounded toward zero); false if n is zero
+__device__ inline bool unit_rz(F3& n) {
+  float l = norm_ru(n);
+  if (!(l > 0.f)) return false;
+  float s = div_dn(1.f, l);
+  n = {__fmul_rz(n.x, s), __fmul_rz(n.y, s), __fmul_rz(n.z, s)};
+  return true;
+}
+
 // Certified distance from p = h + l to the float triangle (a, b, c).
 __device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bool want_lo, PtOut& o) {
   F3 A = local_off(a4, P), B = local_off(b4, P), C = local_off(c4, P);
   float M = fmaxf(fmaxf(amax3(A), amax3(B)), fmaxf(amax3(C), amax3(P.l)));
   float v, w;
-  closest_bary(A, B, C, v, w);
+  int region = closest_bary(A, B, C, v, w);
   F3 E1 = B - A, E2 = C - A;
   F3 Q = {fmaf(w, E2.x, fmaf(v, E1.x, A.x)), fmaf(w, E2.y, fmaf(v, E1.y, A.y)), fmaf(w, E2.z, fmaf(v, E1.z, A.z))};
   float nq = norm_ru(Q);
@@ -142,29 +173,42 @@ __device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bo
   o.esc = false;
   o.lo = 0.f;
   if (!want_lo) return;
-  float lo = 0.f;
-  if (nq > 0.f) {
-    float s = __frcp_rd(nq);
-    F3 n = {__fmul_rz(Q.x, s), __fmul_rz(Q.y, s), __fmul_rz(Q.z, s)};  // |n| <= 1
-    float da = __fmaf_rd(n.x, A.x, __fmaf_rd(n.y, A.y, __fmul_rd(n.z, A.z)));
-    float db = __fmaf_rd(n.x, B.x, __fmaf_rd(n.y, B.y, __fmul_rd(n.z, B.z)));
-    float dc = __fmaf_rd(n.x, C.x, __fmaf_rd(n.y, C.y, __fmul_rd(n.z, C.z)));
-    lo = fmaxf(__fsub_rd(fminf(da, fminf(db, dc)), __fmul_ru(6.f * kU, M)), 0.f);
+  // Support direction by region, so that the certificate stays tight when the triangle is
+  // much larger than the distance (the direction of Q alone carries an error of about u M / d):
+  // face -> the plane normal; edge -> Q with its component along the edge removed;
+  // vertex -> Q, which is then the vertex itself.
+  F3 n = Q;
+  if (region == 0) {
+    F3 np = {E1.y * E2.z - E1.z * E2.y, E1.z * E2.x - E1.x * E2.z, E1.x * E2.y - E1.y * E2.x};
+    n = dotf(np, Q) >= 0.f ? np : F3{-np.x, -np.y, -np.z};
+  } else if (region != 4) {
+    F3 e = region == 1 ? E1 : (region == 2 ? E2 : C - B);
+    float ee = dotf(e, e), qe = dotf(Q, e);
+    if (ee > 0.f) n = {Q.x * ee - e.x * qe, Q.y * ee - e.y * qe, Q.z * ee - e.z * qe};
   }
+  float lo = 0.f;
+  if (unit_rz(n)) lo = fmaxf(__fsub_rd(support_rd(n, A, B, C), __fmul_ru(6.f * kU, M)), 0.f);
   o.lo = lo;
   // a loose certificate means the classification was ill-conditioned: redo in FP64
   if (__fsub_rd(nq, lo) > __fmul_ru(256.f * kU, M)) {
     D3 p = {(double)P.h.x + (double)P.l.x, (double)P.h.y + (double)P.l.y, (double)P.h.z + (double)P.l.z};
     D3 a = {a4.x, a4.y, a4.z}, b = {b4.x, b4.y, b4.z}, c = {c4.x, c4.y, c4.z};
-    D3 q = closest_on_triangle(p, a, b, c) - p;
+    D3 q = closest_on_triangle(p, a, b, c) - p;  // a point of the triangle, relative to p
     double d = len(q);
     // covers the double rounding of these few operations, done in absolute coordinates
     double m = 1e-12 * ((double)M + d + fmax(fabs(p.x), fmax(fabs(p.y), fabs(p.z)))) + 1e-30;
-    double lo64 = 0.0;
-    if (d > 0.0) {
-      D3 n = (1.0 / d) * q;
-      lo64 = fmin(dot(n, a - p), fmin(dot(n, b - p), dot(n, c - p))) - m;
-    }
+    // support-function lower bounds along the closest-point direction and both plane normals:
+    // the first is tight when the nearest point is on an edge or vertex, the others when it
+    // is inside the face
+    D3 Ad = a - p, Bv = b - p, Cv = c - p;
+    auto support = [&](D3 nn) {
+      double s = len(nn);
+      if (!(s > 0.0)) return 0.0;
+      nn = (1.0 / (s * (1.0 + 1e-15))) * nn;
+      return fmin(dot(nn, Ad), fmin(dot(nn, Bv), dot(nn, Cv)));
+    };
+    D3 N = cross(Bv - Ad, Cv - Ad);
+    double lo64 = fmax(support(q), fmax(support(N), support((-1.0) * N))) - m;
     o.esc = true;
     o.lo = fmaxf(o.lo, __double2float_rd(fmax(lo64, 0.0)));
     float hi64 = __double2float_ru(d + m);
@@ -214,53 +258,82 @@ struct NearestM {
   }
 };
 
-// Ordered depth-first traversal as in the FP64 path, with certified float box bounds.
-__device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c) {
-  int stack_node[kStack];
+// Ordered depth-first traversal with certified float box bounds, in the "while-while" form
+// of Aila and Laine (HPG 2009): each lane expands inner nodes until it holds a pending leaf
+// range, then the lanes that hold one test one triangle each, together.  The expensive
+// certified point-triangle test thus runs with most lanes of the warp active, and the cheap
+// node steps absorb the divergence.  Stack entries pack a node index (count 0) or a leaf
+// range (first, count) into 32 bits: count in bits 27..31, index below (n_B < 2^27).
+__device__ inline unsigned pack_ref(int ref, int cnt) { return ((unsigned)cnt << 27) | (unsigned)ref; }
+
+// Must be called by all 32 lanes of the warp; inactive lanes start finished.
+__device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, bool active) {
+  unsigned stack_code[kStack];
   float stack_d[kStack];
   int sp = 0;
-  int node = 0;
+  int node = active ? 0 : -1;  // inner node to expand next, -1 = none
+  int lfirst = 0, lcount = 0;
+  bool done = !active;
   for (;;) {
-    const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
-    float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-    int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
-    float d0 = box_lo2(t.P, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
-    float d1 = box_lo2(t.P, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
-    c.boxes += 2;
-    if (ref.z > 0 && d0 <= t.radius2()) t.range(ref.x, ref.z);
-    if (ref.w > 0 && d1 <= t.radius2()) t.range(ref.y, ref.w);
-    float r2 = t.radius2();
-    bool g0 = ref.z == 0 && d0 <= r2, g1 = ref.w == 0 && d1 <= r2;
-    if (g0 && g1) {
-      int nn = ref.x, nf = ref.y;
-      float df = d1;
-      if (d1 < d0) {
-        nn = ref.y;
-        nf = ref.x;
-        df = d0;
+    while (!done && lcount == 0) {
+      if (node < 0) {
+        bool found = false;
+        while (sp > 0) {
+          --sp;
+          if (stack_d[sp] <= t.radius2()) {
+            unsigned code = stack_code[sp];
+            int cnt = (int)(code >> 27), ref = (int)(code & 0x07ffffffu);
+            if (cnt > 0) { lfirst = ref; lcount = cnt; }
+            else node = ref;
+            found = true;
+            break;
+          }
+        }
+        if (!found) done = true;
+        continue;
       }
-      if (sp < kStack) {
-        stack_node[sp] = nf;
-        stack_d[sp] = df;
-        ++sp;
+      const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
+      float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
+      int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
+      float d0 = box_lo2(t.P, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
+      float d1 = box_lo2(t.P, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
+      c.boxes += 2;
+      float r2 = t.radius2();
+      bool h0 = ref.z >= 0 && d0 <= r2, h1 = ref.w >= 0 && d1 <= r2;
+      int nr = 0, nc = -1;  // child taken now
+      if (h0 && h1) {
+        bool first0 = d0 <= d1;
+        int fr = first0 ? ref.y : ref.x, fc = first0 ? ref.w : ref.z;
+        if (sp < kStack) {
+          stack_code[sp] = pack_ref(fr, fc);
+          stack_d[sp] = first0 ? d1 : d0;
+          ++sp;
+        } else {
+          c.err = 1;  // stack overflow: the far subtree is skipped and the error reported
+        }
+        nr = first0 ? ref.x : ref.y;
+        nc = first0 ? ref.z : ref.w;
+      } else if (h0) {
+        nr = ref.x;
+        nc = ref.z;
+      } else if (h1) {
+        nr = ref.y;
+        nc = ref.w;
+      }
+      if (nc > 0) {
+        lfirst = nr;
+        lcount = nc;
+        node = -1;
       } else {
-        c.err = 1;
-      }
-      node = nn;
-      continue;
-    }
-    if (g0) { node = ref.x; continue; }
-    if (g1) { node = ref.y; continue; }
-    bool found = false;
-    while (sp > 0) {
-      --sp;
-      if (stack_d[sp] <= t.radius2()) {
-        node = stack_node[sp];
-        found = true;
-        break;
+        node = nc == 0 ? nr : -1;
       }
     }
-    if (!found) break;
+    if (__all_sync(0xffffffffu, lcount == 0)) break;
+    if (lcount > 0) {
+      t.test1(lfirst);
+      ++lfirst;
+      --lcount;
+    }
   }
 }
 
@@ -314,7 +387,7 @@ __device__ inline float ubm_u2(const VM t[3]) {
     F3 cr = {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
     float err = __fmul_ru(__fmul_ru(32.f * kU, amax3(a)), amax3(b));
     float c2 = __fsub_rd(norm_rd(cr), err);  // lower bound of 2|T|
-    g = c2 > 0.f ? __fdiv_ru(__fmul_ru(__fmul_ru(hi[0], hi[1]), hi[2]), __fmul_rd(2.f, c2)) : INFINITY;
+    g = c2 > 0.f ? div_up(__fmul_ru(__fmul_ru(hi[0], hi[1]), hi[2]), __fmul_rd(2.f, c2)) : INFINITY;
   }
   return __fadd_ru(g, fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi)));
 }
@@ -474,6 +547,16 @@ struct PolicyM {
   static double slack(double amax) { return ldexp(amax, -40); }
 
   __device__ static FFP pos(const Vtx& v) { return {{v.hx, v.hy, v.hz}, {v.lx, v.ly, v.lz}}; }
+  __device__ static D3 exact_pos(const Vtx& v) {
+    return {(double)v.hx + (double)v.lx, (double)v.hy + (double)v.ly, (double)v.hz + (double)v.lz};
+  }
+  // Split further in FP32 only while the gap U - l is well above the FP32 error width of the
+  // vertex distances; below that, refinement cannot make progress and the item is finished
+  // in the FP64 phase.
+  __device__ static bool promote(const Vtx& a, const Vtx& b, const Vtx& c, double U, double l) {
+    float err = fmaxf(fmaxf(a.dhi - a.dlo, b.dhi - b.dlo), c.dhi - c.dlo);
+    return U - l <= 4.0 * (double)err + ldexp(U, -18);
+  }
 
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {
     v.hx = (float)x;
@@ -484,12 +567,19 @@ struct PolicyM {
     v.lz = (float)(z - (double)v.hz);
   }
 
-  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c) {
+  // Called by every lane of the warp (the traversal votes with __all_sync over the full
+  // warp); lanes with active == false only vote and leave v untouched.
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active) {
     NearestM t;
-    t.P = pos(v);
     t.tri32 = B.tri32;
-    if (v.hint >= 0) t.test1(v.hint);
-    traverse_m(B, t, c);
+    if (active) {
+      t.P = pos(v);
+      if (v.hint >= 0) t.test1(v.hint);
+    } else {
+      t.P = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    }
+    traverse_m(B, t, c, active);
+    if (!active) return;
     c.leaf += t.evals;
     c.escalations += t.esc;
     v.tri = t.best;
