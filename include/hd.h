@@ -144,6 +144,24 @@ int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npa
 int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,
                double* dist, int32_t* idx, double* foot, double* dist_lo);
 
+/* Largest n accepted by hd_nearest_noalloc. */
+#define HD_NOALLOC_MAX_POINTS 65536
+
+/* The same queries as hd_nearest (same arguments, same results), for callers that cannot
+ * let a library allocate device memory during the call: code being recorded into a CUDA
+ * graph, programs whose device memory is all handed to their own allocator, loops that must
+ * not block in the driver.  The paper has no counterpart; this is an interface variant.
+ * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
+ * array of 4 MiB + 256 B in the library's device image, which every GPU that loads the
+ * library keeps until the process exits.  n may be at most HD_NOALLOC_MAX_POINTS (65,536);
+ * larger n returns HD_ERR_INVALID without launching anything.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device current, so
+ * make the first call on a device before any stream capture.  All calls share the array:
+ * calls that overlap on the GPU (different streams or threads without ordering) race and
+ * must be serialised by the caller.  Asynchronous on `stream`. */
+int hd_nearest_noalloc(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,
+                       double* dist, int32_t* idx, double* foot, double* dist_lo);
+
 /* UpperBound(T, l) of Section 4 for n triangles given by their vertices and the
  * vertices' nearest-triangle data (as returned by hd_nearest in HD_FP64):
  * T (device, n x 9 doubles: v1, v2, v3), Td (n x 3), TI (n x 3 int32), Tq (n x 9),

@@ -76,6 +76,8 @@ def lib():
                                            C.POINTER(HdResult)]
         L.hd_nearest.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
         L.hd_upper_bounds.argtypes = [vp, vp, vp, vp, vp, i64, d, C.POINTER(HdOptions), vp, vp, vp]
+        L.hd_nearest_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
+        L.hd_nearest_noalloc.restype = C.c_int
         L.hd_trace_enable.argtypes = [C.c_int]
         L.hd_trace_enable.restype = None
         L.hd_trace_read.argtypes = [C.POINTER(HdTrace), C.c_int]
@@ -254,6 +256,29 @@ def hd_nearest(bvh: Bvh, P, precision: int = HD_FP64, stream=None):
     _check(lib().hd_nearest(bvh.handle, P.data_ptr(), HD_F64 if P.dtype == torch.float64 else HD_F32, n, precision,
                             _stream(True, stream), dist.data_ptr(), idx.data_ptr(), foot.data_ptr(), dlo.data_ptr()),
            "hd_nearest")
+    return dist, idx, foot, dlo
+
+
+HD_NOALLOC_MAX_POINTS = 65536
+
+
+def hd_nearest_noalloc(bvh: Bvh, P, precision: int = HD_FP64, out=None, stream=None):
+    """hd_nearest without any device allocation inside the library (at most
+    HD_NOALLOC_MAX_POINTS points).  The output tensors may be passed in ``out`` =
+    (dist, idx, foot, dist_lo) so that the call allocates nothing at all."""
+    import torch
+
+    assert P.is_cuda
+    P = P.contiguous()
+    n = P.shape[0]
+    if out is None:
+        dev = P.device
+        out = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+               torch.empty((n, 3), dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev))
+    dist, idx, foot, dlo = out
+    _check(lib().hd_nearest_noalloc(bvh.handle, P.data_ptr(), HD_F64 if P.dtype == torch.float64 else HD_F32, n,
+                                    precision, _stream(True, stream), dist.data_ptr(), idx.data_ptr(),
+                                    foot.data_ptr(), dlo.data_ptr()), "hd_nearest_noalloc")
     return dist, idx, foot, dlo
 
 

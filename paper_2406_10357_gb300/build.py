@@ -18,7 +18,7 @@ LIB = os.path.join(HERE, "libhd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", SRC]
-UNITS = ["hd_lbvh.cu", "hd_api.cu", "hd_mixed.cu"]
+UNITS = ["hd_lbvh.cu", "hd_api.cu", "hd_mixed.cu", "hd_noalloc.cu"]
 
 
 def _nvcc() -> str:
