@@ -43,10 +43,11 @@ SLICES = 16
 # closest-point evaluation (Voronoi-region method, face-region path) and one child-box test
 FLOPS_PER_LEAF_TEST = 80
 FLOPS_PER_BOX_TEST = 17
+FLOPS_PER_ITEM_BOUND = 100
 BYTES_PER_NODE = 64
 # device->host bytes per step besides results: build flags (8), bbox of A (64) and one
-# RunState (144 B) per round plus round 0
-RUNSTATE_BYTES = 144
+# RunState (160 B) per round plus round 0
+RUNSTATE_BYTES = 160
 
 
 def parse():
@@ -207,6 +208,7 @@ def run_ours(args):
 
     import paper_2406_10357_gb300 as hd
     from paper_2406_10357_gb300 import build as hb
+    from paper_2406_10357_gb300 import multi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -270,10 +272,7 @@ def run_ours(args):
     trace = hd.hd_trace_read(reset=True)
 
     total_ms = sum(ts)
-    if dist:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = multi.max_over_ranks(total_ms, device=dev)  # the slowest rank's time
     value = world * args.steps / (total_ms / 1e3)
 
     # mixed vs FP64 at the same tol (same workload, fewer steps)
@@ -297,10 +296,7 @@ def run_ours(args):
         lo, up = e2e_r["lower"], e2e_r["upper"]  # result already on the host
         e2e_ts.append(time.perf_counter() - t0)
     e2e_total = sum(e2e_ts)
-    if dist:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = multi.max_over_ranks(e2e_total, device=dev)
     h2d = p.VA.nbytes + p.FA.nbytes + p.VB.nbytes + p.FB.nbytes
     d2h = 8 + 64 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
 
@@ -319,21 +315,44 @@ def run_ours(args):
     else:
         peak_tf = 1.25  # FP64 nominal for GB300 (the pool's profiling recipe)
         peak_note = "FP64 nominal 1.25 TFLOP/s"
-    q_flops = FLOPS_PER_LEAF_TEST * leaf + FLOPS_PER_BOX_TEST * boxes
-    achieved = q_flops / (q["ms"] / 1e3) / 1e12 if q["ms"] > 0 else 0.0
-    roof = dict(kernel="k_query (nearest-triangle traversal)", dominant_kind=dom, bound="alu",
-                achieved=achieved, peak=peak_tf, unit="TFLOP/s", frac=achieved / peak_tf,
-                traffic=profiled_traffic("query", args.precision), peak_note=peak_note,
-                algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x leaf tests + {FLOPS_PER_BOX_TEST} flops x box tests",
-                launches=q["launches"], ms_per_launch=q["ms"] / max(1, q["launches"]),
-                l2_bytes_per_launch=(BYTES_PER_NODE * boxes / 2 + 48 * leaf) / max(1, q["launches"]),
-                share={k: round(trace[k]["ms"] / max(1e-9, sum(v["ms"] for v in trace.values())), 4) for k in trace})
+    share = {k: round(trace[k]["ms"] / max(1e-9, sum(v["ms"] for v in trace.values())), 4) for k in trace}
+    # traversal: 80 flops per leaf test + 17 per child box; cascade: 80 per point-triangle
+    # evaluation of u3 + 100 per bounded sub-triangle (exact case, u1, u2); bounded
+    # sub-triangles per step = faces of A + 4 per split
+    items = sum(len(p.FA) + 4 * s["splits"] for s in stats)
+    kinds = {
+        "query": dict(kernel="k_query (nearest-triangle traversal)",
+                      flops=FLOPS_PER_LEAF_TEST * leaf + FLOPS_PER_BOX_TEST * boxes,
+                      algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x leaf tests + {FLOPS_PER_BOX_TEST} flops x box tests",
+                      l2_bytes=BYTES_PER_NODE * boxes / 2 + 48 * leaf),
+        "bound": dict(kernel="k_bound_faces/k_bound_children (UpperBound cascade)",
+                      flops=FLOPS_PER_LEAF_TEST * (evals - leaf) + FLOPS_PER_ITEM_BOUND * items,
+                      algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x u3 point-triangle evaluations + "
+                                  f"{FLOPS_PER_ITEM_BOUND} flops x bounded sub-triangles",
+                      l2_bytes=3 * 64 * items + 48 * (evals - leaf)),
+    }
+
+    def roofline_of(kind):
+        t, k = trace[kind], kinds[kind]
+        achieved = k["flops"] / (t["ms"] / 1e3) / 1e12 if t["ms"] > 0 else 0.0
+        return dict(kernel=k["kernel"], bound="alu", achieved=achieved, peak=peak_tf, unit="TFLOP/s",
+                    frac=achieved / peak_tf, traffic=profiled_traffic(kind, args.precision), peak_note=peak_note,
+                    algorithmic=k["algorithmic"], launches=t["launches"],
+                    ms_per_launch=t["ms"] / max(1, t["launches"]),
+                    l2_bytes_per_launch=k["l2_bytes"] / max(1, t["launches"]))
+
+    main_kind = "bound" if trace["bound"]["ms"] > trace["query"]["ms"] else "query"
+    roof = roofline_of(main_kind)
+    roof.update(dominant_kind=dom, share=share)
+    roof_other = roofline_of("query" if main_kind == "bound" else "bound")
 
     # kernel launches in the timed region: build (24, or 22 when B fits one leaf), A's
     # validation (2), pool init (1), round-0 query and bound (2), 4 per frontier round
     nb = len(p.FB)
     build_k = 24 if nb > 4 else 22
-    launches = sum(build_k + 5 + 4 * s["rounds"] for s in stats)
+    # (MIXED adds the u4 pass after every bound kernel)
+    per_round = 5 if prec == hd.HD_MIXED else 4
+    launches = sum(build_k + 5 + (prec == hd.HD_MIXED) + per_round * s["rounds"] for s in stats)
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
@@ -343,7 +362,7 @@ def run_ours(args):
                 pointtri_evals_per_s=world * evals / (total_ms / 1e3),
                 result=dict(lower=rs[-1]["lower"], upper=rs[-1]["upper"], eps_abs=rs[-1]["stats"]["eps_abs"],
                             rounds=rs[-1]["stats"]["rounds"], splits=rs[-1]["stats"]["splits"]),
-                roofline=roof, e2e=dict(value=world * len(e2e_ts) / e2e_total, unit=UNIT, h2d_bytes_per_step=h2d,
+                roofline=roof, roofline_other_kernel=roof_other, e2e=dict(value=world * len(e2e_ts) / e2e_total, unit=UNIT, h2d_bytes_per_step=h2d,
                                         d2h_bytes_per_step=d2h),
                 gpu_launches=launches, clocks=clk, fp64_arm=fp64)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -342,6 +342,8 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
   RunParams rp;
   rp.eps = 0.0;
   rp.slack = 0.0;
+  rp.slack_f = 0.f;
+  rp.defer_u4 = 0;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   cudaStream_t s = (cudaStream_t)stream;

@@ -141,21 +141,35 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
   flush_counters(st, c);
 }
 
-// Discard / retire / keep one bounded item (Section 3.1: discard when U < l).
+// Comparison thresholds in the policy's number type, rounded down so that U < lo implies
+// U < l (discard) and U <= hi implies U <= l + eps (retire).
 template <class P>
-__device__ inline void classify(RunState* st, const typename P::Item& it, double l, double eps, int code,
-                                typename P::Item* next, int next_cap) {
-  double U = (double)it.U;
-  if (U < l) {
+struct Thresholds {
+  typename P::UT lo, hi;
+  __device__ Thresholds(double l, double eps) : lo(P::ut_down(l)), hi(P::ut_down(add_rd(l, eps))) {}
+};
+
+// Discard / retire / keep one bounded item (Section 3.1: discard when U < l).  Items whose
+// trailing u4 is deferred go to the u4 list instead.
+template <class P>
+__device__ inline void classify(RunState* st, const typename P::Item& it, const Thresholds<P>& th, int code,
+                                typename P::Item* next, int next_cap, typename P::Item* u4list) {
+  if (code == kDeferU4) {
+    int j = atomicAdd(&st->n_u4, 1);
+    if (j < next_cap) u4list[j] = it;
+    else atomicExch(&st->overflow, 1);
+    return;
+  }
+  if (it.U < th.lo) {
     atomicAdd(&st->discards[code], 1ull);
-  } else if (U <= __dadd_rd(l, eps)) {
-    atomic_max_nonneg(&st->uret_bits, U);
+  } else if (it.U <= th.hi) {
+    atomic_max_nonneg(&st->uret_bits, (double)it.U);
     atomicAdd(&st->retired, 1ull);
   } else {
     int j = atomicAdd(&st->n_next, 1);
     if (j < next_cap) {
       next[j] = it;
-      atomic_max_nonneg(&st->umax_bits, U);
+      atomic_max_nonneg(&st->umax_bits, (double)it.U);
     } else {
       atomicExch(&st->overflow, 1);
     }
@@ -169,9 +183,10 @@ __device__ inline double load_l(const RunState* st) {
 // Round 0: UpperBound for every face of A.
 template <class P>
 __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
-                              RunParams rp, typename P::Item* next, int next_cap) {
+                              RunParams rp, typename P::Item* next, int next_cap, typename P::Item* u4list) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double l = load_l(st);
+  Thresholds<P> th(l, rp.eps);
   Counters c;
   if (f < nFA) {
     typename P::Item it;
@@ -180,9 +195,31 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
     it.v[2] = FA[3 * f + 2];
     int code;
     it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
-    classify<P>(st, it, l, rp.eps, code, next, next_cap);
+    classify<P>(st, it, th, code, next, next_cap, u4list);
   }
   flush_counters(st, c);
+}
+
+// The u4 pass (MIXED): items whose cascade reached a trailing u4 get it here, in FP64, with
+// every lane of a warp on its own item; then discard / retire / keep as usual.
+template <class P>
+__global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
+                           RunState* st, RunParams rp, typename P::Item* next, int next_cap) {
+  int n = min(*(volatile int*)&st->n_u4, cap);
+  double l = load_l(st);
+  Thresholds<P> th(l, rp.eps);
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    typename P::Item it = u4list[t];
+    typename P::UT u = P::bound_u4(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], rp);
+    int code = 5;
+    if (u < th.lo) {
+      code = 4;
+      it.U = u;
+    } else if (u < it.U) {
+      it.U = u;
+    }
+    classify<P>(st, it, th, code, next, next_cap, nullptr);
+  }
 }
 
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
@@ -194,13 +231,14 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_front) return;
   double l = load_l(st);
+  Thresholds<P> th(l, rp.eps);
   typename P::Item it = front[i];
   double U = (double)it.U;
-  if (U < l) {
+  if (it.U < th.lo) {
     atomicAdd(&st->discards[5], 1ull);
     return;
   }
-  if (U <= __dadd_rd(l, rp.eps)) {
+  if (it.U <= th.hi) {
     atomic_max_nonneg(&st->uret_bits, U);
     atomicAdd(&st->retired, 1ull);
     return;
@@ -240,9 +278,11 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
 template <class P>
 __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par, int K, int mbase,
-                                 RunState* st, RunParams rp, typename P::Item* next, int next_cap) {
+                                 RunState* st, RunParams rp, typename P::Item* next, int next_cap,
+                                 typename P::Item* u4list) {
   int S = min(*(volatile int*)&st->n_split, K);
   double l = load_l(st);
+  Thresholds<P> th(l, rp.eps);
   Counters c;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
     bool active = t < 4 * (int64_t)S;
@@ -258,7 +298,7 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
       it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
-      classify<P>(st, it, l, rp.eps, code, next, next_cap);
+      classify<P>(st, it, th, code, next, next_cap, u4list);
     }
   }
   flush_counters(st, c);
@@ -268,6 +308,7 @@ static __global__ void k_round_reset(RunState* st, int n_front) {
   st->n_front = n_front;
   st->n_next = 0;
   st->n_split = 0;
+  st->n_u4 = 0;
   st->umax_bits = 0;
   st->overflow = 0;
 }
@@ -318,7 +359,8 @@ template <class P>
 struct Rounds {
   typename P::Vtx* pool = nullptr;
   typename P::Item* front[2] = {nullptr, nullptr};
-  typename P::Item* promo = nullptr;  // items handed to the FP64 phase (MIXED only)
+  typename P::Item* promo = nullptr;   // items handed to the FP64 phase (MIXED only)
+  typename P::Item* u4list = nullptr;  // items waiting for the u4 pass (MIXED only)
   int4* split_par = nullptr;
   int64_t pool_cap = 0, front_cap = 0, chunk = 0, promo_cap = 0;
   int64_t n_pool = 0, n_front = 0;
@@ -347,6 +389,7 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
   HD_TRY(cudaMallocAsync((void**)&R.front[1], sizeof(Item) * R.front_cap, s));
   HD_TRY(cudaMallocAsync((void**)&R.split_par, sizeof(int4) * R.chunk, s));
   if (promo) HD_TRY(cudaMallocAsync((void**)&R.promo, sizeof(Item) * R.promo_cap, s));
+  if (promo) HD_TRY(cudaMallocAsync((void**)&R.u4list, sizeof(Item) * R.front_cap, s));
   return HD_OK;
 }
 
@@ -357,6 +400,7 @@ void free_rounds(Rounds<P>& R, cudaStream_t s) {
   cudaFreeAsync(R.front[1], s);
   cudaFreeAsync(R.split_par, s);
   if (R.promo) cudaFreeAsync(R.promo, s);
+  if (R.u4list) cudaFreeAsync(R.u4list, s);
 }
 
 inline double round_upper(const RunState* h, int64_t n_front) {
@@ -409,7 +453,10 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, RunState* hst, cons
       TraceScope tr(HD_K_BOUND, s);
       unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
       k_bound_children<P><<<gb, bs, 0, s>>>(B, R.pool, R.split_par, (int)K, (int)R.n_pool, st, rp,
-                                            R.front[R.cur ^ 1], (int)R.front_cap);
+                                            R.front[R.cur ^ 1], (int)R.front_cap, R.u4list);
+      if (R.u4list)
+        k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[R.cur ^ 1],
+                                              (int)R.front_cap);
     }
     HD_TRY_LAUNCH();
     HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
@@ -478,8 +525,11 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   }
   {
     TraceScope tr(HD_K_BOUND, s);
-    k_bound_faces<PolicyD><<<blocks_for(n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, tris, n_pro, st, rp,
-                                                                                   D.front[1], (int)D.front_cap);
+    RunParams rpd = rp;
+    rpd.defer_u4 = 0;
+    k_bound_faces<PolicyD><<<blocks_for(n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, tris, n_pro, st, rpd,
+                                                                                   D.front[1], (int)D.front_cap,
+                                                                                   nullptr);
   }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
@@ -528,6 +578,9 @@ int run_bnb(const RunIO& io) {
   RunParams rp;
   rp.eps = eps;
   rp.slack = P::slack(amax);
+  rp.slack_f = (float)rp.slack;
+  if ((double)rp.slack_f < rp.slack) rp.slack_f = std::nextafter(rp.slack_f, INFINITY);
+  rp.defer_u4 = P::kFp64 ? 0 : 1;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   const int bs = o.block_size;
@@ -554,7 +607,10 @@ int run_bnb(const RunIO& io) {
   {
     TraceScope tr(HD_K_BOUND, s);
     k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
-                                                           (int)R.front_cap);
+                                                           (int)R.front_cap, R.u4list);
+    if (R.u4list)
+      k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[1],
+                                            (int)R.front_cap);
   }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));

@@ -179,10 +179,11 @@ __device__ inline double ub_u3(const BvhDev& B, const VI t[3], unsigned long lon
     else if (t[0].I == t[1].I) lone = 2;
   }
   int fs0, fs1, fo, go;
-  if (lone >= 0 && shared_edge(B, t[lone].I, t[(lone + 1) % 3].I, fs0, fs1, fo, go)) {
-    const VI& v1 = t[lone];
-    const VI& v2 = t[(lone + 1) % 3];
-    const VI& v3 = t[(lone + 2) % 3];
+  // v1 is the vertex alone on its triangle (selected by branches: no runtime array index)
+  VI v1 = t[0], v2 = t[1], v3 = t[2];
+  if (lone == 1) { v1 = t[1]; v2 = t[2]; v3 = t[0]; }
+  else if (lone == 2) { v1 = t[2]; v2 = t[0]; v3 = t[1]; }
+  if (lone >= 0 && shared_edge(B, v1.I, v2.I, fs0, fs1, fo, go)) {
     int S1 = v1.I, S2 = v2.I;
     D3 p0 = tri_vertex(B, S1, fs0), e = tri_vertex(B, S1, fs1) - p0;
     D3 b1 = 0.5 * (v1.v + v2.v), b2 = 0.5 * (v1.v + v3.v);
@@ -258,7 +259,9 @@ __device__ inline double ub_u4(const VI t[3]) {
   double m = l0;
   if (l1 < m) { k = 1; m = l1; }
   if (l2 < m) k = 2;
-  D3 q2 = t[k].q, q3 = t[(k + 1) % 3].q, q1 = t[(k + 2) % 3].q;
+  D3 q2 = t[0].q, q3 = t[1].q, q1 = t[2].q;  // shortest edge v1v2 (k = 0)
+  if (k == 1) { q2 = t[1].q; q3 = t[2].q; q1 = t[0].q; }
+  else if (k == 2) { q2 = t[2].q; q3 = t[0].q; q1 = t[1].q; }
   return fmin(h_two_points(t, q1, q2), h_two_points(t, q1, q3));
 }
 
@@ -315,6 +318,8 @@ struct PolicyD {
   __device__ static double out_dlo(const Vtx& v) { return v.d; }
   __device__ static D3 out_foot(const Vtx& v) { return {v.qx, v.qy, v.qz}; }
   static double slack(double) { return 0.0; }
+  __device__ static double ut_down(double x) { return x; }
+  __device__ static double bound_u4(const Vtx&, const Vtx&, const Vtx&, const RunParams&) { return INFINITY; }
   __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
   __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {

@@ -101,6 +101,7 @@ struct RunState {
   int overflow;                  // next frontier or split list ran out of room
   int err;                       // traversal stack overflow and similar
   int n_promote;                 // MIXED items handed to the FP64 phase
+  int n_u4;                      // MIXED items whose u4 is evaluated in the separate u4 pass
   unsigned long long upro_bits;  // max U of those items (double bits)
   unsigned long long evals, box_tests, queries, retired, escalations, leaf_tests;
   unsigned long long discards[6];
@@ -123,7 +124,12 @@ struct RunParams {
                  // error of subdivided vertices as float pairs; 0 in FP64)
   uint8_t order[4];
   int n_bounds;
+  float slack_f;  // slack rounded up to float
+  int defer_u4;   // MIXED: a trailing u4 is evaluated in the separate u4 pass
 };
+
+// UpperBound result code: u4 still to be evaluated by the u4 pass (MIXED)
+constexpr int kDeferU4 = 6;
 
 // Per-thread statistics, flushed with one atomic per warp.
 struct Counters {
@@ -153,6 +159,8 @@ __device__ inline unsigned float_to_ordered(float f) {
 __device__ inline float ordered_to_float(unsigned u) {
   return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
 }
+
+__device__ inline double add_rd(double a, double b) { return __dadd_rd(a, b); }
 
 __device__ inline void atomic_max_nonneg(unsigned long long* addr, double v) {
   atomicMax(addr, (unsigned long long)__double_as_longlong(v));

@@ -70,6 +70,7 @@ __device__ inline int closest_edge_bary(F3 A, F3 B, F3 C, float& v, float& w) {
   F3 o[3] = {A, B, C};
   float best = INFINITY;
   int region = 1;
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
     float ee = dotf(e[k], e[k]);
     float t = ee > 0.f ? fminf(fmaxf(-dotf(o[k], e[k]) / ee, 0.f), 1.f) : 0.f;
@@ -409,7 +410,7 @@ __device__ inline FFP along(const VM& base, F3 e, float s, float& beta) {
 }
 
 // u3 (Kang et al. 2018), Eqs. (Kang2018_case1) and (Kang2018_case2).
-__device__ inline float ubm_u3(const BvhDev& B, const VM t[3], unsigned long long& evals) {
+__device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned long long& evals) {
   int lone = -1;
   if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
     if (t[1].I == t[2].I) lone = 0;
@@ -417,10 +418,12 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], unsigned long lon
     else if (t[0].I == t[1].I) lone = 2;
   }
   int fs0, fs1, fo, go;
-  if (lone >= 0 && shared_edge(B, t[lone].I, t[(lone + 1) % 3].I, fs0, fs1, fo, go)) {
-    const VM& v1 = t[lone];
-    const VM& v2 = t[(lone + 1) % 3];
-    const VM& v3 = t[(lone + 2) % 3];
+  // v1 is the vertex alone on its triangle; selected by branches (no runtime array index, so
+  // the three vertices stay in registers)
+  VM v1 = t[0], v2 = t[1], v3 = t[2];
+  if (lone == 1) { v1 = t[1]; v2 = t[2]; v3 = t[0]; }
+  else if (lone == 2) { v1 = t[2]; v2 = t[0]; v3 = t[1]; }
+  if (lone >= 0 && shared_edge(B, v1.I, v2.I, fs0, fs1, fo, go)) {
     int S1 = v1.I, S2 = v2.I;
     F3 e12 = edge(v1, v2), e13 = edge(v1, v3);
     // split parameters: the bisecting plane of the two supporting half-planes (any value
@@ -456,7 +459,21 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], unsigned long lon
                      fmaxf(dist_hi(B, S2, b1, be1), v2.dhi));
     return fmaxf(hR, hQ);
   }
-  // case 2: quadrilaterals (v_i, m_i, b, m_{i-1}) against S_i, then min with h(T, S_i)
+  // case 2: u3 = min(u3~, min_i h(T, S_i)).  The second term is computed first: once the
+  // minimum is below l the item is discarded whatever u3~ is (U of a discarded item is not
+  // used further), and the quadrilateral maximum u3~ is abandoned as soon as it reaches the
+  // current minimum, since it can then no longer lower it.
+  float best = INFINITY;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    float h = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) h = fmaxf(h, j == i ? t[j].dhi : dist_hi(B, t[i].I, t[j].p, 0.f));
+    best = fminf(best, h);
+  }
+  evals += 6;
+  if (best < l) return best;
+  // quadrilaterals (v_i, m_i, b, m_{i-1}) against S_i
   F3 e01 = edge(t[0], t[1]), e02 = edge(t[0], t[2]), e12 = edge(t[1], t[2]);
   float bm[3];
   FFP m[3];
@@ -467,23 +484,16 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], unsigned long lon
   float bb;
   FFP bc = along(t[0], sum, 1.f / 3.f, bb);
   bb = __fmul_ru(16.f * kU, fmaxf(amax3(e01), fmaxf(amax3(e02), amax3(t[0].p.l))));
-  float ut = 0.f;
+  float ut = fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi));
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
+    if (ut >= best) break;
     int S = t[i].I;
-    float h = fmaxf(fmaxf(t[i].dhi, dist_hi(B, S, m[i], bm[i])),
-                    fmaxf(dist_hi(B, S, bc, bb), dist_hi(B, S, m[(i + 2) % 3], bm[(i + 2) % 3])));
-    ut = fmaxf(ut, h);
+    ut = fmaxf(ut, dist_hi(B, S, m[i], bm[i]));
+    ut = fmaxf(ut, dist_hi(B, S, bc, bb));
+    ut = fmaxf(ut, dist_hi(B, S, m[(i + 2) % 3], bm[(i + 2) % 3]));
+    evals += 3;
   }
-  float best = INFINITY;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float h = 0.f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) h = fmaxf(h, j == i ? t[j].dhi : dist_hi(B, t[i].I, t[j].p, 0.f));
-    best = fminf(best, h);
-  }
-  evals += 15;
   return fminf(ut, best);
 }
 
@@ -508,6 +518,8 @@ __device__ inline float ubm_u4(const VM t[3], double slack) {
 
 __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], double l, const RunParams& rp, int& code,
                                       Counters& c) {
+  // comparisons against l in float: lf <= l, so u < lf still means u < l
+  const float lf = __double2float_rd(l);
   float U;
   if (t[0].I == t[1].I && t[1].I == t[2].I) {
     code = 0;
@@ -516,22 +528,28 @@ __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], double l, 
     U = INFINITY;
     code = 5;
     for (int k = 0; k < rp.n_bounds; ++k) {
+      if (rp.order[k] == 4 && k == rp.n_bounds - 1 && rp.defer_u4) {
+        // u4 (FP64) is evaluated for all such items together in the u4 pass, with full
+        // warps, instead of by scattered lanes here; U so far is a valid upper bound
+        code = kDeferU4;
+        break;
+      }
       float u;
       switch (rp.order[k]) {
         case 1: u = ubm_u1(t); break;
         case 2: u = ubm_u2(t); break;
-        case 3: u = ubm_u3(B, t, c.evals); break;
+        case 3: u = ubm_u3(B, t, lf, c.evals); break;
         default: u = ubm_u4(t, rp.slack); break;
       }
       U = fminf(U, u);
-      if ((double)u < l) {
+      if (u < lf) {
         code = rp.order[k];
         U = u;
         break;
       }
     }
   }
-  return __fadd_ru(U, __double2float_ru(rp.slack));
+  return __fadd_ru(U, rp.slack_f);
 }
 
 // ----------------------------------------------------------------------------- the policy
@@ -545,6 +563,14 @@ struct PolicyM {
   // 2^-40 of the largest coordinate: covers the float-pair representation of subdivided
   // vertices (2^-48 relative per level, at most 60 levels) and the double rounding of u4
   static double slack(double amax) { return ldexp(amax, -40); }
+  __device__ static float ut_down(double x) { return __double2float_rd(x); }
+  // the u4 pass: Eq. (bound_u4) for one item, plus the slack
+  __device__ static float bound_u4(const Vtx& a, const Vtx& b, const Vtx& c, const RunParams& rp) {
+    VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
+               {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
+               {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
+    return __fadd_ru(ubm_u4(t, rp.slack), rp.slack_f);
+  }
 
   __device__ static FFP pos(const Vtx& v) { return {{v.hx, v.hy, v.hz}, {v.lx, v.ly, v.lz}}; }
   __device__ static D3 exact_pos(const Vtx& v) {
