@@ -127,12 +127,10 @@ static void keep_pool_memory() {
   }
 }
 
-int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax) {
+int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale) {
   cudaStream_t s = io.s;
-  unsigned long long* box = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&box, 64, s));
-  unsigned long long init[8] = {~0ull, ~0ull, ~0ull, 0, 0, 0, 0, 0};
-  HD_TRY(cudaMemcpyAsync(box, init, 64, cudaMemcpyHostToDevice, s));
+  HD_TRY(cudaMemsetAsync(box, 0xff, 3 * sizeof(unsigned long long), s));  // ordered minima start high
+  HD_TRY(cudaMemsetAsync(box + 3, 0, 5 * sizeof(unsigned long long), s));  // maxima low, flag clear
   HD_TRY(cudaMemsetAsync(ref, 0, io.nVA, s));
   int* bad = (int*)(box + 6);
   {
@@ -142,23 +140,9 @@ int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax) {
       k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
     else
       k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
+    k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn);
   }
   HD_TRY_LAUNCH();
-  unsigned long long h[8];
-  HD_TRY(cudaMemcpyAsync(h, box, 64, cudaMemcpyDeviceToHost, s));
-  HD_TRY(cudaFreeAsync(box, s));
-  HD_TRY(cudaStreamSynchronize(s));
-  if (h[6] & 0xffffffffull) return HD_ERR_INVALID;
-  double v[6];
-  for (int k = 0; k < 6; ++k) {
-    unsigned long long u = h[k];
-    u = (u >> 63) ? (u & ~(1ull << 63)) : ~u;
-    memcpy(&v[k], &u, 8);
-  }
-  double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
-  *dA = sqrt(dx * dx + dy * dy + dz * dz);
-  *amax = 0.0;
-  for (int k = 0; k < 6; ++k) *amax = fmax(*amax, fabs(v[k]));
   return HD_OK;
 }
 

@@ -95,6 +95,28 @@ static __global__ void k_check_bbox(const T* VA, int64_t nVA, const uint8_t* ref
   }
 }
 
+__device__ inline double ordered_to_double(unsigned long long u) {
+  u = (u >> 63) ? (u & ~(1ull << 63)) : ~u;
+  return __longlong_as_double((long long)u);
+}
+
+// dA, eps and the slack from A's bounding box, on the device (one thread).
+static __global__ void k_prep_finish(const unsigned long long* box, double tol, int tol_rel, double slack_scale,
+                                     DynParams* dyn) {
+  double v[6];
+  for (int k = 0; k < 6; ++k) v[k] = ordered_to_double(box[k]);
+  double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
+  double dA = sqrt(dx * dx + dy * dy + dz * dz);
+  double amax = 0.0;
+  for (int k = 0; k < 6; ++k) amax = fmax(amax, fabs(v[k]));
+  double slack = slack_scale * amax;
+  dyn->dA = dA;
+  dyn->eps = tol_rel ? tol * dA : tol;
+  dyn->slack = slack;
+  dyn->slack_f = __double2float_ru(slack);
+  dyn->pad = 0;
+}
+
 template <class P, typename T>
 __global__ void k_init_pool(const T* VA, int64_t nVA, const uint8_t* ref, typename P::Vtx* pool) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -111,7 +133,8 @@ __global__ void k_init_pool(const T* VA, int64_t nVA, const uint8_t* ref, typena
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.
 template <class P>
 __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
-                        RunState* st, double slack) {
+                        RunState* st, double slack_in, const DynParams* dyn) {
+  const double slack = dyn ? dyn->slack : slack_in;
   int count = cap;
   if (count_ptr) count = min(*count_ptr * mult, cap);
   Counters c;
@@ -183,11 +206,23 @@ __device__ inline double load_l(const RunState* st) {
 // Round 0: UpperBound for every face of A.
 template <class P>
 __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
-                              RunParams rp, typename P::Item* next, int next_cap, typename P::Item* u4list) {
+                              RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list,
+                              int64_t n_pool_valid) {
+  const RunParams rp = with_dyn(rp_in);
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
   Counters c;
+  if (f < nFA) {
+    typename P::Item it;
+    it.v[0] = FA[3 * f];
+    it.v[1] = FA[3 * f + 1];
+    it.v[2] = FA[3 * f + 2];
+    // A is validated concurrently (the host checks the flag after round 0): skip bad rows
+    bool ok = it.v[0] >= 0 && it.v[1] >= 0 && it.v[2] >= 0 && it.v[0] < n_pool_valid && it.v[1] < n_pool_valid &&
+              it.v[2] < n_pool_valid;
+    if (!ok) f = nFA;
+  }
   if (f < nFA) {
     typename P::Item it;
     it.v[0] = FA[3 * f];
@@ -204,7 +239,8 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
 // every lane of a warp on its own item; then discard / retire / keep as usual.
 template <class P>
 __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
-                           RunState* st, RunParams rp, typename P::Item* next, int next_cap) {
+                           RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
+  const RunParams rp = with_dyn(rp_in);
   int n = min(*(volatile int*)&st->n_u4, cap);
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
@@ -225,11 +261,12 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
 // rest (three midpoints each into the pool at mbase), carry the others over.
 template <class P>
-__global__ void k_select(const typename P::Item* front, int n_front, RunState* st, RunParams rp, int K,
+__global__ void k_select(const typename P::Item* front, int n_front, RunState* st, RunParams rp_in, int K,
                          int4* split_par, typename P::Vtx* pool, int mbase, typename P::Item* next, int next_cap,
                          typename P::Item* promo, int promo_cap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_front) return;
+  const RunParams rp = with_dyn(rp_in);
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
   typename P::Item it = front[i];
@@ -278,8 +315,9 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
 template <class P>
 __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par, int K, int mbase,
-                                 RunState* st, RunParams rp, typename P::Item* next, int next_cap,
+                                 RunState* st, RunParams rp_in, typename P::Item* next, int next_cap,
                                  typename P::Item* u4list) {
+  const RunParams rp = with_dyn(rp_in);
   int S = min(*(volatile int*)&st->n_split, K);
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
@@ -352,11 +390,13 @@ inline double bits_to_double(unsigned long long b) {
 }
 
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
-int prepare_A(const RunIO& io, uint8_t* ref, double* dA, double* amax);
+// Enqueues the validation of A, its bounding box and the device-side parameters (no sync).
+int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale);
 
 // Buffers of one policy's frontier loop.
 template <class P>
 struct Rounds {
+  char* base = nullptr;  // the single allocation the buffers below are carved from
   typename P::Vtx* pool = nullptr;
   typename P::Item* front[2] = {nullptr, nullptr};
   typename P::Item* promo = nullptr;   // items handed to the FP64 phase (MIXED only)
@@ -384,23 +424,28 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
   R.chunk = o.frontier_chunk > 0 ? o.frontier_chunk : std::max<int64_t>(R.front_cap / 4, 1024);
   R.chunk = std::min<int64_t>(R.chunk, R.front_cap);
   R.promo_cap = promo ? R.front_cap : 0;
-  HD_TRY(cudaMallocAsync((void**)&R.pool, sizeof(Vtx) * R.pool_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&R.front[0], sizeof(Item) * R.front_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&R.front[1], sizeof(Item) * R.front_cap, s));
-  HD_TRY(cudaMallocAsync((void**)&R.split_par, sizeof(int4) * R.chunk, s));
-  if (promo) HD_TRY(cudaMallocAsync((void**)&R.promo, sizeof(Item) * R.promo_cap, s));
-  if (promo) HD_TRY(cudaMallocAsync((void**)&R.u4list, sizeof(Item) * R.front_cap, s));
+  // one stream-ordered allocation, carved into the buffers (256-byte aligned)
+  auto round_up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t b_pool = round_up(sizeof(Vtx) * R.pool_cap), b_front = round_up(sizeof(Item) * R.front_cap),
+               b_split = round_up(sizeof(int4) * R.chunk), b_promo = promo ? b_front : 0;
+  char* base = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&base, b_pool + 2 * b_front + b_split + 2 * b_promo, s));
+  R.base = base;
+  R.pool = (Vtx*)base;
+  R.front[0] = (Item*)(base + b_pool);
+  R.front[1] = (Item*)(base + b_pool + b_front);
+  R.split_par = (int4*)(base + b_pool + 2 * b_front);
+  if (promo) {
+    R.promo = (Item*)(base + b_pool + 2 * b_front + b_split);
+    R.u4list = (Item*)(base + b_pool + 2 * b_front + b_split + b_promo);
+  }
   return HD_OK;
 }
 
 template <class P>
 void free_rounds(Rounds<P>& R, cudaStream_t s) {
-  cudaFreeAsync(R.pool, s);
-  cudaFreeAsync(R.front[0], s);
-  cudaFreeAsync(R.front[1], s);
-  cudaFreeAsync(R.split_par, s);
-  if (R.promo) cudaFreeAsync(R.promo, s);
-  if (R.u4list) cudaFreeAsync(R.u4list, s);
+  if (R.base) cudaFreeAsync(R.base, s);
+  R.base = nullptr;
 }
 
 inline double round_upper(const RunState* h, int64_t n_front) {
@@ -447,7 +492,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, RunState* hst, cons
     {
       TraceScope tr(HD_K_QUERY, s);
       unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
-      k_query<P><<<gq, bs, 0, s>>>(B, R.pool, (int)R.n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack);
+      k_query<P><<<gq, bs, 0, s>>>(B, R.pool, (int)R.n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack, rp.dyn);
     }
     {
       TraceScope tr(HD_K_BOUND, s);
@@ -509,7 +554,11 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   int rc = alloc_rounds<PolicyD>(D, o, 3 * n_pro, n_pro, false, s);
   if (rc != HD_OK) return rc;
   int32_t* tris = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&tris, sizeof(int32_t) * 3 * n_pro, s));
+  cudaError_t e = cudaMallocAsync((void**)&tris, sizeof(int32_t) * 3 * n_pro, s);
+  if (e != cudaSuccess) {
+    free_rounds(D, s);
+    return set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+  }
   {
     TraceScope tr(HD_K_PREP, s);
     k_promote_init<P><<<blocks_for(n_pro, 256), 256, 0, s>>>(RM.promo, (int)n_pro, RM.pool, D.pool, tris);
@@ -521,7 +570,8 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, 0, nullptr, 1,
-                                                                                 (int)(3 * n_pro), st, rp.slack);
+                                                                                 (int)(3 * n_pro), st, rp.slack,
+                                                                                 rp.dyn);
   }
   {
     TraceScope tr(HD_K_BOUND, s);
@@ -529,7 +579,7 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
     rpd.defer_u4 = 0;
     k_bound_faces<PolicyD><<<blocks_for(n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, tris, n_pro, st, rpd,
                                                                                    D.front[1], (int)D.front_cap,
-                                                                                   nullptr);
+                                                                                   nullptr, 3 * n_pro);
   }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
@@ -552,34 +602,45 @@ int run_bnb(const RunIO& io) {
   hd_result& res = *io.out;
   memset(&res, 0, sizeof res);
 
-  uint8_t* ref = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&ref, std::max<int64_t>(io.nVA, 1), s));
-  double dA = 0.0;
-  double amax = 0.0;
-  int rc = prepare_A(io, ref, &dA, &amax);
+  struct HostBlock {
+    RunState st;
+    DynParams dyn;
+    unsigned long long bad;
+  };
+  static thread_local HostBlock* hb = nullptr;  // pinned read-back buffer, kept for the thread's lifetime
+  if (!hb) HD_TRY(cudaMallocHost((void**)&hb, sizeof(HostBlock)));
+
+  // small per-call device block: referenced-vertex flags, A's bbox + invalid flag, the
+  // device-side parameters, and the run state
+  const size_t ref_bytes = ((size_t)std::max<int64_t>(io.nVA, 1) + 255) & ~(size_t)255;
+  unsigned char* small = nullptr;
+  HD_TRY(cudaMallocAsync((void**)&small, ref_bytes + 256 + 256 + sizeof(RunState), s));
+  uint8_t* ref = small;
+  unsigned long long* box = (unsigned long long*)(small + ref_bytes);  // [0..5] bbox, [6] invalid flag
+  DynParams* dyn = (DynParams*)(small + ref_bytes + 256);
+  RunState* st = (RunState*)(small + ref_bytes + 512);
+  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
+  // validation of A and its bbox run asynchronously; the host reads the result with round 0
+  int rc = prepare_A(io, ref, box, dyn, P::slack(1.0));
   if (rc != HD_OK) {
-    cudaFreeAsync(ref, s);
+    cudaFreeAsync(small, s);
     return rc;
   }
-  const double eps = o.tol_mode == HD_TOL_REL ? io.tol * dA : io.tol;
-  res.stats.dA = dA;
-  res.stats.eps_abs = eps;
 
   Rounds<P> R;
   rc = alloc_rounds<P>(R, o, io.nVA, io.nFA, !P::kFp64, s);
-  if (rc != HD_OK) return rc;
-  RunState* st = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
-  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
-  static thread_local RunState* hst = nullptr;  // pinned read-back buffer, kept for the thread's lifetime
-  if (!hst) HD_TRY(cudaMallocHost((void**)&hst, sizeof(RunState)));
+  if (rc != HD_OK) {
+    cudaFreeAsync(small, s);
+    return rc;
+  }
+  RunState* hst = &hb->st;
 
   BvhDev B = bvh_dev(io.B);
   RunParams rp;
-  rp.eps = eps;
-  rp.slack = P::slack(amax);
-  rp.slack_f = (float)rp.slack;
-  if ((double)rp.slack_f < rp.slack) rp.slack_f = std::nextafter(rp.slack_f, INFINITY);
+  rp.eps = 0.0;  // taken from dyn on the device
+  rp.slack = 0.0;
+  rp.slack_f = 0.f;
+  rp.dyn = dyn;
   rp.defer_u4 = P::kFp64 ? 0 : 1;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
@@ -601,20 +662,32 @@ int run_bnb(const RunIO& io) {
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
-                                                                       rp.slack);
+                                                                       rp.slack, rp.dyn);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_BOUND, s);
     k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
-                                                           (int)R.front_cap, R.u4list);
+                                                           (int)R.front_cap, R.u4list, io.nVA);
     if (R.u4list)
       k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[1],
                                             (int)R.front_cap);
   }
   HD_TRY_LAUNCH();
   HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+  HD_TRY(cudaMemcpyAsync(&hb->dyn, dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+  HD_TRY(cudaMemcpyAsync(&hb->bad, box + 6, 8, cudaMemcpyDeviceToHost, s));
   HD_TRY(cudaStreamSynchronize(s));
+  if (hb->bad & 0xffffffffull) {  // invalid A: nothing of round 0 is used
+    free_rounds(R, s);
+    cudaFreeAsync(small, s);
+    return HD_ERR_INVALID;
+  }
+  res.stats.dA = hb->dyn.dA;
+  res.stats.eps_abs = hb->dyn.eps;
+  rp.eps = hb->dyn.eps;  // host copies, for the FP64 phase's own parameter block
+  rp.slack = hb->dyn.slack;
+  rp.slack_f = hb->dyn.slack_f;
 
   Totals T;
   R.cur = 1;
@@ -627,7 +700,11 @@ int run_bnb(const RunIO& io) {
   int64_t n_pro = hst->n_promote;
   if (rc == HD_OK && status == HD_OK && n_pro > 0)
     rc = finish_in_fp64<P>(io, R, std::min<int64_t>(n_pro, R.promo_cap), st, hst, rp, T, &status);
-  if (rc != HD_OK) return rc;
+  if (rc != HD_OK) {
+    free_rounds(R, s);
+    cudaFreeAsync(small, s);
+    return rc;
+  }
 
   double l = bits_to_double(hst->l_bits);
   double uret = bits_to_double(hst->uret_bits);
@@ -653,8 +730,7 @@ int run_bnb(const RunIO& io) {
   S.pool_vertices = R.n_pool;
 
   free_rounds(R, s);
-  cudaFreeAsync(st, s);
-  cudaFreeAsync(ref, s);
+  cudaFreeAsync(small, s);
   return HD_OK;
 }
 

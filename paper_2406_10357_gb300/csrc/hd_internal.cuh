@@ -117,6 +117,17 @@ struct BvhDev {
   float eta;
 };
 
+// Per-run values that are only known on the device (they depend on A's bounding box):
+// written by k_prep_finish, read by every round kernel, so that no host round trip is needed
+// between validating A and round 0.
+struct DynParams {
+  double eps;     // absolute tolerance
+  double slack;   // see RunParams
+  double dA;      // bbox diagonal of A's referenced vertices
+  float slack_f;  // slack rounded up to float
+  int pad;
+};
+
 // Per-run constants of the round kernels.
 struct RunParams {
   double eps;    // absolute tolerance
@@ -126,7 +137,17 @@ struct RunParams {
   int n_bounds;
   float slack_f;  // slack rounded up to float
   int defer_u4;   // MIXED: a trailing u4 is evaluated in the separate u4 pass
+  const DynParams* dyn;  // if set, eps / slack / slack_f are taken from here on the device
 };
+
+__device__ inline RunParams with_dyn(RunParams rp) {
+  if (rp.dyn) {
+    rp.eps = rp.dyn->eps;
+    rp.slack = rp.dyn->slack;
+    rp.slack_f = rp.dyn->slack_f;
+  }
+  return rp;
+}
 
 // UpperBound result code: u4 still to be evaluated by the u4 pass (MIXED)
 constexpr int kDeferU4 = 6;
