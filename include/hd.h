@@ -113,7 +113,11 @@ void hd_options_default(hd_options* opt);
  * hd_free_B(*out).  opt may be NULL. */
 int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** out);
 
-/* Release everything hd_build_B allocated.  NULL is allowed. */
+/* Release everything hd_build_B allocated.  NULL is allowed.  The device memory goes
+ * back to the device's stream-ordered pool in stream order on the legacy default stream,
+ * so it follows earlier work on blocking streams; work that reads the BVH on a stream
+ * created non-blocking (hd_nearest, hd_nearest_noalloc, hd_upper_bounds are asynchronous)
+ * must be synchronized before this call.  hd_hausdorff returns after its work is done. */
 void hd_free_B(hd_bvh* bvh);
 
 /* Triangle count of B and whether its vertices were given as float64. */

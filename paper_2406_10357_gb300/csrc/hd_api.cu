@@ -250,11 +250,15 @@ int hd_build_B(const hd_mesh* B, const hd_options* opt, void* stream, hd_bvh** o
 
 void hd_free_B(hd_bvh* b) {
   if (!b) return;
-  cudaFree(b->nodes);
-  cudaFree(b->tri32);
-  cudaFree(b->tri64);
-  cudaFree(b->tri_vid);
-  cudaFree(b->inv);
+  if (b->block) {
+    // stream-ordered release on the legacy default stream of the BVH's device: it follows
+    // all earlier work on blocking streams; the block returns to the pool, not the driver
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != b->device) cudaSetDevice(b->device);
+    cudaFreeAsync(b->block, 0);
+    if (cur >= 0 && cur != b->device) cudaSetDevice(cur);
+  }
   delete b;
 }
 

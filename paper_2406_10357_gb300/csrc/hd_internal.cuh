@@ -42,6 +42,7 @@ struct hd_bvh {
   int leaf_size;
   int input_f64;
   int64_t n_nodes;
+  void* block;         // one stream-ordered allocation; the arrays below are carved from it
   hd::BvhNode* nodes;  // n_nodes
   float4* tri32;       // 3 per triangle: a.xyz|orig-index-bits, b.xyz|0, c.xyz|0 (RN of input)
   double* tri64;       // 9 per triangle: a, b, c (exact input values)

@@ -3,7 +3,7 @@
 // The paper builds libigl's AABB tree over B once and uses it for all distance queries
 // (Section 4).  Here the hierarchy is a linear BVH built on the GPU:
 //   1. triangle centroids and their bounding box;
-//   2. 48-bit Morton codes (16 bits per axis) of the centroids;
+//   2. Morton codes of the centroids, 10 to 16 bits per axis (wider for larger B);
 //   3. a stable LSD radix sort of (code, triangle) pairs, 8-bit digits;
 //   4. the binary radix tree of Karras (HPG 2012) over the sorted codes, ties broken by
 //      position;
@@ -79,8 +79,9 @@ __device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit
   return x;
 }
 
-__global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned* cbox, uint64_t* keys,
+__global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
                          uint32_t* vals) {
+  const double cells = (double)(1u << bits);
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nF) return;
   const double* t = tri_unsorted + 9 * f;
@@ -91,7 +92,7 @@ __global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned*
     double ext = (double)hi - (double)lo;
     double u = ext > 0.0 ? (c - lo) / ext : 0.5;
     u = fmin(fmax(u, 0.0), 1.0);
-    q[k] = (uint32_t)fmin(u * 65536.0, 65535.0);
+    q[k] = (uint32_t)fmin(u * cells, cells - 1.0);
   }
   keys[f] = (spread16(q[0]) << 2) | (spread16(q[1]) << 1) | spread16(q[2]);
   vals[f] = (uint32_t)f;
@@ -388,16 +389,29 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   }
 
   hd_bvh* h = new hd_bvh();
+  h->block = nullptr;
   h->device = dev;
   h->nF = n;
   h->leaf_size = o.leaf_size;
   h->input_f64 = B->vtype == HD_F64;
   h->n_nodes = n > 1 ? n - 1 : 1;
-  HD_TRY(cudaMalloc((void**)&h->nodes, sizeof(BvhNode) * h->n_nodes));
-  HD_TRY(cudaMalloc((void**)&h->tri32, sizeof(float4) * 3 * n));
-  HD_TRY(cudaMalloc((void**)&h->tri64, sizeof(double) * 9 * n));
-  HD_TRY(cudaMalloc((void**)&h->tri_vid, sizeof(int4) * n));
-  HD_TRY(cudaMalloc((void**)&h->inv, sizeof(int) * n));
+  {
+    // the BVH's own arrays: one allocation from the device's stream-ordered pool
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_nodes = up(sizeof(BvhNode) * h->n_nodes), b_t32 = up(sizeof(float4) * 3 * n),
+                 b_t64 = up(sizeof(double) * 9 * n), b_vid = up(sizeof(int4) * n), b_inv = up(sizeof(int) * n);
+    cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv, s);
+    if (e != cudaSuccess) {
+      delete h;
+      return set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
+    }
+    char* c = (char*)h->block;
+    h->nodes = (BvhNode*)c;
+    h->tri32 = (float4*)(c + b_nodes);
+    h->tri64 = (double*)(c + b_nodes + b_t32);
+    h->tri_vid = (int4*)(c + b_nodes + b_t32 + b_t64);
+    h->inv = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid);
+  }
 
   // scratch: one block, carved up
   const int rs_rounds = n < (1 << 20) ? 4 : 16;
@@ -433,10 +447,14 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s)
                               : launch_prep<float>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s);
   if (rc != HD_OK) return rc;
-  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, n, misc, k0, v0);
+  // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
+  // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
+  int bits = 10;
+  while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
+  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, n, misc, bits, k0, v0);
   HD_TRY_LAUNCH();
 
-  for (int shift = 0; shift < 48; shift += 8) {
+  for (int shift = 0; shift < 3 * bits; shift += 8) {
     if (rs_rounds == 4) k_rs_hist<4><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
     else k_rs_hist<16><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
     k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
