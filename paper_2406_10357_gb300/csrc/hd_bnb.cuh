@@ -17,6 +17,8 @@
 // i.e. when every item is discarded or retired, which is the paper's (u - l) <= eps.
 #pragma once
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -164,6 +166,50 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
   flush_counters(st, c);
 }
 
+// A slot in a device-side list for each calling lane: one atomic per warp (the lanes that
+// reach the call together share it).
+__device__ inline int warp_slot(int* counter) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (int)g.size());
+  return g.shfl(base, 0) + (int)g.thread_rank();
+}
+
+// Per-thread outcome counts and maxima of classified items, flushed once per warp.
+template <class P>
+struct Tally {
+  unsigned d0 = 0, d1 = 0, d2 = 0, d3 = 0, d4 = 0, d5 = 0, retired = 0;
+  typename P::UT uret = 0, umax = 0;
+  __device__ void discard(int code) {
+    d0 += code == 0;
+    d1 += code == 1;
+    d2 += code == 2;
+    d3 += code == 3;
+    d4 += code == 4;
+    d5 += code == 5;
+  }
+};
+
+// Every lane of the warp must call it.
+template <class P>
+__device__ inline void flush_tally(RunState* st, const Tally<P>& t) {
+  unsigned long long d[6] = {warp_sum(t.d0), warp_sum(t.d1), warp_sum(t.d2),
+                             warp_sum(t.d3), warp_sum(t.d4), warp_sum(t.d5)};
+  unsigned long long r = warp_sum(t.retired);
+  double uret = warp_max((double)t.uret), umax = warp_max((double)t.umax);
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      if (d[k]) atomicAdd(&st->discards[k], d[k]);
+    if (r) {
+      atomicAdd(&st->retired, r);
+      atomic_max_nonneg(&st->uret_bits, uret);
+    }
+    if (umax > 0.0) atomic_max_nonneg(&st->umax_bits, umax);
+  }
+}
+
 // Comparison thresholds in the policy's number type, rounded down so that U < lo implies
 // U < l (discard) and U <= hi implies U <= l + eps (retire).
 template <class P>
@@ -176,23 +222,23 @@ struct Thresholds {
 // trailing u4 is deferred go to the u4 list instead.
 template <class P>
 __device__ inline void classify(RunState* st, const typename P::Item& it, const Thresholds<P>& th, int code,
-                                typename P::Item* next, int next_cap, typename P::Item* u4list) {
+                                typename P::Item* next, int next_cap, typename P::Item* u4list, Tally<P>& ty) {
   if (code == kDeferU4) {
-    int j = atomicAdd(&st->n_u4, 1);
+    int j = warp_slot(&st->n_u4);
     if (j < next_cap) u4list[j] = it;
     else atomicExch(&st->overflow, 1);
     return;
   }
   if (it.U < th.lo) {
-    atomicAdd(&st->discards[code], 1ull);
+    ty.discard(code);
   } else if (it.U <= th.hi) {
-    atomic_max_nonneg(&st->uret_bits, (double)it.U);
-    atomicAdd(&st->retired, 1ull);
+    ty.uret = ty.uret > it.U ? ty.uret : it.U;
+    ++ty.retired;
   } else {
-    int j = atomicAdd(&st->n_next, 1);
+    int j = warp_slot(&st->n_next);
     if (j < next_cap) {
       next[j] = it;
-      atomic_max_nonneg(&st->umax_bits, (double)it.U);
+      ty.umax = ty.umax > it.U ? ty.umax : it.U;
     } else {
       atomicExch(&st->overflow, 1);
     }
@@ -213,6 +259,7 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
   Counters c;
+  Tally<P> ty;
   if (f < nFA) {
     typename P::Item it;
     it.v[0] = FA[3 * f];
@@ -230,9 +277,10 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
     it.v[2] = FA[3 * f + 2];
     int code;
     it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
-    classify<P>(st, it, th, code, next, next_cap, u4list);
+    classify<P>(st, it, th, code, next, next_cap, u4list, ty);
   }
   flush_counters(st, c);
+  flush_tally(st, ty);
 }
 
 // The u4 pass (MIXED): items whose cascade reached a trailing u4 get it here, in FP64, with
@@ -244,6 +292,7 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
   int n = min(*(volatile int*)&st->n_u4, cap);
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
+  Tally<P> ty;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     typename P::Item it = u4list[t];
     typename P::UT u = P::bound_u4(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], rp);
@@ -254,8 +303,9 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
     } else if (u < it.U) {
       it.U = u;
     }
-    classify<P>(st, it, th, code, next, next_cap, nullptr);
+    classify<P>(st, it, th, code, next, next_cap, nullptr, ty);
   }
+  flush_tally(st, ty);
 }
 
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
@@ -265,50 +315,51 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
                          int4* split_par, typename P::Vtx* pool, int mbase, typename P::Item* next, int next_cap,
                          typename P::Item* promo, int promo_cap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_front) return;
   const RunParams rp = with_dyn(rp_in);
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
-  typename P::Item it = front[i];
-  double U = (double)it.U;
-  if (it.U < th.lo) {
-    atomicAdd(&st->discards[5], 1ull);
-    return;
-  }
-  if (it.U <= th.hi) {
-    atomic_max_nonneg(&st->uret_bits, U);
-    atomicAdd(&st->retired, 1ull);
-    return;
-  }
-  typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
-  if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
-    int j = atomicAdd(&st->n_promote, 1);
-    if (j < promo_cap) {
-      promo[j] = it;
-      atomic_max_nonneg(&st->upro_bits, U);
+  Tally<P> ty;
+  if (i < n_front) {
+    typename P::Item it = front[i];
+    double U = (double)it.U;
+    if (it.U < th.lo) {
+      ty.discard(5);
+    } else if (it.U <= th.hi) {
+      ty.uret = it.U;
+      ty.retired = 1;
     } else {
-      atomicExch(&st->overflow, 1);
+      typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
+      if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
+        int j = atomicAdd(&st->n_promote, 1);
+        if (j < promo_cap) {
+          promo[j] = it;
+          atomic_max_nonneg(&st->upro_bits, U);
+        } else {
+          atomicExch(&st->overflow, 1);
+        }
+      } else {
+        int s = warp_slot(&st->n_split);
+        if (s < K) {
+          split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], 0);
+          P::midpoint(a, b, m);
+          pool[mbase + 3 * s] = m;
+          P::midpoint(b, c, m);
+          pool[mbase + 3 * s + 1] = m;
+          P::midpoint(c, a, m);
+          pool[mbase + 3 * s + 2] = m;
+        } else {
+          int j = warp_slot(&st->n_next);
+          if (j < next_cap) {
+            next[j] = it;
+            ty.umax = it.U;
+          } else {
+            atomicExch(&st->overflow, 1);
+          }
+        }
+      }
     }
-    return;
   }
-  int s = atomicAdd(&st->n_split, 1);
-  if (s < K) {
-    split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], 0);
-    P::midpoint(a, b, m);
-    pool[mbase + 3 * s] = m;
-    P::midpoint(b, c, m);
-    pool[mbase + 3 * s + 1] = m;
-    P::midpoint(c, a, m);
-    pool[mbase + 3 * s + 2] = m;
-  } else {
-    int j = atomicAdd(&st->n_next, 1);
-    if (j < next_cap) {
-      next[j] = it;
-      atomic_max_nonneg(&st->umax_bits, U);
-    } else {
-      atomicExch(&st->overflow, 1);
-    }
-  }
+  flush_tally(st, ty);
 }
 
 // The four children of every split (Section 4, midpoint subdivision):
@@ -322,6 +373,7 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
   double l = load_l(st);
   Thresholds<P> th(l, rp.eps);
   Counters c;
+  Tally<P> ty;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
     bool active = t < 4 * (int64_t)S;
     if (__all_sync(0xffffffffu, !active)) break;
@@ -336,10 +388,11 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
       it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
-      classify<P>(st, it, th, code, next, next_cap, u4list);
+      classify<P>(st, it, th, code, next, next_cap, u4list, ty);
     }
   }
   flush_counters(st, c);
+  flush_tally(st, ty);
 }
 
 static __global__ void k_round_reset(RunState* st, int n_front) {
