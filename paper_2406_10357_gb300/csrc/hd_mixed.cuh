@@ -393,11 +393,43 @@ __device__ inline float ubm_u2(const VM t[3]) {
   return __fadd_ru(g, fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi)));
 }
 
+// Upper bound of d(x, S) for the float triangle S = (a4, b4, c4), x = h + l, computed without
+// branches: the distance to the projection of x onto the plane of S when it falls inside S
+// (well-conditioned triangles only), else to the nearest of the three edge projections.  Any
+// point of S gives an upper bound, so the parameters need not be exact; they only have to lie
+// in [0, 1] (the face point: v, w >= 0, v + w <= 1), and the point built from a vertex, the
+// parameters and the edge vectors carries the same rounding as in pt_cert, covered by the
+// same 48 u M margin.
+__device__ inline float pt_hi(const FFP& P, float4 a4, float4 b4, float4 c4) {
+  F3 A = local_off(a4, P), B = local_off(b4, P), C = local_off(c4, P);
+  float M = fmaxf(fmaxf(amax3(A), amax3(B)), fmaxf(amax3(C), amax3(P.l)));
+  F3 E1 = B - A, E2 = C - A, E3 = C - B;
+  float d00 = dotf(E1, E1), d01 = dotf(E1, E2), d11 = dotf(E2, E2);
+  float a1 = -dotf(A, E1), a2 = -dotf(A, E2);
+  // edge parameters; a zero-length edge gives 0/0 = NaN, which saturates to 0
+  float t1 = __saturatef(__fdividef(a1, d00)), t2 = __saturatef(__fdividef(a2, d11));
+  float t3 = __saturatef(__fdividef(-dotf(B, E3), dotf(E3, E3)));
+  F3 Q = {fmaf(t1, E1.x, A.x), fmaf(t1, E1.y, A.y), fmaf(t1, E1.z, A.z)};
+  F3 Q2 = {fmaf(t2, E2.x, A.x), fmaf(t2, E2.y, A.y), fmaf(t2, E2.z, A.z)};
+  F3 Q3 = {fmaf(t3, E3.x, B.x), fmaf(t3, E3.y, B.y), fmaf(t3, E3.z, B.z)};
+  float n = dotf(Q, Q), n2 = dotf(Q2, Q2), n3 = dotf(Q3, Q3);
+  if (n2 < n) { Q = Q2; n = n2; }
+  if (n3 < n) Q = Q3;
+  float den = d00 * d11 - d01 * d01;
+  if (den > 1e-5f * d00 * d11) {
+    float r = __fdividef(1.f, den);
+    float v = (d11 * a1 - d01 * a2) * r, w = (d00 * a2 - d01 * a1) * r;
+    if (v >= 0.f && w >= 0.f && v + w <= 1.f) {
+      w = fminf(w, __fsub_rd(1.f, v));  // v + w <= 1 exactly
+      Q = {fmaf(w, E2.x, fmaf(v, E1.x, A.x)), fmaf(w, E2.y, fmaf(v, E1.y, A.y)), fmaf(w, E2.z, fmaf(v, E1.z, A.z))};
+    }
+  }
+  return __fadd_ru(norm_ru(Q), __fmul_ru(48.f * kU, M));
+}
+
 __device__ inline float dist_hi(const BvhDev& B, int j, const FFP& x, float beta) {
   const float4* t = B.tri32 + 3 * (size_t)j;
-  PtOut o;
-  pt_cert(x, __ldg(t), __ldg(t + 1), __ldg(t + 2), false, o);
-  return __fadd_ru(o.hi, beta);
+  return __fadd_ru(pt_hi(x, __ldg(t), __ldg(t + 1), __ldg(t + 2)), beta);
 }
 
 // Point base + s * e (s in [0, 1]) as a float pair, with its representation error.
@@ -409,7 +441,10 @@ __device__ inline FFP along(const VM& base, F3 e, float s, float& beta) {
   return x;
 }
 
-// u3 (Kang et al. 2018), Eqs. (Kang2018_case1) and (Kang2018_case2).
+// u3 (Kang et al. 2018), Eqs. (Kang2018_case1) and (Kang2018_case2).  Both cases start with
+// point-triangle distances that are laid out as six evaluation slots, so that the lanes of a
+// warp run the same code whichever case each item is in: case 1 fills four slots, (b1, S1),
+// (b2, S1), (b1, S2), (b2, S2); case 2 fills all six with (v_j, S_i), j != i.
 __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned long long& evals) {
   int lone = -1;
   if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
@@ -423,8 +458,11 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned
   VM v1 = t[0], v2 = t[1], v3 = t[2];
   if (lone == 1) { v1 = t[1]; v2 = t[2]; v3 = t[0]; }
   else if (lone == 2) { v1 = t[2]; v2 = t[0]; v3 = t[1]; }
-  if (lone >= 0 && shared_edge(B, v1.I, v2.I, fs0, fs1, fo, go)) {
-    int S1 = v1.I, S2 = v2.I;
+  const bool c1 = lone >= 0 && shared_edge(B, v1.I, v2.I, fs0, fs1, fo, go);
+  const int S1 = v1.I, S2 = v2.I;
+  FFP b1 = v1.p, b2 = v1.p;
+  float be1 = 0.f, be2 = 0.f;
+  if (c1) {
     F3 e12 = edge(v1, v2), e13 = edge(v1, v3);
     // split parameters: the bisecting plane of the two supporting half-planes (any value
     // in [0, 1] gives a valid split; this choice only affects tightness)
@@ -451,26 +489,30 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned
         }
       }
     }
-    float be1, be2;
-    FFP b1 = along(v1, e12, s2, be1), b2 = along(v1, e13, s3, be2);
+    b1 = along(v1, e12, s2, be1);
+    b2 = along(v1, e13, s3, be2);
+  }
+  float d[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    // case 2 slot k: triangle of vertex k / 2, and the next or the other vertex
+    const int i = k >> 1, j = (k == 0 || k == 5) ? 1 : ((k == 1 || k == 3) ? 2 : 0);
+    FFP x = c1 ? ((k & 1) ? b2 : b1) : t[j].p;
+    float be = c1 ? ((k & 1) ? be2 : be1) : 0.f;
+    int S = c1 ? (k < 2 ? S1 : S2) : t[i].I;
+    d[k] = (c1 && k >= 4) ? 0.f : dist_hi(B, S, x, be);
+  }
+  const float dmax = fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi));
+  if (c1) {
     evals += 4;
-    float hR = fmaxf(v1.dhi, fmaxf(dist_hi(B, S1, b1, be1), dist_hi(B, S1, b2, be2)));
-    float hQ = fmaxf(fmaxf(v3.I == S2 ? v3.dhi : dist_hi(B, S2, v3.p, 0.f), dist_hi(B, S2, b2, be2)),
-                     fmaxf(dist_hi(B, S2, b1, be1), v2.dhi));
-    return fmaxf(hR, hQ);
+    return fmaxf(dmax, fmaxf(fmaxf(d[0], d[1]), fmaxf(d[2], d[3])));
   }
-  // case 2: u3 = min(u3~, min_i h(T, S_i)).  The second term is computed first: once the
-  // minimum is below l the item is discarded whatever u3~ is (U of a discarded item is not
-  // used further), and the quadrilateral maximum u3~ is abandoned as soon as it reaches the
+  // case 2: u3 = min(u3~, min_i h(T, S_i)).  The second term comes from the slots: once it is
+  // below l the item is discarded whatever u3~ is (U of a discarded item is not used
+  // further), and the quadrilateral maximum u3~ is abandoned as soon as it reaches the
   // current minimum, since it can then no longer lower it.
-  float best = INFINITY;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float h = 0.f;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) h = fmaxf(h, j == i ? t[j].dhi : dist_hi(B, t[i].I, t[j].p, 0.f));
-    best = fminf(best, h);
-  }
+  float best = fminf(fmaxf(t[0].dhi, fmaxf(d[0], d[1])),
+                     fminf(fmaxf(t[1].dhi, fmaxf(d[2], d[3])), fmaxf(t[2].dhi, fmaxf(d[4], d[5]))));
   evals += 6;
   if (best < l) return best;
   // quadrilaterals (v_i, m_i, b, m_{i-1}) against S_i
@@ -484,7 +526,7 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned
   float bb;
   FFP bc = along(t[0], sum, 1.f / 3.f, bb);
   bb = __fmul_ru(16.f * kU, fmaxf(amax3(e01), fmaxf(amax3(e02), amax3(t[0].p.l))));
-  float ut = fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi));
+  float ut = dmax;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     if (ut >= best) break;
