@@ -10,6 +10,7 @@
 //   5. bottom-up boxes (float, rounded outward so they contain the exact triangles);
 //   6. traversal nodes: 64 B each, holding both child boxes; subtrees of at most
 //      leaf_size triangles become leaf ranges.
+#include <cmath>
 #include <cstdio>
 #include <vector>
 
@@ -29,7 +30,7 @@ __device__ inline D3 load_vertex(const T* V, int64_t i) {
 }
 
 template <typename T>
-__global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, double* tri_unsorted,
+__global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, double* tri_unsorted, float4* cent,
                        unsigned* cbox /*6 ordered floats: min xyz (as ~max), max xyz*/, int* bad) {
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
@@ -52,6 +53,7 @@ __global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, dou
         lo[0] = hi[0] = (float)m.x;
         lo[1] = hi[1] = (float)m.y;
         lo[2] = hi[2] = (float)m.z;
+        cent[f] = make_float4(lo[0], lo[1], lo[2], 0.f);
       }
     }
   }
@@ -79,20 +81,20 @@ __device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit
   return x;
 }
 
-__global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
+__global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
                          uint32_t* vals) {
-  const double cells = (double)(1u << bits);
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nF) return;
-  const double* t = tri_unsorted + 9 * f;
+  const float cells = (float)(1u << bits);
+  float4 c = cent[f];
+  float cc[3] = {c.x, c.y, c.z};
   uint32_t q[3];
+#pragma unroll
   for (int k = 0; k < 3; ++k) {
     float lo = ordered_to_float(cbox[k]), hi = ordered_to_float(cbox[3 + k]);
-    double c = (t[k] + t[3 + k] + t[6 + k]) / 3.0;
-    double ext = (double)hi - (double)lo;
-    double u = ext > 0.0 ? (c - lo) / ext : 0.5;
-    u = fmin(fmax(u, 0.0), 1.0);
-    q[k] = (uint32_t)fmin(u * cells, cells - 1.0);
+    float ext = hi - lo;
+    float u = ext > 0.f ? (cc[k] - lo) * (cells / ext) : 0.5f * cells;
+    q[k] = (uint32_t)fminf(fmaxf(u, 0.f), cells - 1.f);
   }
   keys[f] = (spread16(q[0]) << 2) | (spread16(q[1]) << 1) | spread16(q[2]);
   vals[f] = (uint32_t)f;
@@ -104,7 +106,9 @@ __global__ void k_morton(const double* tri_unsorted, int64_t nF, const unsigned*
 // Small inputs use 4 rounds (1024-key tiles) so that more blocks share the work.
 constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32;
 
-template <int ROUNDS>
+// Per-block digit counts: digit-major (hist[d * nblocks + b], scanned by k_rs_scan) or, for
+// the fused small-input path, block-major (hist[b * 256 + d], read by every scatter block).
+template <int ROUNDS, bool FUSED>
 __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks) {
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
   __shared__ unsigned cnt[256];
@@ -116,8 +120,15 @@ __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* 
     if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 0xff], 1u);
   }
   __syncthreads();
-  for (int d = threadIdx.x; d < 256; d += blockDim.x) hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+    if (FUSED) hist[(int64_t)blockIdx.x * 256 + d] = cnt[d];
+    else hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+  }
 }
+
+// Largest block count of the fused path: each scatter block then reads all nblocks x 256
+// counts itself instead of waiting for a separate scan launch.
+constexpr int RS_FUSED_MAX_BLOCKS = 64;
 
 // exclusive scan of `n` counters in place, one block of 1024 threads
 __global__ void k_rs_scan(unsigned* a, int64_t n) {
@@ -142,12 +153,36 @@ __global__ void k_rs_scan(unsigned* a, int64_t n) {
   }
 }
 
-template <int ROUNDS>
+template <int ROUNDS, bool FUSED>
 __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
                              int shift, const unsigned* hist, int nblocks) {
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
+  static_assert(RS_THREADS == 256, "one digit per thread in the fused offsets");
   __shared__ unsigned wcnt[RS_WARPS][256];
+  __shared__ unsigned doff[256];
+  __shared__ unsigned wsum[RS_WARPS];
   int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (FUSED) {
+    // this block's start for digit d: all keys of smaller digits, plus the keys of digit d in
+    // earlier blocks
+    const int d = threadIdx.x;
+    unsigned tot = 0, mine = 0;
+    for (int b = 0; b < nblocks; ++b) {
+      unsigned c = hist[(int64_t)b * 256 + d];
+      tot += c;
+      mine += b < (int)blockIdx.x ? c : 0u;
+    }
+    unsigned x = tot;  // inclusive warp scan, then across the 8 warps
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    unsigned before = 0;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    doff[d] = before + x - tot + mine;
+  }
   for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
@@ -183,7 +218,7 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
     if (i < n) {
       uint64_t key = kin[i];
       unsigned dig = (unsigned)((key >> shift) & 0xff);
-      unsigned pos = hist[(int64_t)dig * nblocks + blockIdx.x] + wcnt[w][dig] + rank[r];
+      unsigned pos = (FUSED ? doff[dig] : hist[(int64_t)dig * nblocks + blockIdx.x]) + wcnt[w][dig] + rank[r];
       kout[pos] = key;
       vout[pos] = vin[i];
     }
@@ -197,38 +232,43 @@ __device__ inline float ru(double x) { return __double2float_ru(x); }
 
 __global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uint32_t* order, int64_t nF,
                          double* tri64, float4* tri32, int4* tri_vid, int* inv, float4* leafbox /*2 per leaf*/,
-                         unsigned* eta_bits) {
+                         unsigned* e2_bits) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nF) return;
-  uint32_t f = order[i];
-  const double* s = tri_unsorted + 9 * (size_t)f;
-  double* t = tri64 + 9 * i;
-  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  float eta = 0.0f;
-  float4 out[3];
-  for (int v = 0; v < 3; ++v) {
-    float c[3];
-    for (int k = 0; k < 3; ++k) {
-      double x = s[3 * v + k];
-      t[3 * v + k] = x;
-      lo[k] = fminf(lo[k], rd(x));
-      hi[k] = fmaxf(hi[k], ru(x));
-      c[k] = (float)x;
+  double e2 = 0.0;  // squared distance between a float vertex and its input vertex
+  if (i < nF) {
+    uint32_t f = order[i];
+    const double* s = tri_unsorted + 9 * (size_t)f;
+    double* t = tri64 + 9 * i;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    float4 out[3];
+    for (int v = 0; v < 3; ++v) {
+      float c[3];
+      for (int k = 0; k < 3; ++k) {
+        double x = s[3 * v + k];
+        t[3 * v + k] = x;
+        lo[k] = fminf(lo[k], rd(x));
+        hi[k] = fmaxf(hi[k], ru(x));
+        c[k] = (float)x;
+      }
+      // x - float(x) is exact in double
+      double ex = s[3 * v] - c[0], ey = s[3 * v + 1] - c[1], ez = s[3 * v + 2] - c[2];
+      e2 = fmax(e2, ex * ex + ey * ey + ez * ez);
+      out[v] = make_float4(c[0], c[1], c[2], 0.0f);
     }
-    // distance between the float vertex and the input vertex, rounded up
-    double ex = s[3 * v] - c[0], ey = s[3 * v + 1] - c[1], ez = s[3 * v + 2] - c[2];
-    eta = fmaxf(eta, __double2float_ru(sqrt(ex * ex + ey * ey + ez * ez) * (1.0 + 1e-12)));
-    out[v] = make_float4(c[0], c[1], c[2], 0.0f);
+    out[0].w = __int_as_float((int)f);
+    tri32[3 * i] = out[0];
+    tri32[3 * i + 1] = out[1];
+    tri32[3 * i + 2] = out[2];
+    tri_vid[i] = make_int4(F[3 * f], F[3 * f + 1], F[3 * f + 2], (int)f);
+    inv[f] = (int)i;
+    leafbox[2 * i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    leafbox[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
   }
-  out[0].w = __int_as_float((int)f);
-  tri32[3 * i] = out[0];
-  tri32[3 * i + 1] = out[1];
-  tri32[3 * i + 2] = out[2];
-  tri_vid[i] = make_int4(F[3 * f], F[3 * f + 1], F[3 * f + 2], (int)f);
-  inv[f] = (int)i;
-  leafbox[2 * i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
-  leafbox[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
-  if (eta > 0.0f) atomicMax(eta_bits, __float_as_uint(eta));
+  // the largest squared error, rounded up (the host takes its square root): the squares and
+  // their sum carry at most 3 * 2^-53 relative error, covered by the margin
+  float e2f = __double2float_ru(e2 * (1.0 + 1e-12));
+  for (int o = 16; o > 0; o >>= 1) e2f = fmaxf(e2f, __shfl_xor_sync(0xffffffffu, e2f, o));
+  if ((threadIdx.x & 31) == 0 && e2f > 0.0f) atomicMax(e2_bits, __float_as_uint(e2f));
 }
 
 // ---------------------------------------------------------------- 5: Karras binary radix tree
@@ -280,39 +320,23 @@ __device__ inline void load_box(const float4* b, float lo[3], float hi[3]) {
   hi[0] = c.x; hi[1] = c.y; hi[2] = c.z;
 }
 
-// Bottom-up boxes: the second child to arrive at a node computes its box.
-__global__ void k_refit(int64_t n, const int* left, const int* right, const int* parent_int,
-                        const int* parent_leaf, const float4* leafbox, float4* ibox, int* flags) {
-  int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (leaf >= n) return;
-  int node = parent_leaf[leaf];
-  while (node >= 0) {
-    __threadfence();
-    if (atomicAdd(&flags[node], 1) == 0) return;
-    __threadfence();
-    float lo[3], hi[3], lo2[3], hi2[3];
-    int cl = left[node], cr = right[node];
-    load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo, hi);
-    load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo2, hi2);
-    __stcg(ibox + 2 * node, make_float4(fminf(lo[0], lo2[0]), fminf(lo[1], lo2[1]), fminf(lo[2], lo2[2]), 0.f));
-    __stcg(ibox + 2 * node + 1,
-           make_float4(fmaxf(hi[0], hi2[0]), fmaxf(hi[1], hi2[1]), fmaxf(hi[2], hi2[2]), 0.f));
-    node = parent_int[node];
-  }
+// atomicAdd with acquire-release ordering at device scope: the box a thread stored before
+// its update is visible to the thread whose update comes second.
+__device__ inline int atomic_add_acq_rel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
 }
 
-// ---------------------------------------------------------------- 6: traversal nodes
-
-__device__ inline void child_ref(int c, const int* first, const int* last, const float4* leafbox,
-                                 const float4* ibox, int L, int& ref, int& cnt, float lo[3], float hi[3]) {
+// Traversal reference of child c: a leaf range (first triangle, count <= L) or an inner
+// node (index, count 0).
+__device__ inline void child_meta(int c, const int* first, const int* last, int L, int& ref, int& cnt) {
   if (c < 0) {
     ref = ~c;
     cnt = 1;
-    load_box(leafbox + 2 * (int64_t)(~c), lo, hi);
     return;
   }
   int sz = last[c] - first[c] + 1;
-  load_box(ibox + 2 * (int64_t)c, lo, hi);
   if (sz <= L) {
     ref = first[c];
     cnt = sz;
@@ -322,21 +346,37 @@ __device__ inline void child_ref(int c, const int* first, const int* last, const
   }
 }
 
-__global__ void k_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
-                       const float4* leafbox, const float4* ibox, BvhNode* nodes) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n - 1) return;
-  if (last[i] - first[i] + 1 <= L) return;  // inside a leaf range: never visited
-  int r0, c0, r1, c1;
-  float lo0[3], hi0[3], lo1[3], hi1[3];
-  child_ref(left[i], first, last, leafbox, ibox, L, r0, c0, lo0, hi0);
-  child_ref(right[i], first, last, leafbox, ibox, L, r1, c1, lo1, hi1);
-  BvhNode nd;
-  nd.f0 = make_float4(lo0[0], lo0[1], lo0[2], hi0[0]);
-  nd.f1 = make_float4(hi0[1], hi0[2], lo1[0], lo1[1]);
-  nd.f2 = make_float4(lo1[2], hi1[0], hi1[1], hi1[2]);
-  nd.ref = make_int4(r0, r1, c0, c1);
-  nodes[i] = nd;
+// Bottom-up boxes and traversal nodes in one pass: the second child to arrive at a node
+// computes its box and, when the node covers more than L triangles, writes its 64-byte
+// traversal node (both child boxes and references).
+__global__ void k_refit_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
+                             const int* parent_int, const int* parent_leaf, const float4* leafbox, float4* ibox,
+                             int* flags, BvhNode* nodes) {
+  int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (leaf >= n) return;
+  int node = parent_leaf[leaf];
+  while (node >= 0) {
+    if (atomic_add_acq_rel(&flags[node], 1) == 0) return;
+    float lo0[3], hi0[3], lo1[3], hi1[3];
+    int cl = left[node], cr = right[node];
+    load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo0, hi0);
+    load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo1, hi1);
+    __stcg(ibox + 2 * node, make_float4(fminf(lo0[0], lo1[0]), fminf(lo0[1], lo1[1]), fminf(lo0[2], lo1[2]), 0.f));
+    __stcg(ibox + 2 * node + 1,
+           make_float4(fmaxf(hi0[0], hi1[0]), fmaxf(hi0[1], hi1[1]), fmaxf(hi0[2], hi1[2]), 0.f));
+    if (last[node] - first[node] + 1 > L) {
+      int r0, c0, r1, c1;
+      child_meta(cl, first, last, L, r0, c0);
+      child_meta(cr, first, last, L, r1, c1);
+      BvhNode nd;
+      nd.f0 = make_float4(lo0[0], lo0[1], lo0[2], hi0[0]);
+      nd.f1 = make_float4(hi0[1], hi0[2], lo1[0], lo1[1]);
+      nd.f2 = make_float4(lo1[2], hi1[0], hi1[1], hi1[2]);
+      nd.ref = make_int4(r0, r1, c0, c1);
+      nodes[node] = nd;
+    }
+    node = parent_int[node];
+  }
 }
 
 // Root for n <= leaf_size: one node whose first child is the whole range.
@@ -359,9 +399,10 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
 }
 
 template <typename T>
-int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, unsigned* cbox, int* bad,
-                cudaStream_t s) {
-  k_prep<T><<<blocks_for(B->nF, kThreads), kThreads, 0, s>>>((const T*)V, B->nV, F, B->nF, tri_unsorted, cbox, bad);
+int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, float4* cent, unsigned* cbox,
+                int* bad, cudaStream_t s) {
+  k_prep<T><<<blocks_for(B->nF, kThreads), kThreads, 0, s>>>((const T*)V, B->nV, F, B->nF, tri_unsorted, cent, cbox,
+                                                              bad);
   HD_TRY_LAUNCH();
   return HD_OK;
 }
@@ -414,21 +455,25 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   }
 
   // scratch: one block, carved up
-  const int rs_rounds = n < (1 << 20) ? 4 : 16;
+  // radix-sort tiles: 1024 keys for small inputs (more blocks), 4096 above; up to
+  // RS_FUSED_MAX_BLOCKS tiles the digit offsets are computed inside the scatter kernel
+  const int rs_rounds = n <= (int64_t)RS_FUSED_MAX_BLOCKS * RS_THREADS * 4 ? 4 : 16;
   const int64_t rs_tile = (int64_t)RS_THREADS * rs_rounds;
   const int nblk = (int)((n + rs_tile - 1) / rs_tile);
+  const bool fused = nblk <= RS_FUSED_MAX_BLOCKS;
   size_t off = 0;
   auto carve = [&](size_t bytes) {
     size_t at = off;
     off += (bytes + 255) & ~(size_t)255;
     return at;
   };
-  size_t o_tri = carve(sizeof(double) * 9 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
+  size_t o_tri = carve(sizeof(double) * 9 * n), o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
          o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
          o_ibox = carve(32 * n), o_int = carve(4 * 7 * n + 64), o_misc = carve(64);
   char* scratch = nullptr;
   HD_TRY(cudaMallocAsync((void**)&scratch, off, s));
   double* tri_unsorted = (double*)(scratch + o_tri);
+  float4* cent = (float4*)(scratch + o_cent);
   uint64_t* k0 = (uint64_t*)(scratch + o_k0);
   uint64_t* k1 = (uint64_t*)(scratch + o_k1);
   uint32_t* v0 = (uint32_t*)(scratch + o_v0);
@@ -439,27 +484,34 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   int* ints = (int*)(scratch + o_int);
   int *left = ints, *right = ints + n, *first = ints + 2 * n, *last = ints + 3 * n, *pint = ints + 4 * n,
       *pleaf = ints + 5 * n, *flags = ints + 6 * n;
-  unsigned* misc = (unsigned*)(scratch + o_misc);  // [0..5] centroid box, [6] bad, [7] eta bits
+  // [0..5] centroid box (ordered bits: minima start at all ones), [6] bad, [7] squared eta bits
+  unsigned* misc = (unsigned*)(scratch + o_misc);
 
   TraceScope trace_build(HD_K_BUILD, s);  // the whole build counts as one launch
-  unsigned init[8] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0u, 0u, 0u, 0u, 0u};
-  HD_TRY(cudaMemcpyAsync(misc, init, sizeof init, cudaMemcpyHostToDevice, s));
-  int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s)
-                              : launch_prep<float>(B, V, F, tri_unsorted, misc, (int*)(misc + 6), s);
+  HD_TRY(cudaMemsetAsync(misc, 0xff, 3 * sizeof(unsigned), s));
+  HD_TRY(cudaMemsetAsync(misc + 3, 0, 5 * sizeof(unsigned), s));
+  int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, cent, misc, (int*)(misc + 6), s)
+                              : launch_prep<float>(B, V, F, tri_unsorted, cent, misc, (int*)(misc + 6), s);
   if (rc != HD_OK) return rc;
   // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
   // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
   int bits = 10;
   while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
-  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, n, misc, bits, k0, v0);
+  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(cent, n, misc, bits, k0, v0);
   HD_TRY_LAUNCH();
 
   for (int shift = 0; shift < 3 * bits; shift += 8) {
-    if (rs_rounds == 4) k_rs_hist<4><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
-    else k_rs_hist<16><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
-    k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
-    if (rs_rounds == 4) k_rs_scatter<4><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
-    else k_rs_scatter<16><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    if (fused && rs_rounds == 4) {
+      k_rs_hist<4, true><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+      k_rs_scatter<4, true><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    } else if (fused) {
+      k_rs_hist<16, true><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+      k_rs_scatter<16, true><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    } else {
+      k_rs_hist<16, false><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
+      k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
+      k_rs_scatter<16, false><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+    }
     HD_TRY_LAUNCH();
     std::swap(k0, k1);
     std::swap(v0, v1);
@@ -471,9 +523,8 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   if (n > o.leaf_size) {
     HD_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * n, s));
     k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last, pint, pleaf);
-    k_refit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, left, right, pint, pleaf, leafbox, ibox, flags);
-    k_emit<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, leafbox, ibox,
-                                                            h->nodes);
+    k_refit_emit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, pint, pleaf,
+                                                              leafbox, ibox, flags, h->nodes);
   } else {
     k_root_leaf<<<1, 1, 0, s>>>(n, leafbox, h->nodes);
   }
@@ -485,9 +536,13 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   if (Vtmp) HD_TRY(cudaFreeAsync(Vtmp, s));
   if (Ftmp) HD_TRY(cudaFreeAsync(Ftmp, s));
   HD_TRY(cudaStreamSynchronize(s));
-  uint32_t eta_bits = flags_host[1];
-  float eta;
-  memcpy(&eta, &eta_bits, 4);
+  uint32_t e2_bits = flags_host[1];
+  float e2;
+  memcpy(&e2, &e2_bits, 4);
+  // eta = sqrt(e2), rounded up
+  double r = std::sqrt((double)e2) * (1.0 + 1e-15);
+  float eta = (float)r;
+  if ((double)eta < r) eta = std::nextafter(eta, INFINITY);
   h->eta = eta;
   if (flags_host[0]) {
     hd_free_B(h);
