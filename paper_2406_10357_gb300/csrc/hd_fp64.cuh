@@ -231,14 +231,18 @@ __device__ inline double ub_u3(const BvhDev& B, const VI t[3], unsigned long lon
   return fmin(ut, best);
 }
 
-// max over T of d(., {a, b}), attained at a vertex of T or where an edge of T crosses the
-// bisector plane of a and b (Section 3.2.4).
-__device__ inline double h_two_points(const VI t[3], D3 a, D3 b) {
-  double h = 0.0;
+// Squared max over T of d(., {a, b}), attained at a vertex of T or where an edge of T crosses
+// the bisector plane of a and b (Section 3.2.4).  Squared distances throughout: the one square
+// root is taken by ub_u4 (FP64 square roots are costly on GB300, whose FP64 rate is low).
+__device__ inline double h2_two_points(const VI t[3], D3 a, D3 b) {
+  double h2 = 0.0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) h = fmax(h, fmin(len(t[i].v - a), len(t[i].v - b)));
+  for (int i = 0; i < 3; ++i) {
+    D3 ea = t[i].v - a, eb = t[i].v - b;
+    h2 = fmax(h2, fmin(dot(ea, ea), dot(eb, eb)));
+  }
   D3 n = b - a;
-  if (dot(n, n) == 0.0) return h;
+  if (dot(n, n) == 0.0) return h2;
   D3 mid = 0.5 * (a + b);
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
@@ -246,15 +250,17 @@ __device__ inline double h_two_points(const VI t[3], D3 a, D3 b) {
     double c0 = dot(n, x0 - mid), c1 = dot(n, x1 - mid);
     if (((c0 <= 0.0 && c1 >= 0.0) || (c0 >= 0.0 && c1 <= 0.0)) && c0 != c1) {
       D3 x = x0 + (c0 / (c0 - c1)) * (x1 - x0);
-      h = fmax(h, fmin(len(x - a), len(x - b)));
+      D3 ea = x - a, eb = x - b;
+      h2 = fmax(h2, fmin(dot(ea, ea), dot(eb, eb)));
     }
   }
-  return h;
+  return h2;
 }
 
 // Eq. (bound_u4)
 __device__ inline double ub_u4(const VI t[3]) {
-  double l0 = len(t[0].v - t[1].v), l1 = len(t[1].v - t[2].v), l2 = len(t[2].v - t[0].v);
+  D3 e0 = t[0].v - t[1].v, e1 = t[1].v - t[2].v, e2 = t[2].v - t[0].v;
+  double l0 = dot(e0, e0), l1 = dot(e1, e1), l2 = dot(e2, e2);
   int k = 0;
   double m = l0;
   if (l1 < m) { k = 1; m = l1; }
@@ -262,7 +268,7 @@ __device__ inline double ub_u4(const VI t[3]) {
   D3 q2 = t[0].q, q3 = t[1].q, q1 = t[2].q;  // shortest edge v1v2 (k = 0)
   if (k == 1) { q2 = t[1].q; q3 = t[2].q; q1 = t[0].q; }
   else if (k == 2) { q2 = t[2].q; q3 = t[0].q; q1 = t[1].q; }
-  return fmin(h_two_points(t, q1, q2), h_two_points(t, q1, q3));
+  return sqrt(fmin(h2_two_points(t, q1, q2), h2_two_points(t, q1, q3)));
 }
 
 // UpperBound(T, l) of Section 4.

@@ -159,6 +159,38 @@ __device__ inline bool unit_rz(F3& n) {
   return true;
 }
 
+// The FP64 redo of pt_cert for ill-conditioned cases (rare): not inlined, so that its
+// double-precision temporaries do not add to the register budget of the traversal.
+static __device__ __noinline__ void pt_escalate(FFP P, float4 a4, float4 b4, float4 c4, float M, PtOut& o) {
+  D3 p = {(double)P.h.x + (double)P.l.x, (double)P.h.y + (double)P.l.y, (double)P.h.z + (double)P.l.z};
+  D3 a = {a4.x, a4.y, a4.z}, b = {b4.x, b4.y, b4.z}, c = {c4.x, c4.y, c4.z};
+  D3 q = closest_on_triangle(p, a, b, c) - p;  // a point of the triangle, relative to p
+  double d = len(q);
+  // covers the double rounding of these few operations, done in absolute coordinates
+  double m = 1e-12 * ((double)M + d + fmax(fabs(p.x), fmax(fabs(p.y), fabs(p.z)))) + 1e-30;
+  // support-function lower bounds along the closest-point direction and both plane normals:
+  // the first is tight when the nearest point is on an edge or vertex, the others when it
+  // is inside the face
+  D3 Ad = a - p, Bv = b - p, Cv = c - p;
+  auto support = [&](D3 nn) {
+    double s = len(nn);
+    if (!(s > 0.0)) return 0.0;
+    nn = (1.0 / (s * (1.0 + 1e-15))) * nn;
+    return fmin(dot(nn, Ad), fmin(dot(nn, Bv), dot(nn, Cv)));
+  };
+  D3 N = cross(Bv - Ad, Cv - Ad);
+  double lo64 = fmax(support(q), fmax(support(N), support((-1.0) * N))) - m;
+  o.esc = true;
+  o.lo = fmaxf(o.lo, __double2float_rd(fmax(lo64, 0.0)));
+  float hi64 = __double2float_ru(d + m);
+  if (hi64 < o.hi) {
+    o.hi = hi64;
+    o.q = {(float)q.x, (float)q.y, (float)q.z};
+    // float rounding of q plus the double margin
+    o.qerr = __double2float_ru(3e-7 * (fabs(q.x) + fabs(q.y) + fabs(q.z)) + m);
+  }
+}
+
 // Certified distance from p = h + l to the float triangle (a, b, c).
 __device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bool want_lo, PtOut& o) {
   F3 A = local_off(a4, P), B = local_off(b4, P), C = local_off(c4, P);
@@ -191,35 +223,7 @@ __device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bo
   if (unit_rz(n)) lo = fmaxf(__fsub_rd(support_rd(n, A, B, C), __fmul_ru(6.f * kU, M)), 0.f);
   o.lo = lo;
   // a loose certificate means the classification was ill-conditioned: redo in FP64
-  if (__fsub_rd(nq, lo) > __fmul_ru(256.f * kU, M)) {
-    D3 p = {(double)P.h.x + (double)P.l.x, (double)P.h.y + (double)P.l.y, (double)P.h.z + (double)P.l.z};
-    D3 a = {a4.x, a4.y, a4.z}, b = {b4.x, b4.y, b4.z}, c = {c4.x, c4.y, c4.z};
-    D3 q = closest_on_triangle(p, a, b, c) - p;  // a point of the triangle, relative to p
-    double d = len(q);
-    // covers the double rounding of these few operations, done in absolute coordinates
-    double m = 1e-12 * ((double)M + d + fmax(fabs(p.x), fmax(fabs(p.y), fabs(p.z)))) + 1e-30;
-    // support-function lower bounds along the closest-point direction and both plane normals:
-    // the first is tight when the nearest point is on an edge or vertex, the others when it
-    // is inside the face
-    D3 Ad = a - p, Bv = b - p, Cv = c - p;
-    auto support = [&](D3 nn) {
-      double s = len(nn);
-      if (!(s > 0.0)) return 0.0;
-      nn = (1.0 / (s * (1.0 + 1e-15))) * nn;
-      return fmin(dot(nn, Ad), fmin(dot(nn, Bv), dot(nn, Cv)));
-    };
-    D3 N = cross(Bv - Ad, Cv - Ad);
-    double lo64 = fmax(support(q), fmax(support(N), support((-1.0) * N))) - m;
-    o.esc = true;
-    o.lo = fmaxf(o.lo, __double2float_rd(fmax(lo64, 0.0)));
-    float hi64 = __double2float_ru(d + m);
-    if (hi64 < o.hi) {
-      o.hi = hi64;
-      o.q = {(float)q.x, (float)q.y, (float)q.z};
-      // float rounding of q plus the double margin
-      o.qerr = __double2float_ru(3e-7 * (fabs(q.x) + fabs(q.y) + fabs(q.z)) + m);
-    }
-  }
+  if (__fsub_rd(nq, lo) > __fmul_ru(256.f * kU, M)) pt_escalate(P, a4, b4, c4, M, o);
 }
 
 // Lower bound of |p - box|^2 (downward rounding).
