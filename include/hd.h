@@ -74,7 +74,14 @@ typedef struct {
   int32_t n_bounds;        /* how many entries of bound_order are used, 1..4 (default 4)  */
   int64_t max_rounds;      /* frontier rounds before HD_ERR_TIMEOUT (default 1e6)         */
   int64_t max_frontier_bytes; /* device memory for frontier + vertex pool (0 = automatic) */
+  int32_t flags;           /* HD_FLAG_* bits (default 0)                                  */
+  int32_t reserved;        /* must be 0                                                   */
 } hd_options;
+
+/* hd_options.flags.  By default the UpperBound of a child sub-triangle is clamped to its
+ * parent's: h(child, B) <= h(parent, B) <= U(parent) since the child lies inside the parent.
+ * The paper's cascade (Section 4) has no such clamp; HD_FLAG_NO_PARENT_CLAMP turns it off. */
+enum { HD_FLAG_NO_PARENT_CLAMP = 1 };
 
 typedef struct {
   int64_t rounds;            /* frontier rounds after round 0                              */

@@ -19,6 +19,7 @@ HD_OK, HD_ERR_INVALID, HD_ERR_CAPACITY, HD_ERR_NUMERIC, HD_ERR_TIMEOUT, HD_ERR_C
 HD_F32, HD_F64 = 0, 1
 HD_TOL_ABS, HD_TOL_REL = 0, 1
 HD_FP64, HD_MIXED = 0, 1
+HD_FLAG_NO_PARENT_CLAMP = 1
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 
@@ -31,7 +32,7 @@ class HdOptions(C.Structure):
     _fields_ = [("tol_mode", C.c_int32), ("precision", C.c_int32), ("max_face_factor", C.c_double),
                 ("frontier_chunk", C.c_int64), ("leaf_size", C.c_int32), ("block_size", C.c_int32),
                 ("bound_order", C.c_uint8 * 4), ("n_bounds", C.c_int32), ("max_rounds", C.c_int64),
-                ("max_frontier_bytes", C.c_int64)]
+                ("max_frontier_bytes", C.c_int64), ("flags", C.c_int32), ("reserved", C.c_int32)]
 
 
 class HdStats(C.Structure):

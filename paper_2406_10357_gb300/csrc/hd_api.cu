@@ -92,6 +92,8 @@ int resolve_options(const hd_options* in, Opts* o) {
   o->max_rounds = x.max_rounds;
   o->max_frontier_bytes = x.max_frontier_bytes;
   memcpy(o->order, x.bound_order, 4);
+  o->flags = x.flags;
+  if (x.reserved != 0 || (o->flags & ~(int)HD_FLAG_NO_PARENT_CLAMP)) return HD_ERR_INVALID;
   if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
   if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
   if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;
@@ -332,6 +334,7 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
   rp.slack = 0.0;
   rp.slack_f = 0.f;
   rp.defer_u4 = 0;
+  rp.parent_clamp = 0;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   cudaStream_t s = (cudaStream_t)stream;

@@ -340,7 +340,8 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
       } else {
         int s = warp_slot(&st->n_split);
         if (s < K) {
-          split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], 0);
+          // the parent's U, rounded up to float, for the children's clamp
+          split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], __float_as_int(__double2float_ru(U)));
           P::midpoint(a, b, m);
           pool[mbase + 3 * s] = m;
           P::midpoint(b, c, m);
@@ -388,6 +389,9 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
       it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
+      // the child lies inside its parent: h(child, B) <= U(parent)
+      const typename P::UT Up = (typename P::UT)__int_as_float(par.w);
+      if (rp.parent_clamp && Up < it.U) it.U = Up;
       classify<P>(st, it, th, code, next, next_cap, u4list, ty);
     }
   }
@@ -695,6 +699,7 @@ int run_bnb(const RunIO& io) {
   rp.slack_f = 0.f;
   rp.dyn = dyn;
   rp.defer_u4 = P::kFp64 ? 0 : 1;
+  rp.parent_clamp = (o.flags & HD_FLAG_NO_PARENT_CLAMP) ? 0 : 1;
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   const int bs = o.block_size;

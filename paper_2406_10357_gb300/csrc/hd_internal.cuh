@@ -138,6 +138,7 @@ struct RunParams {
   int n_bounds;
   float slack_f;  // slack rounded up to float
   int defer_u4;   // MIXED: a trailing u4 is evaluated in the separate u4 pass
+  int parent_clamp;  // children's U is clamped to their parent's U
   const DynParams* dyn;  // if set, eps / slack / slack_f are taken from here on the device
 };
 
@@ -278,7 +279,7 @@ inline unsigned blocks_for(int64_t n, int threads) {
 
 // Options after defaults and validation.
 struct Opts {
-  int tol_mode, precision, leaf_size, block_size, n_bounds;
+  int tol_mode, precision, leaf_size, block_size, n_bounds, flags;
   double max_face_factor;
   int64_t frontier_chunk, max_rounds, max_frontier_bytes;
   uint8_t order[4];

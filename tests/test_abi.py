@@ -4,6 +4,7 @@ import ctypes as C
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -26,6 +27,15 @@ def declared_symbols():
     return sorted(set(re.findall(r"\b(hd_[A-Za-z_0-9]+)\s*\(", text)))
 
 
+def _has_gpu():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
 def test_every_declared_symbol_is_exported(hd):
     names = declared_symbols()
     assert {"hd_build_B", "hd_hausdorff", "hd_hausdorff_batched", "hd_free_B", "hd_status_str"} <= set(names)
@@ -37,7 +47,7 @@ def test_every_declared_symbol_is_exported(hd):
 def test_struct_layouts_match_header(hd):
     # sizes of the ABI structs as laid out by a C compiler for this header
     assert C.sizeof(hd.HdMesh) == 40
-    assert C.sizeof(hd.HdOptions) == 56
+    assert C.sizeof(hd.HdOptions) == 64
     assert C.sizeof(hd.HdStats) == 8 * 18
     assert C.sizeof(hd.HdResult) == 24 + 8 * 18
     assert C.sizeof(hd.HdTrace) == 128
@@ -62,3 +72,14 @@ def test_invalid_arguments_rejected_before_any_launch(hd):
     assert L.hd_build_B(C.byref(m), None, None, C.byref(out)) == hd.HD_ERR_INVALID
     bad = hd.hd_options_default(leaf_size=40)
     assert L.hd_build_B(C.byref(m), C.byref(bad), None, C.byref(out)) == hd.HD_ERR_INVALID
+    # a valid host mesh: unknown flag bits or a nonzero reserved field are rejected before
+    # any CUDA call (a good option set gets past validation)
+    V = np.zeros((3, 3), np.float64)
+    V[1, 0] = V[2, 1] = 1.0
+    Fi = np.array([[0, 1, 2]], np.int32)
+    mv = hd.HdMesh(V.ctypes.data, 3, Fi.ctypes.data, 1, hd.HD_F64, 0)
+    for b in (hd.hd_options_default(flags=4), hd.hd_options_default(reserved=1)):
+        assert L.hd_build_B(C.byref(mv), C.byref(b), None, C.byref(out)) == hd.HD_ERR_INVALID
+    if not _has_gpu():
+        good = hd.hd_options_default(flags=hd.HD_FLAG_NO_PARENT_CLAMP)
+        assert L.hd_build_B(C.byref(mv), C.byref(good), None, C.byref(out)) == hd.HD_ERR_CUDA

@@ -164,6 +164,19 @@ def test_bracket_reduced_workloads_fp64(hd, orc, k, scale):
     _bracket_parity(hd, orc, mg.workload(k, scale), tight=(k != 3))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_parent_clamp_on_and_off(hd, orc, precision):
+    """Clamping a child's U to its parent's is sound (the child lies inside the parent): with
+    and without it the bracket is within eps and meets the oracle's."""
+    p = mg.workload(1)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    on = _bracket_parity(hd, orc, p, opt=hd.hd_options_default(tol_mode=p.tol_mode, precision=prec))[0]
+    off = _bracket_parity(hd, orc, p, opt=hd.hd_options_default(tol_mode=p.tol_mode, precision=prec,
+                                                                  flags=hd.HD_FLAG_NO_PARENT_CLAMP))[0]
+    assert on["stats"]["splits"] > 0 and off["stats"]["splits"] > 0
+    assert max(on["lower"], off["lower"]) <= min(on["upper"], off["upper"]) + 1e-12
+
+
 def test_bracket_all_bound_orders_fp64(hd, orc):
     import itertools
 
