@@ -138,6 +138,18 @@ int64_t hd_bvh_num_faces(const hd_bvh* bvh);
 int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
                  hd_result* out);
 
+/* Two-sided H(A, B) = max(h(A, B), h(B, A)) (Section 6, conclusion and future work):
+ * h(A, B) as hd_hausdorff (bvhB is B's BVH), then h(B, A) through A's BVH (bvhA) at the
+ * same absolute tolerance, with l starting from h(A, B)'s final lower bound, as the paper
+ * suggests: sub-triangles of B bounded below that value are discarded at once.  *out gets
+ * the bracket of H (lower = max of the lowers, upper = max of the uppers) and the summed
+ * statistics; ab and ba (either may be NULL) get the two runs.  ba brackets
+ * max(l_AB, h(B, A)), which is all H needs; it is not h(B, A) itself when h(B, A) is the
+ * smaller side.  tol follows opt->tol_mode for the first run (HD_TOL_REL: tol times A's
+ * bbox diagonal).  Returns the first error of the two runs. */
+int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, const hd_mesh* B, double tol,
+                     const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba);
+
 /* npairs independent problems h(As[i], Bs[i]) with one tolerance; outs[i] receives each
  * result.  The pairs share the stream and the device.  Returns the first non-OK status
  * (HD_ERR_INVALID/HD_ERR_CUDA abort; per-pair CAPACITY/TIMEOUT/NUMERIC are reported in

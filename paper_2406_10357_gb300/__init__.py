@@ -75,6 +75,8 @@ def lib():
         L.hd_hausdorff.argtypes = [vp, C.POINTER(HdMesh), d, C.POINTER(HdOptions), vp, C.POINTER(HdResult)]
         L.hd_hausdorff_batched.argtypes = [C.POINTER(vp), C.POINTER(HdMesh), i64, d, C.POINTER(HdOptions), vp,
                                            C.POINTER(HdResult)]
+        L.hd_hausdorff_sym.argtypes = [vp, C.POINTER(HdMesh), vp, C.POINTER(HdMesh), d, C.POINTER(HdOptions), vp,
+                                       C.POINTER(HdResult), C.POINTER(HdResult), C.POINTER(HdResult)]
         L.hd_nearest.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
         L.hd_upper_bounds.argtypes = [vp, vp, vp, vp, vp, i64, d, C.POINTER(HdOptions), vp, vp, vp]
         L.hd_nearest_noalloc.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
@@ -219,6 +221,20 @@ def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, str
     if rc in (HD_ERR_INVALID, HD_ERR_CUDA):
         raise HdError(rc, "hd_hausdorff")
     return _result(r)
+
+
+def hd_hausdorff_sym(bvhB: Bvh, VA, FA, bvhA: Bvh, VB, FB, tol: float, opt: HdOptions | None = None,
+                     stream=None) -> tuple[dict, dict, dict]:
+    """Two-sided H(A, B): (H bracket, h(A, B) run, h(B, A) run warm-started from it)."""
+    mA, keepA, devA = _mesh(VA, FA)
+    mB, keepB, devB = _mesh(VB, FB)
+    r, rab, rba = HdResult(), HdResult(), HdResult()
+    rc = lib().hd_hausdorff_sym(bvhB.handle, C.byref(mA), bvhA.handle, C.byref(mB), float(tol),
+                                C.byref(opt) if opt else None, _stream(devA or devB, stream), C.byref(r),
+                                C.byref(rab), C.byref(rba))
+    if rc in (HD_ERR_INVALID, HD_ERR_CUDA):
+        raise HdError(rc, "hd_hausdorff_sym")
+    return _result(r), _result(rab), _result(rba)
 
 
 def hd_hausdorff_batched(bvhs, As, tol: float, opt: HdOptions | None = None, stream=None) -> list[dict]:

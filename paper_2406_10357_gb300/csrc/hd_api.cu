@@ -129,7 +129,8 @@ static void keep_pool_memory() {
   }
 }
 
-int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale) {
+int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale,
+              RunState* st) {
   cudaStream_t s = io.s;
   HD_TRY(cudaMemsetAsync(box, 0xff, 3 * sizeof(unsigned long long), s));  // ordered minima start high
   HD_TRY(cudaMemsetAsync(box + 3, 0, 5 * sizeof(unsigned long long), s));  // maxima low, flag clear
@@ -142,7 +143,7 @@ int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams*
       k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
     else
       k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
-    k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn);
+    k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0);
   }
   HD_TRY_LAUNCH();
   return HD_OK;
@@ -183,6 +184,44 @@ __global__ void k_upper_bounds(BvhDev B, const int* inv, const double* T, const 
 }  // namespace hd
 
 using namespace hd;
+
+// One-sided h(A, B) with l starting at l0 (a known lower bound of the quantity bracketed).
+static int hausdorff_one(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
+                         hd_result* out, double l0) {
+  if (!out) return HD_ERR_INVALID;
+  memset(out, 0, sizeof *out);
+  out->status = HD_ERR_INVALID;
+  Opts o;
+  if (!B || !(tol > 0.0) || !(l0 >= 0.0) || resolve_options(opt, &o) != HD_OK || check_mesh(A) != HD_OK)
+    return HD_ERR_INVALID;
+  int dev = -1;
+  HD_TRY(cudaGetDevice(&dev));
+  if (dev != B->device) return HD_ERR_INVALID;
+  keep_pool_memory();
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t vbytes = (size_t)A->nV * 3 * (A->vtype == HD_F64 ? 8 : 4);
+  const void* VA = A->V;
+  const int32_t* FA = A->F;
+  void* Vtmp = nullptr;
+  int32_t* Ftmp = nullptr;
+  if (!A->on_device) {
+    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, s));
+    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)A->nF * 12, s));
+    HD_TRY(cudaMemcpyAsync(Vtmp, A->V, vbytes, cudaMemcpyHostToDevice, s));
+    HD_TRY(cudaMemcpyAsync(Ftmp, A->F, (size_t)A->nF * 12, cudaMemcpyHostToDevice, s));
+    VA = Vtmp;
+    FA = Ftmp;
+  }
+  RunIO io{B, VA, A->vtype, A->nV, FA, A->nF, tol, &o, s, out, l0};
+  int rc = o.precision == HD_FP64 ? run_fp64(io) : run_mixed(io);
+  if (Vtmp) cudaFreeAsync(Vtmp, s);
+  if (Ftmp) cudaFreeAsync(Ftmp, s);
+  if (rc != HD_OK) {
+    out->status = rc;
+    return rc;
+  }
+  return HD_OK;
+}
 
 extern "C" {
 
@@ -268,37 +307,45 @@ int64_t hd_bvh_num_faces(const hd_bvh* b) { return b ? b->nF : 0; }
 
 int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
                  hd_result* out) {
+  return hausdorff_one(B, A, tol, opt, stream, out, 0.0);
+}
+
+int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, const hd_mesh* B, double tol,
+                     const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba) {
   if (!out) return HD_ERR_INVALID;
   memset(out, 0, sizeof *out);
   out->status = HD_ERR_INVALID;
-  Opts o;
-  if (!B || !(tol > 0.0) || resolve_options(opt, &o) != HD_OK || check_mesh(A) != HD_OK) return HD_ERR_INVALID;
-  int dev = -1;
-  HD_TRY(cudaGetDevice(&dev));
-  if (dev != B->device) return HD_ERR_INVALID;
-  keep_pool_memory();
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t vbytes = (size_t)A->nV * 3 * (A->vtype == HD_F64 ? 8 : 4);
-  const void* VA = A->V;
-  const int32_t* FA = A->F;
-  void* Vtmp = nullptr;
-  int32_t* Ftmp = nullptr;
-  if (!A->on_device) {
-    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, s));
-    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)A->nF * 12, s));
-    HD_TRY(cudaMemcpyAsync(Vtmp, A->V, vbytes, cudaMemcpyHostToDevice, s));
-    HD_TRY(cudaMemcpyAsync(Ftmp, A->F, (size_t)A->nF * 12, cudaMemcpyHostToDevice, s));
-    VA = Vtmp;
-    FA = Ftmp;
-  }
-  RunIO io{B, VA, A->vtype, A->nV, FA, A->nF, tol, &o, s, out};
-  int rc = o.precision == HD_FP64 ? run_fp64(io) : run_mixed(io);
-  if (Vtmp) cudaFreeAsync(Vtmp, s);
-  if (Ftmp) cudaFreeAsync(Ftmp, s);
-  if (rc != HD_OK) {
-    out->status = rc;
-    return rc;
-  }
+  hd_result rab, rba;
+  int rc = hausdorff_one(bvhB, A, tol, opt, stream, &rab, 0.0);
+  if (ab) *ab = rab;
+  if (rc != HD_OK) return rc;
+  // h(B, A) at the same absolute tolerance, with l starting from h(A, B)'s lower bound: a
+  // sub-triangle of B whose U is below it cannot raise H = max(h(A, B), h(B, A))
+  hd_options o2;
+  if (opt) o2 = *opt;
+  else hd_options_default(&o2);
+  o2.tol_mode = HD_TOL_ABS;
+  rc = hausdorff_one(bvhA, B, rab.stats.eps_abs, &o2, stream, &rba, rab.lower);
+  if (ba) *ba = rba;
+  if (rc != HD_OK) return rc;
+  out->lower = std::max(rab.lower, rba.lower);
+  out->upper = std::max(rab.upper, rba.upper);
+  out->status = rab.status != HD_OK ? rab.status : rba.status;
+  hd_stats& S = out->stats;
+  const hd_stats &X = rab.stats, &Y = rba.stats;
+  S.rounds = X.rounds + Y.rounds;
+  S.splits = X.splits + Y.splits;
+  S.queries = X.queries + Y.queries;
+  S.pointtri_evals = X.pointtri_evals + Y.pointtri_evals;
+  S.leaf_tests = X.leaf_tests + Y.leaf_tests;
+  S.box_tests = X.box_tests + Y.box_tests;
+  for (int k = 0; k < 6; ++k) S.discards[k] = X.discards[k] + Y.discards[k];
+  S.retired = X.retired + Y.retired;
+  S.fp64_escalations = X.fp64_escalations + Y.fp64_escalations;
+  S.peak_frontier = std::max(X.peak_frontier, Y.peak_frontier);
+  S.pool_vertices = X.pool_vertices + Y.pool_vertices;
+  S.eps_abs = X.eps_abs;
+  S.dA = X.dA;
   return HD_OK;
 }
 

@@ -104,7 +104,8 @@ __device__ inline double ordered_to_double(unsigned long long u) {
 
 // dA, eps and the slack from A's bounding box, on the device (one thread).
 static __global__ void k_prep_finish(const unsigned long long* box, double tol, int tol_rel, double slack_scale,
-                                     DynParams* dyn) {
+                                     DynParams* dyn, RunState* st, double l0) {
+  if (l0 > 0.0) st->l_bits = (unsigned long long)__double_as_longlong(l0);  // warm start of l
   double v[6];
   for (int k = 0; k < 6; ++k) v[k] = ordered_to_double(box[k]);
   double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
@@ -436,6 +437,7 @@ struct RunIO {
   const Opts* o;
   cudaStream_t s;
   hd_result* out;
+  double l0;  // a known lower bound to start l from (0: none)
 };
 
 inline BvhDev bvh_dev(const hd_bvh* B) { return {B->nodes, B->tri32, B->tri64, B->tri_vid, B->nF, B->eta}; }
@@ -448,7 +450,8 @@ inline double bits_to_double(unsigned long long b) {
 
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
 // Enqueues the validation of A, its bounding box and the device-side parameters (no sync).
-int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale);
+int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale,
+              RunState* st);
 
 // Buffers of one policy's frontier loop.
 template <class P>
@@ -678,7 +681,7 @@ int run_bnb(const RunIO& io) {
   RunState* st = (RunState*)(small + ref_bytes + 512);
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
   // validation of A and its bbox run asynchronously; the host reads the result with round 0
-  int rc = prepare_A(io, ref, box, dyn, P::slack(1.0));
+  int rc = prepare_A(io, ref, box, dyn, P::slack(1.0), st);
   if (rc != HD_OK) {
     cudaFreeAsync(small, s);
     return rc;
@@ -769,7 +772,9 @@ int run_bnb(const RunIO& io) {
   if (status == HD_OK) {
     // frontier empty: everything was discarded or retired
     T.u_run = std::min(T.u_run, std::max(l, uret));
-    if (P::kFp64 && uret < l) status = HD_ERR_NUMERIC;
+    // in exact arithmetic the sub-triangle holding the farthest point of A is never
+    // discarded, so some retired U is >= h >= l -- unless l was warm-started above h
+    if (P::kFp64 && uret < l && !(io.l0 > 0.0)) status = HD_ERR_NUMERIC;
   }
   res.lower = l;
   res.upper = std::max(l, T.u_run);

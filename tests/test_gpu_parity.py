@@ -165,6 +165,29 @@ def test_bracket_reduced_workloads_fp64(hd, orc, k, scale):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("k,scale", [(1, 1.0), (2, 0.02), (5, 0.005)])
+def test_two_sided_matches_oracle(hd, orc, precision, k, scale):
+    """H(A, B) = max(h(A, B), h(B, A)) with the second run's l warm-started from the first's
+    lower bound: the bracket is within eps and meets the one the oracle gets from two
+    independent one-sided runs."""
+    p = mg.workload(k, scale)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    bvhB, bvhA = hd.hd_build_B(p.VB, p.FB), hd.hd_build_B(p.VA, p.FA)
+    H, ab, ba = hd.hd_hausdorff_sym(bvhB, p.VA, p.FA, bvhA, p.VB, p.FB, p.tol,
+                                    hd.hd_options_default(tol_mode=p.tol_mode, precision=prec))
+    eps = p.tol * (_dA(p.VA, p.FA) if p.tol_mode else 1.0)
+    o_ab = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, eps, 0)
+    o_ba = orc.hausdorff(p.VB, p.FB, p.VA, p.FA, eps, 0)
+    Ho = (max(o_ab["lower"], o_ba["lower"]), max(o_ab["upper"], o_ba["upper"]))
+    assert H["status"] == hd.HD_OK, H
+    assert H["upper"] - H["lower"] <= eps * (1 + 1e-12)
+    assert max(H["lower"], Ho[0]) <= min(H["upper"], Ho[1]) + 1e-12 * eps
+    assert abs(ab["stats"]["eps_abs"] - eps) <= 1e-9 * eps and abs(ba["stats"]["eps_abs"] - eps) <= 1e-9 * eps
+    assert ba["lower"] >= ab["lower"]  # warm start: l never starts below h(A, B)'s lower bound
+    assert H["lower"] == max(ab["lower"], ba["lower"]) and H["upper"] == max(ab["upper"], ba["upper"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parent_clamp_on_and_off(hd, orc, precision):
     """Clamping a child's U to its parent's is sound (the child lies inside the parent): with
     and without it the bracket is within eps and meets the oracle's."""
