@@ -150,10 +150,13 @@ int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options
 int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, const hd_mesh* B, double tol,
                      const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba);
 
-/* npairs independent problems h(As[i], Bs[i]) with one tolerance; outs[i] receives each
- * result.  The pairs share the stream and the device.  Returns the first non-OK status
- * (HD_ERR_INVALID/HD_ERR_CUDA abort; per-pair CAPACITY/TIMEOUT/NUMERIC are reported in
- * outs[i].status and the call still returns HD_OK). */
+/* npairs independent problems h(As[i], Bs[i]) with one tolerance and one option set;
+ * outs[i] receives each result.  Up to 8 host threads, each with its own non-blocking
+ * stream on the current device, take the pairs in turn, so that the kernels of several
+ * small pairs run on the GPU at the same time; they start after the work already queued on
+ * `stream`, and every pair is complete when the call returns.  All Bs[i] must live on the
+ * current device.  Returns HD_ERR_INVALID (nothing launched) or the first HD_ERR_CUDA, else
+ * HD_OK; per-pair CAPACITY/TIMEOUT/NUMERIC are reported in outs[i].status. */
 int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
                          const hd_options* opt, void* stream, hd_result* outs);
 

@@ -1,8 +1,11 @@
 // The C ABI of include/hd.h: options, validation, dispatch to the FP64 or certified FP32
 // branch-and-bound, and the step-level entry points used for parity checks.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "hd_bnb.cuh"
@@ -352,9 +355,68 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
 int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
                          const hd_options* opt, void* stream, hd_result* outs) {
   if (!Bs || !As || !outs || npairs < 0) return HD_ERR_INVALID;
-  for (int64_t i = 0; i < npairs; ++i) {
-    int rc = hd_hausdorff(Bs[i], &As[i], tol, opt, stream, &outs[i]);
-    if (rc == HD_ERR_INVALID || rc == HD_ERR_CUDA) return rc;
+  if (npairs == 0) return HD_OK;
+  Opts o;
+  if (!(tol > 0.0) || resolve_options(opt, &o) != HD_OK) return HD_ERR_INVALID;
+  int dev = -1;
+  HD_TRY(cudaGetDevice(&dev));
+  for (int64_t i = 0; i < npairs; ++i)
+    if (!Bs[i] || Bs[i]->device != dev || check_mesh(&As[i]) != HD_OK) return HD_ERR_INVALID;
+  // Pairs are independent: kBatchStreams host threads, each with its own non-blocking
+  // stream, take pairs in turn, so that the kernels of several small pairs share the GPU.
+  // The streams start after the work queued so far on the caller's stream; every pair is
+  // complete when the call returns.
+  constexpr int kBatchStreams = 8;
+  const int nw = (int)std::min<int64_t>(npairs, kBatchStreams);
+  cudaEvent_t start;
+  HD_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(start, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(start);
+    return set_cuda_error(e, "cudaEventRecord", __FILE__, __LINE__);
+  }
+  std::atomic<int64_t> next{0};
+  std::atomic<int> fail{HD_OK};
+  std::mutex em;
+  std::string first_err;
+  auto work = [&]() {
+    cudaStream_t s = nullptr;
+    cudaError_t err = cudaSetDevice(dev);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, start, 0);
+    if (err != cudaSuccess) {
+      set_cuda_error(err, "batch stream set-up", __FILE__, __LINE__);
+      int ok = HD_OK;
+      if (fail.compare_exchange_strong(ok, HD_ERR_CUDA)) {
+        std::lock_guard<std::mutex> g(em);
+        first_err = g_err;
+      }
+    }
+    while (err == cudaSuccess && fail.load() == HD_OK) {
+      int64_t i = next.fetch_add(1);
+      if (i >= npairs) break;
+      int rc = hausdorff_one(Bs[i], &As[i], tol, opt, s, &outs[i], 0.0);
+      if (rc == HD_ERR_INVALID || rc == HD_ERR_CUDA) {
+        int ok = HD_OK;
+        if (fail.compare_exchange_strong(ok, rc)) {
+          std::lock_guard<std::mutex> g(em);
+          first_err = g_err;
+        }
+      }
+    }
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nw; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  cudaEventDestroy(start);
+  if (fail.load() != HD_OK) {
+    snprintf(g_err, sizeof g_err, "%s", first_err.c_str());
+    return fail.load();
   }
   return HD_OK;
 }

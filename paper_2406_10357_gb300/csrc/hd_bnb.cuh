@@ -667,8 +667,16 @@ int run_bnb(const RunIO& io) {
     DynParams dyn;
     unsigned long long bad;
   };
-  static thread_local HostBlock* hb = nullptr;  // pinned read-back buffer, kept for the thread's lifetime
-  if (!hb) HD_TRY(cudaMallocHost((void**)&hb, sizeof(HostBlock)));
+  // pinned read-back buffer, kept for the thread's lifetime and released when it exits
+  struct Holder {
+    HostBlock* p = nullptr;
+    ~Holder() {
+      if (p) cudaFreeHost(p);
+    }
+  };
+  static thread_local Holder holder;
+  if (!holder.p) HD_TRY(cudaMallocHost((void**)&holder.p, sizeof(HostBlock)));
+  HostBlock* hb = holder.p;
 
   // small per-call device block: referenced-vertex flags, A's bbox + invalid flag, the
   // device-side parameters, and the run state

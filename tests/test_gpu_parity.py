@@ -188,6 +188,37 @@ def test_two_sided_matches_oracle(hd, orc, precision, k, scale):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_pairs_match_oracle(hd, orc, precision):
+    """Workload 4's generator at reduced sizes: every pair of the concurrent batched call is
+    within eps and meets the oracle's bracket, and agrees with the same pair run alone."""
+    pairs = mg.batch_workload(n_pairs=12, lo=300, hi=3000)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=prec)
+    bvhs = [hd.hd_build_B(p.VB, p.FB) for p in pairs]
+    rs = hd.hd_hausdorff_batched(bvhs, [(p.VA, p.FA) for p in pairs], pairs[0].tol, o)
+    assert len(rs) == len(pairs)
+    for p, b, r in zip(pairs, bvhs, rs):
+        assert p.tol == pairs[0].tol and p.tol_mode == hd.HD_TOL_REL
+        eps = p.tol * _dA(p.VA, p.FA)
+        ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+        assert r["status"] == hd.HD_OK, (p.name, r)
+        assert r["upper"] - r["lower"] <= eps * (1 + 1e-12), p.name
+        assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + 1e-12 * eps, p.name
+        r1 = hd.hd_hausdorff(b, p.VA, p.FA, p.tol, o)
+        assert max(r["lower"], r1["lower"]) <= min(r["upper"], r1["upper"]) + 1e-12 * eps, p.name
+
+
+def test_batched_invalid_pair_is_reported(hd):
+    p = mg.workload(1)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    bad = np.array(p.FA, copy=True)
+    bad[0, 0] = len(p.VA) + 5
+    with pytest.raises(hd.HdError):
+        hd.hd_hausdorff_batched([bvh, bvh], [(p.VA, p.FA), (p.VA, bad)], 1e-4,
+                                hd.hd_options_default(tol_mode=hd.HD_TOL_ABS))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parent_clamp_on_and_off(hd, orc, precision):
     """Clamping a child's U to its parent's is sound (the child lies inside the parent): with
     and without it the bracket is within eps and meets the oracle's."""
