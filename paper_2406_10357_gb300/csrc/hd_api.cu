@@ -132,26 +132,6 @@ static void keep_pool_memory() {
   }
 }
 
-int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale,
-              RunState* st) {
-  cudaStream_t s = io.s;
-  HD_TRY(cudaMemsetAsync(box, 0xff, 3 * sizeof(unsigned long long), s));  // ordered minima start high
-  HD_TRY(cudaMemsetAsync(box + 3, 0, 5 * sizeof(unsigned long long), s));  // maxima low, flag clear
-  HD_TRY(cudaMemsetAsync(ref, 0, io.nVA, s));
-  int* bad = (int*)(box + 6);
-  {
-    TraceScope tr(HD_K_PREP, s);
-    k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
-    if (io.vtype == HD_F64)
-      k_check_bbox<double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad);
-    else
-      k_check_bbox<float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad);
-    k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0);
-  }
-  HD_TRY_LAUNCH();
-  return HD_OK;
-}
-
 int run_fp64(const RunIO& io) { return run_bnb<PolicyD>(io); }
 int run_mixed(const RunIO& io);
 

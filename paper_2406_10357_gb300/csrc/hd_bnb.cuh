@@ -67,33 +67,51 @@ __device__ inline unsigned long long double_to_ordered(double d) {
   return (u >> 63) ? ~u : (u | (1ull << 63));
 }
 
-// Finite coordinates everywhere, and the bounding box of the referenced vertices.
-template <typename T>
-static __global__ void k_check_bbox(const T* VA, int64_t nVA, const uint8_t* ref, unsigned long long* box, int* bad) {
+// Finite coordinates everywhere, the bounding box of the referenced vertices, and the pool
+// entries of A's vertices (round 0).  The box is kept as six maxima of ordered bits -- the
+// minima as complements -- so that a zero-filled block is its starting value; one atomic
+// per block and bound.  Launched with 256 threads per block.
+template <class P, typename T>
+__global__ void k_check_init(const T* VA, int64_t nVA, const uint8_t* ref, unsigned long long* box, int* bad,
+                             typename P::Vtx* pool) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  unsigned long long lo[3] = {~0ull, ~0ull, ~0ull}, hi[3] = {0, 0, 0};
+  unsigned long long m[6] = {0, 0, 0, 0, 0, 0};  // ~lo xyz, hi xyz
   if (i < nVA) {
     double x = VA[3 * i], y = VA[3 * i + 1], z = VA[3 * i + 2];
+    const bool used = ref[i] != 0;
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
       atomicExch(bad, 1);
-    } else if (ref[i]) {
-      lo[0] = hi[0] = double_to_ordered(x);
-      lo[1] = hi[1] = double_to_ordered(y);
-      lo[2] = hi[2] = double_to_ordered(z);
+      x = y = z = 0.0;
+    } else if (used) {
+      m[3] = double_to_ordered(x);
+      m[4] = double_to_ordered(y);
+      m[5] = double_to_ordered(z);
+      m[0] = ~m[3];
+      m[1] = ~m[4];
+      m[2] = ~m[5];
     }
+    typename P::Vtx v;
+    memset(&v, 0, sizeof v);
+    P::set_pos(v, x, y, z);
+    v.tri = used ? -2 : -1;
+    v.hint = -1;
+    pool[i] = v;
   }
-  // warp reduction first: one atomic per warp and bound instead of one per vertex
-  for (int k = 0; k < 3; ++k)
+  __shared__ unsigned long long part[6][8];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
     for (int o = 16; o > 0; o >>= 1) {
-      unsigned long long a = __shfl_xor_sync(0xffffffffu, lo[k], o), b = __shfl_xor_sync(0xffffffffu, hi[k], o);
-      lo[k] = a < lo[k] ? a : lo[k];
-      hi[k] = b > hi[k] ? b : hi[k];
+      unsigned long long a = __shfl_xor_sync(0xffffffffu, m[k], o);
+      m[k] = a > m[k] ? a : m[k];
     }
-  if ((threadIdx.x & 31) == 0 && hi[0] != 0) {
-    for (int k = 0; k < 3; ++k) {
-      atomicMin(&box[k], lo[k]);
-      atomicMax(&box[3 + k], hi[k]);
-    }
+    if (lane == 0) part[k][w] = m[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    unsigned long long r = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) r = part[threadIdx.x][k] > r ? part[threadIdx.x][k] : r;
+    if (r) atomicMax(&box[threadIdx.x], r);
   }
 }
 
@@ -107,7 +125,7 @@ static __global__ void k_prep_finish(const unsigned long long* box, double tol, 
                                      DynParams* dyn, RunState* st, double l0) {
   if (l0 > 0.0) st->l_bits = (unsigned long long)__double_as_longlong(l0);  // warm start of l
   double v[6];
-  for (int k = 0; k < 6; ++k) v[k] = ordered_to_double(box[k]);
+  for (int k = 0; k < 6; ++k) v[k] = ordered_to_double(k < 3 ? ~box[k] : box[k]);
   double dx = v[3] - v[0], dy = v[4] - v[1], dz = v[5] - v[2];
   double dA = sqrt(dx * dx + dy * dy + dz * dz);
   double amax = 0.0;
@@ -118,18 +136,6 @@ static __global__ void k_prep_finish(const unsigned long long* box, double tol, 
   dyn->slack = slack;
   dyn->slack_f = __double2float_ru(slack);
   dyn->pad = 0;
-}
-
-template <class P, typename T>
-__global__ void k_init_pool(const T* VA, int64_t nVA, const uint8_t* ref, typename P::Vtx* pool) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= nVA) return;
-  typename P::Vtx v;
-  memset(&v, 0, sizeof v);
-  P::set_pos(v, (double)VA[3 * i], (double)VA[3 * i + 1], (double)VA[3 * i + 2]);
-  v.tri = ref[i] ? -2 : -1;
-  v.hint = -1;
-  pool[i] = v;
 }
 
 // Nearest-triangle queries for pool vertices [beg, beg + count); count = min(*count_ptr *
@@ -296,7 +302,7 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
   Tally<P> ty;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     typename P::Item it = u4list[t];
-    typename P::UT u = P::bound_u4(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], rp);
+    typename P::UT u = P::bound_u4(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], rp, it.U);
     int code = 5;
     if (u < th.lo) {
       code = 4;
@@ -450,8 +456,24 @@ inline double bits_to_double(unsigned long long b) {
 
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
 // Enqueues the validation of A, its bounding box and the device-side parameters (no sync).
+// Round-0 set-up of A, all on the stream with no host round trip: referenced vertices,
+// validation, bounding box and pool entries, then eps / slack (and the warm-start l) on the
+// device.  `small` (ref | box | dyn | st) must be zero-filled first.
+template <class P>
 int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale,
-              RunState* st);
+              RunState* st, typename P::Vtx* pool) {
+  cudaStream_t s = io.s;
+  int* bad = (int*)(box + 6);
+  TraceScope tr(HD_K_PREP, s);
+  k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
+  if (io.vtype == HD_F64)
+    k_check_init<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad, pool);
+  else
+    k_check_init<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad, pool);
+  k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0);
+  HD_TRY_LAUNCH();
+  return HD_OK;
+}
 
 // Buffers of one policy's frontier loop.
 template <class P>
@@ -687,17 +709,19 @@ int run_bnb(const RunIO& io) {
   unsigned long long* box = (unsigned long long*)(small + ref_bytes);  // [0..5] bbox, [6] invalid flag
   DynParams* dyn = (DynParams*)(small + ref_bytes + 256);
   RunState* st = (RunState*)(small + ref_bytes + 512);
-  HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
-  // validation of A and its bbox run asynchronously; the host reads the result with round 0
-  int rc = prepare_A(io, ref, box, dyn, P::slack(1.0), st);
+  HD_TRY(cudaMemsetAsync(small, 0, ref_bytes + 512 + sizeof(RunState), s));
+
+  Rounds<P> R;
+  int rc = alloc_rounds<P>(R, o, io.nVA, io.nFA, !P::kFp64, s);
   if (rc != HD_OK) {
     cudaFreeAsync(small, s);
     return rc;
   }
-
-  Rounds<P> R;
-  rc = alloc_rounds<P>(R, o, io.nVA, io.nFA, !P::kFp64, s);
+  // validation of A, its bbox and the pool entries of its vertices run asynchronously; the
+  // host reads the result with round 0
+  rc = prepare_A<P>(io, ref, box, dyn, P::slack(1.0), st, R.pool);
   if (rc != HD_OK) {
+    free_rounds(R, s);
     cudaFreeAsync(small, s);
     return rc;
   }
@@ -720,14 +744,6 @@ int run_bnb(const RunIO& io) {
   const unsigned max_grid = (unsigned)sms * 16;
 
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
-  {
-    TraceScope tr(HD_K_PREP, s);
-    if (io.vtype == HD_F64)
-      k_init_pool<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, R.pool);
-    else
-      k_init_pool<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, R.pool);
-  }
-  HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, R.pool, 0, nullptr, 1, (int)io.nVA, st,

@@ -325,7 +325,7 @@ struct PolicyD {
   __device__ static D3 out_foot(const Vtx& v) { return {v.qx, v.qy, v.qz}; }
   static double slack(double) { return 0.0; }
   __device__ static double ut_down(double x) { return x; }
-  __device__ static double bound_u4(const Vtx&, const Vtx&, const Vtx&, const RunParams&) { return INFINITY; }
+  __device__ static double bound_u4(const Vtx&, const Vtx&, const Vtx&, const RunParams&, double) { return INFINITY; }
   __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
   __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {

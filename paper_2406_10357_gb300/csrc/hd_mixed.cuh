@@ -562,6 +562,44 @@ __device__ inline float ubm_u4(const VM t[3], double slack) {
   return __fadd_ru(__double2float_ru(u + 2.0 * slack + 1e-12 * u), qe);
 }
 
+// Plain FP32 value of Eq. (bound_u4), without rounding control, in coordinates relative to
+// the first vertex.  It only decides whether the certified FP64 evaluation can pay off (see
+// PolicyM::bound_u4): a wrong estimate costs tightness, never validity.
+__device__ inline float u4_h2_estimate(const F3 X[3], F3 a, F3 b) {
+  float h2 = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    F3 ea = X[i] - a, eb = X[i] - b;
+    h2 = fmaxf(h2, fminf(dotf(ea, ea), dotf(eb, eb)));
+  }
+  F3 n = b - a;
+  F3 mid = {0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    F3 x0 = X[i], x1 = X[(i + 1) % 3];
+    float c0 = dotf(n, x0 - mid), c1 = dotf(n, x1 - mid);
+    if (((c0 <= 0.f && c1 >= 0.f) || (c0 >= 0.f && c1 <= 0.f)) && c0 != c1) {
+      float tau = __fdividef(c0, c0 - c1);
+      F3 x = {fmaf(tau, x1.x - x0.x, x0.x), fmaf(tau, x1.y - x0.y, x0.y), fmaf(tau, x1.z - x0.z, x0.z)};
+      F3 ea = x - a, eb = x - b;
+      h2 = fmaxf(h2, fminf(dotf(ea, ea), dotf(eb, eb)));
+    }
+  }
+  return h2;
+}
+
+__device__ inline float u4_estimate(const VM t[3]) {
+  const F3 X[3] = {{0.f, 0.f, 0.f}, edge(t[0], t[1]), edge(t[0], t[2])};
+  const F3 Q[3] = {t[0].q, X[1] + t[1].q, X[2] + t[2].q};
+  F3 e0 = X[0] - X[1], e1 = X[1] - X[2], e2 = X[2] - X[0];
+  float l0 = dotf(e0, e0), l1 = dotf(e1, e1), l2 = dotf(e2, e2);
+  // shortest edge v1v2 with footpoints q1 (the opposite vertex's), q2, q3 as in ub_u4
+  F3 q2 = Q[0], q3 = Q[1], q1 = Q[2];
+  if (l1 < l0 && l1 <= l2) { q2 = Q[1]; q3 = Q[2]; q1 = Q[0]; }
+  else if (l2 < l0 && l2 < l1) { q2 = Q[2]; q3 = Q[0]; q1 = Q[1]; }
+  return sqrtf(fminf(u4_h2_estimate(X, q1, q2), u4_h2_estimate(X, q1, q3)));
+}
+
 __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], double l, const RunParams& rp, int& code,
                                       Counters& c) {
   // comparisons against l in float: lf <= l, so u < lf still means u < l
@@ -610,11 +648,15 @@ struct PolicyM {
   // vertices (2^-48 relative per level, at most 60 levels) and the double rounding of u4
   static double slack(double amax) { return ldexp(amax, -40); }
   __device__ static float ut_down(double x) { return __double2float_rd(x); }
-  // the u4 pass: Eq. (bound_u4) for one item, plus the slack
-  __device__ static float bound_u4(const Vtx& a, const Vtx& b, const Vtx& c, const RunParams& rp) {
+  // the u4 pass: Eq. (bound_u4) for one item, plus the slack, for an item whose bound so far
+  // is U (not below l).  The certified value is evaluated in FP64 (slow on GB300) only when
+  // the FP32 estimate says it may lower U or discard the item; otherwise +inf (no change).
+  __device__ static float bound_u4(const Vtx& a, const Vtx& b, const Vtx& c, const RunParams& rp, float U) {
     VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
                {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
                {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
+    const float est = u4_estimate(t);
+    if (!(est * (1.f - 1e-3f) < U)) return INFINITY;
     return __fadd_ru(ubm_u4(t, rp.slack), rp.slack_f);
   }
 
