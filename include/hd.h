@@ -138,6 +138,14 @@ int64_t hd_bvh_num_faces(const hd_bvh* bvh);
 int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
                  hd_result* out);
 
+/* hd_hausdorff with l starting at l0 >= 0, a lower bound already known for the quantity
+ * being bracketed (Section 3.1 starts l at the largest vertex distance; a larger known value
+ * lets sub-triangles bounded below it go at once).  *out then brackets max(l0, h(A, B)),
+ * which is h(A, B) whenever l0 <= h(A, B).  Used for the two-sided distance and for A's
+ * faces split over several GPUs, whose ranks share the largest vertex distance. */
+int hd_hausdorff_from(const hd_bvh* B, const hd_mesh* A, double tol, double l0, const hd_options* opt,
+                      void* stream, hd_result* out);
+
 /* Two-sided H(A, B) = max(h(A, B), h(B, A)) (Section 6, conclusion and future work):
  * h(A, B) as hd_hausdorff (bvhB is B's BVH), then h(B, A) through A's BVH (bvhA) at the
  * same absolute tolerance, with l starting from h(A, B)'s final lower bound, as the paper

@@ -75,6 +75,7 @@ def lib():
         L.hd_hausdorff.argtypes = [vp, C.POINTER(HdMesh), d, C.POINTER(HdOptions), vp, C.POINTER(HdResult)]
         L.hd_hausdorff_batched.argtypes = [C.POINTER(vp), C.POINTER(HdMesh), i64, d, C.POINTER(HdOptions), vp,
                                            C.POINTER(HdResult)]
+        L.hd_hausdorff_from.argtypes = [vp, C.POINTER(HdMesh), d, d, C.POINTER(HdOptions), vp, C.POINTER(HdResult)]
         L.hd_hausdorff_sym.argtypes = [vp, C.POINTER(HdMesh), vp, C.POINTER(HdMesh), d, C.POINTER(HdOptions), vp,
                                        C.POINTER(HdResult), C.POINTER(HdResult), C.POINTER(HdResult)]
         L.hd_nearest.argtypes = [vp, vp, i32, i64, i32, vp, vp, vp, vp, vp]
@@ -88,7 +89,8 @@ def lib():
         L.hd_status_str.argtypes = [C.c_int]
         L.hd_status_str.restype = C.c_char_p
         L.hd_last_error.restype = C.c_char_p
-        for f in ("hd_build_B", "hd_hausdorff", "hd_hausdorff_batched", "hd_nearest", "hd_upper_bounds"):
+        for f in ("hd_build_B", "hd_hausdorff", "hd_hausdorff_batched", "hd_hausdorff_from", "hd_hausdorff_sym",
+                  "hd_nearest", "hd_upper_bounds"):
             getattr(L, f).restype = C.c_int
         _lib = L
     return _lib
@@ -220,6 +222,17 @@ def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, str
                             C.byref(r))
     if rc in (HD_ERR_INVALID, HD_ERR_CUDA):
         raise HdError(rc, "hd_hausdorff")
+    return _result(r)
+
+
+def hd_hausdorff_from(bvh: Bvh, VA, FA, tol: float, l0: float, opt: HdOptions | None = None, stream=None) -> dict:
+    """hd_hausdorff with l starting at l0 (a known lower bound); brackets max(l0, h(A, B))."""
+    m, keep, dev = _mesh(VA, FA)
+    r = HdResult()
+    rc = lib().hd_hausdorff_from(bvh.handle, C.byref(m), float(tol), float(l0), C.byref(opt) if opt else None,
+                                 _stream(dev, stream), C.byref(r))
+    if rc in (HD_ERR_INVALID, HD_ERR_CUDA):
+        raise HdError(rc, "hd_hausdorff_from")
     return _result(r)
 
 

@@ -293,6 +293,11 @@ int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options
   return hausdorff_one(B, A, tol, opt, stream, out, 0.0);
 }
 
+int hd_hausdorff_from(const hd_bvh* B, const hd_mesh* A, double tol, double l0, const hd_options* opt,
+                      void* stream, hd_result* out) {
+  return hausdorff_one(B, A, tol, opt, stream, out, l0);
+}
+
 int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, const hd_mesh* B, double tol,
                      const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba) {
   if (!out) return HD_ERR_INVALID;

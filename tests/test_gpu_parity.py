@@ -219,6 +219,29 @@ def test_batched_invalid_pair_is_reported(hd):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_face_split_pair_gpu(hd, orc, precision):
+    """One pair with A's faces split in three parts, as three ranks would run it (here one
+    after another on one GPU): the shared seed, hd_hausdorff_from per part and the max of the
+    brackets give a bracket within eps that meets the oracle's for the whole pair."""
+    from paper_2406_10357_gb300 import multi
+
+    p = mg.workload(2, 0.02)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    engine, seed = multi.gpu_engine(bvh, hd.hd_options_default(precision=prec))
+    eps = p.tol * multi.referenced_diagonal(p.VA, p.FA)
+    FA = np.asarray(p.FA)
+    parts = [FA[slice(*multi.shard_faces(len(FA), r, 3))] for r in range(3)]
+    l0 = max(seed(p.VA, part) for part in parts)
+    brs = [engine(p.VA, part, eps, l0) for part in parts]
+    lo, up = max(b[0] for b in brs), max(b[1] for b in brs)
+    assert all(b[2] == hd.HD_OK for b in brs) and all(b[0] >= l0 for b in brs)
+    assert up - lo <= eps * (1 + 1e-12)
+    ref = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    assert max(lo, ref["lower"]) <= min(up, ref["upper"]) + 1e-12 * eps
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parent_clamp_on_and_off(hd, orc, precision):
     """Clamping a child's U to its parent's is sound (the child lies inside the parent): with
     and without it the bracket is within eps and meets the oracle's."""
