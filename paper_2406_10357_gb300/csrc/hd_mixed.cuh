@@ -13,15 +13,21 @@
 //    length plus an a-priori error term (48 u M, M the local magnitude, u = 2^-24) is an
 //    upper bound.  The lower bound is a support-function certificate: for any n with
 //    |n| <= 1, d(p, S) >= min over the vertices X of S of n.(X - p), evaluated with
-//    downward rounding; n points to the computed closest point, which makes it tight
-//    whenever the classification was right.  If the certificate is loose (near-degenerate
-//    sliver, where the barycentric test is ill-conditioned), the test is redone in FP64.
+//    downward rounding; n is chosen by the closest point's region (the plane normal for
+//    the face, the closest-point direction less its along-edge component for an edge, the
+//    direction itself for a vertex), which makes it tight whenever the classification was
+//    right.  If the certificate is loose (near-degenerate sliver, where the barycentric
+//    test is ill-conditioned), the test is redone in FP64.
+//  * Terms of u3 need only upper bounds, and any point of the triangle gives one: there
+//    the closest point is found without branches (plane projection if inside, else the
+//    nearest edge projection) with the same margin.
 //  * Box distances for pruning are lower bounds (downward rounding); pruning compares
 //    them with the best certified upper bound, so the minimum of the tested lower bounds
 //    is a lower bound of d(p, B).
 //  * Bounds of Section 3.2 take certified vertex distances (upper bounds), edge lengths
 //    rounded up, the circumradius only with the area rounded down, and the split points of
-//    u3 with their representation error added.  u4 runs in FP64 with a relative margin.
+//    u3 with their representation error added.  u4 runs in FP64 with a relative margin,
+//    where an FP32 estimate says it can pay off.
 #pragma once
 
 #include "hd_fp64.cuh"
