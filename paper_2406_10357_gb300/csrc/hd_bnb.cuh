@@ -204,16 +204,21 @@ __device__ inline void flush_tally(RunState* st, const Tally<P>& t) {
   unsigned long long d[6] = {warp_sum(t.d0), warp_sum(t.d1), warp_sum(t.d2),
                              warp_sum(t.d3), warp_sum(t.d4), warp_sum(t.d5)};
   unsigned long long r = warp_sum(t.retired);
-  double uret = warp_max((double)t.uret), umax = warp_max((double)t.umax);
+  typename P::UT uret = t.uret, umax = t.umax;
+  for (int o = 16; o > 0; o >>= 1) {
+    typename P::UT a = __shfl_xor_sync(0xffffffffu, uret, o), b = __shfl_xor_sync(0xffffffffu, umax, o);
+    uret = a > uret ? a : uret;
+    umax = b > umax ? b : umax;
+  }
   if ((threadIdx.x & 31) == 0) {
 #pragma unroll
     for (int k = 0; k < 6; ++k)
       if (d[k]) atomicAdd(&st->discards[k], d[k]);
     if (r) {
       atomicAdd(&st->retired, r);
-      atomic_max_nonneg(&st->uret_bits, uret);
+      atomic_max_nonneg(&st->uret_bits, (double)uret);
     }
-    if (umax > 0.0) atomic_max_nonneg(&st->umax_bits, umax);
+    if (umax > 0) atomic_max_nonneg(&st->umax_bits, (double)umax);
   }
 }
 
@@ -223,6 +228,8 @@ template <class P>
 struct Thresholds {
   typename P::UT lo, hi;
   __device__ Thresholds(double l, double eps) : lo(P::ut_down(l)), hi(P::ut_down(add_rd(l, eps))) {}
+  struct Raw {};
+  __device__ Thresholds(Raw, typename P::UT lo_, typename P::UT hi_) : lo(lo_), hi(hi_) {}
 };
 
 // Discard / retire / keep one bounded item (Section 3.1: discard when U < l).  Items whose
@@ -256,6 +263,32 @@ __device__ inline double load_l(const RunState* st) {
   return __longlong_as_double((long long)*(volatile unsigned long long*)&st->l_bits);
 }
 
+// l and the comparison thresholds, computed once per block (l does not change while a bound
+// or select kernel runs: only the queries raise it) and shared, so that the FP64 conversions
+// are not repeated per thread.  Every thread of the block must call it.
+template <class P>
+struct Level {
+  double l;
+  float lf;  // l rounded down to float: u < lf implies u < l
+  Thresholds<P> th;
+};
+template <class P>
+__device__ inline Level<P> block_level(const RunState* st, double eps) {
+  __shared__ double s_l;
+  __shared__ float s_lf;
+  __shared__ typename P::UT s_lo, s_hi;
+  if (threadIdx.x == 0) {
+    const double l = load_l(st);
+    const Thresholds<P> th(l, eps);
+    s_l = l;
+    s_lf = __double2float_rd(l);
+    s_lo = th.lo;
+    s_hi = th.hi;
+  }
+  __syncthreads();
+  return Level<P>{s_l, s_lf, Thresholds<P>(typename Thresholds<P>::Raw{}, s_lo, s_hi)};
+}
+
 // Round 0: UpperBound for every face of A.
 template <class P>
 __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
@@ -263,8 +296,8 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
                               int64_t n_pool_valid) {
   const RunParams rp = with_dyn(rp_in);
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double l = load_l(st);
-  Thresholds<P> th(l, rp.eps);
+  const Level<P> lv = block_level<P>(st, rp.eps);
+  const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
   if (f < nFA) {
@@ -283,7 +316,7 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
     it.v[1] = FA[3 * f + 1];
     it.v[2] = FA[3 * f + 2];
     int code;
-    it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
+    it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
     classify<P>(st, it, th, code, next, next_cap, u4list, ty);
   }
   flush_counters(st, c);
@@ -297,8 +330,8 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
                            RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
   const RunParams rp = with_dyn(rp_in);
   int n = min(*(volatile int*)&st->n_u4, cap);
-  double l = load_l(st);
-  Thresholds<P> th(l, rp.eps);
+  const Level<P> lv = block_level<P>(st, rp.eps);
+  const Thresholds<P>& th = lv.th;
   Tally<P> ty;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
     typename P::Item it = u4list[t];
@@ -323,8 +356,9 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
                          typename P::Item* promo, int promo_cap) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   const RunParams rp = with_dyn(rp_in);
-  double l = load_l(st);
-  Thresholds<P> th(l, rp.eps);
+  const Level<P> lv = block_level<P>(st, rp.eps);
+  const Thresholds<P>& th = lv.th;
+  const double l = lv.l;
   Tally<P> ty;
   if (i < n_front) {
     typename P::Item it = front[i];
@@ -378,8 +412,8 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
                                  typename P::Item* u4list) {
   const RunParams rp = with_dyn(rp_in);
   int S = min(*(volatile int*)&st->n_split, K);
-  double l = load_l(st);
-  Thresholds<P> th(l, rp.eps);
+  const Level<P> lv = block_level<P>(st, rp.eps);
+  const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
@@ -395,7 +429,7 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
       else if (k == 2) { it.v[0] = m31; it.v[1] = m23; it.v[2] = par.z; }
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
-      it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], l, rp, code, c);
+      it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
       // the child lies inside its parent: h(child, B) <= U(parent)
       const typename P::UT Up = (typename P::UT)__int_as_float(par.w);
       if (rp.parent_clamp && Up < it.U) it.U = Up;

@@ -342,7 +342,7 @@ struct PolicyD {
     m.tri = -2;
     m.hint = a.tri;
   }
-  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l,
+  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l, float,
                                    const RunParams& rp, int& code, Counters& cnt) {
     VI t[3] = {{{a.x, a.y, a.z}, a.d, a.tri, {a.qx, a.qy, a.qz}},
                {{b.x, b.y, b.z}, b.d, b.tri, {b.qx, b.qy, b.qz}},

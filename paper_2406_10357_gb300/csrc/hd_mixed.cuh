@@ -606,10 +606,9 @@ __device__ inline float u4_estimate(const VM t[3]) {
   return sqrtf(fminf(u4_h2_estimate(X, q1, q2), u4_h2_estimate(X, q1, q3)));
 }
 
-__device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], double l, const RunParams& rp, int& code,
+// lf is l rounded down to float: comparisons against it in float are safe, u < lf => u < l
+__device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], float lf, const RunParams& rp, int& code,
                                       Counters& c) {
-  // comparisons against l in float: lf <= l, so u < lf still means u < l
-  const float lf = __double2float_rd(l);
   float U;
   if (t[0].I == t[1].I && t[1].I == t[2].I) {
     code = 0;
@@ -728,12 +727,12 @@ struct PolicyM {
     m.hint = a.tri;
     m.pad0 = m.pad1 = 0.f;
   }
-  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double l,
-                                   const RunParams& rp, int& code, Counters& cnt) {
+  __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double,
+                                   float lf, const RunParams& rp, int& code, Counters& cnt) {
     VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
                {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
                {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
-    return upper_bound_m(B, t, l, rp, code, cnt);
+    return upper_bound_m(B, t, lf, rp, code, cnt);
   }
 };
 
