@@ -199,8 +199,8 @@ def profiled_traffic(kind: str, precision: str):
 def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 2) -> int:
     """Kernels one hd_build_B + hd_hausdorff call launches (the library's launch sequence):
     build -- centroids, Morton codes, per sort pass a digit count and a scatter (plus a scan
-    when B needs more than 64 sort tiles), the gather, then the radix tree and the fused
-    refit/emit (one root kernel instead when B fits in one leaf); A's referenced vertices,
+    when B needs more than 64 sort tiles), the gather, then the radix tree, the refit and
+    the node emission (one root kernel instead when B fits in one leaf); A's referenced vertices,
     validation with pool set-up, and the tolerance (3), round 0 (query, bound faces), 4 per
     frontier round (reset, select, query, bound children), and in MIXED the u4 pass after
     every bound kernel."""
@@ -210,7 +210,7 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 2) -> in
     passes = -(-3 * bits // 8)
     tile = 256 * (4 if nB <= 64 * 256 * 4 else 16)
     fused = -(-nB // tile) <= 64
-    build = 2 + passes * (2 if fused else 3) + 1 + (2 if nB > leaf_size else 1)
+    build = 2 + passes * (2 if fused else 3) + 1 + (3 if nB > leaf_size else 1)
     rounds = stats["rounds"]
     run = 3 + 2 + 4 * rounds + ((1 + rounds) if mixed else 0)
     return build + run

@@ -6,7 +6,7 @@
 
 namespace hd {
 
-constexpr int kStack = 64;
+constexpr int kStack = 96;  // up to 3 pushes per 4-wide node
 
 // Nearest triangle of B to p by ordered depth-first traversal of the BVH: both child
 // boxes come with one node fetch, leaf children are tested at once, the nearer internal
@@ -20,35 +20,58 @@ __device__ inline void traverse(const BvhDev& B, D3 p, Test& test, Counters& c) 
   int node = 0;
   for (;;) {
     const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
-    float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-    int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
-    double d0 = box_dist2(p, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
-    double d1 = box_dist2(p, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
-    c.boxes += 2;
-    if (ref.z > 0 && d0 < test.radius2()) test.range(ref.x, ref.z);
-    if (ref.w > 0 && d1 < test.radius2()) test.range(ref.y, ref.w);
-    double r2 = test.radius2();
-    bool g0 = ref.z == 0 && d0 < r2, g1 = ref.w == 0 && d1 < r2;
-    if (g0 && g1) {
-      int nn = ref.x, nf = ref.y;
-      double df = d1;
-      if (d1 < d0) {
-        nn = ref.y;
-        nf = ref.x;
-        df = d0;
+    const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
+    const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
+    const uint4 cd = __ldg(reinterpret_cast<const uint4*>(np + 6));
+    double e[4] = {box_dist2(p, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x), box_dist2(p, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y),
+                   box_dist2(p, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z), box_dist2(p, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w)};
+    unsigned k[4] = {cd.x, cd.y, cd.z, cd.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      c.boxes += k[j] != kNoChild;
+      if (k[j] == kNoChild) e[j] = INFINITY;
+    }
+    // nearest first (sorting network on four)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const int a = q == 0 ? 0 : q == 1 ? 2 : q == 2 ? 0 : q == 3 ? 1 : 1;
+      const int b = q == 0 ? 1 : q == 1 ? 3 : q == 2 ? 2 : q == 3 ? 3 : 2;
+      if (e[b] < e[a]) {
+        double te = e[a];
+        e[a] = e[b];
+        e[b] = te;
+        unsigned tk = k[a];
+        k[a] = k[b];
+        k[b] = tk;
       }
-      if (sp < kStack) {
-        stack_node[sp] = nf;
-        stack_d[sp] = df;
-        ++sp;
-      } else {
-        c.err = 1;  // stack overflow: the far subtree is skipped and the error reported
+    }
+    // leaf ranges first, nearest first, so that the radius shrinks before the inner
+    // children are kept or dropped
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (k[j] != kNoChild && code_count(k[j]) > 0 && e[j] < test.radius2()) test.range(code_ref(k[j]), code_count(k[j]));
+    const double r2 = test.radius2();
+    int next = -1;
+    double next_d = 0.0;
+#pragma unroll
+    for (int j = 3; j >= 0; --j) {  // farthest inner children pushed first; the nearest is taken
+      if (k[j] == kNoChild || code_count(k[j]) > 0 || !(e[j] < r2)) continue;
+      if (next >= 0) {
+        if (sp < kStack) {
+          stack_node[sp] = next;
+          stack_d[sp] = next_d;
+          ++sp;
+        } else {
+          c.err = 1;  // stack overflow: the subtree is skipped and the error reported
+        }
       }
-      node = nn;
+      next = code_ref(k[j]);
+      next_d = e[j];
+    }
+    if (next >= 0) {
+      node = next;
       continue;
     }
-    if (g0) { node = ref.x; continue; }
-    if (g1) { node = ref.y; continue; }
     bool found = false;
     while (sp > 0) {
       --sp;

@@ -22,16 +22,22 @@ int set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
 // ----------------------------------------------------------------------------- BVH layout
 
-// One traversal node, 64 bytes: the boxes of both children (so one node fetch gives both
-// child boxes), and for each child either an internal node index (count == 0), a leaf
-// range [ref, ref + count) of sorted triangles (count > 0), or nothing (count < 0).
+// One traversal node, 128 bytes, with up to four children (a node of the binary radix tree
+// together with its children's children, so a traversal takes half as many dependent node
+// fetches): the children's boxes stored by component (lo.x of children 0..3, then lo.y, ...),
+// and per child a code, count << 27 | index -- an inner node (count 0), a leaf range
+// [index, index + count) of sorted triangles (count > 0), or no child (kNoChild, with an
+// empty box: lo = +inf, hi = -inf).
 struct __align__(16) BvhNode {
-  float4 f0;  // c0.lo.x c0.lo.y c0.lo.z c0.hi.x
-  float4 f1;  // c0.hi.y c0.hi.z c1.lo.x c1.lo.y
-  float4 f2;  // c1.lo.z c1.hi.x c1.hi.y c1.hi.z
-  int4 ref;   // c0.ref c1.ref c0.count c1.count
+  float4 lox, loy, loz, hix, hiy, hiz;
+  uint4 code;
+  uint4 pad;
 };
-static_assert(sizeof(BvhNode) == 64, "node is 64 B");
+static_assert(sizeof(BvhNode) == 128, "node is 128 B");
+constexpr unsigned kNoChild = 0xffffffffu;
+__host__ __device__ inline unsigned node_code(int ref, int cnt) { return ((unsigned)cnt << 27) | (unsigned)ref; }
+__host__ __device__ inline int code_count(unsigned code) { return (int)(code >> 27); }
+__host__ __device__ inline int code_ref(unsigned code) { return (int)(code & 0x07ffffffu); }
 
 }  // namespace hd
 

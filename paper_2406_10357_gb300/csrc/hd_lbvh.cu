@@ -8,8 +8,8 @@
 //   4. the binary radix tree of Karras (HPG 2012) over the sorted codes, ties broken by
 //      position;
 //   5. bottom-up boxes (float, rounded outward so they contain the exact triangles);
-//   6. traversal nodes: 64 B each, holding both child boxes; subtrees of at most
-//      leaf_size triangles become leaf ranges.
+//   6. traversal nodes: 128 B each, holding up to four child boxes (a binary node with its
+//      grandchildren); subtrees of at most leaf_size triangles become leaf ranges.
 #include <cmath>
 #include <cstdio>
 #include <vector>
@@ -346,12 +346,41 @@ __device__ inline void child_meta(int c, const int* first, const int* last, int 
   }
 }
 
-// Bottom-up boxes and traversal nodes in one pass: the second child to arrive at a node
-// computes its box and, when the node covers more than L triangles, writes its 64-byte
-// traversal node (both child boxes and references).
-__global__ void k_refit_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
-                             const int* parent_int, const int* parent_leaf, const float4* leafbox, float4* ibox,
-                             int* flags, BvhNode* nodes) {
+// Slots 2j, 2j + 1 of a 4-wide node from binary child c: c's two children when c is an inner
+// node that is split further (covers more than L triangles), else c itself as a leaf range
+// and an empty slot.  cbox is c's box; the children's boxes are read from ibox / leafbox.
+__device__ inline void wide_slots(int c, const float clo[3], const float chi[3], const int* left, const int* right,
+                                  const int* first, const int* last, int L, const float4* leafbox,
+                                  const float4* ibox, float lo[2][3], float hi[2][3], unsigned code[2]) {
+  const bool expand = c >= 0 && last[c] - first[c] + 1 > L;
+  if (!expand) {
+    int r, k;
+    child_meta(c, first, last, L, r, k);
+    code[0] = node_code(r, k);
+    code[1] = kNoChild;
+    for (int a = 0; a < 3; ++a) {
+      lo[0][a] = clo[a];
+      hi[0][a] = chi[a];
+      lo[1][a] = INFINITY;
+      hi[1][a] = -INFINITY;
+    }
+    return;
+  }
+  const int g[2] = {left[c], right[c]};
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    int r, k;
+    child_meta(g[j], first, last, L, r, k);
+    code[j] = node_code(r, k);
+    load_box(g[j] >= 0 ? ibox + 2 * g[j] : leafbox + 2 * (int64_t)(~g[j]), lo[j], hi[j]);
+  }
+}
+
+// Bottom-up boxes: the second child to arrive at a node computes its box.  (Only the box:
+// this pass is a chain of dependent steps as deep as the tree, so it is kept short; the
+// nodes are written afterwards in parallel by k_emit.)
+__global__ void k_refit(int64_t n, const int* left, const int* right, const int* parent_int, const int* parent_leaf,
+                        const float4* leafbox, float4* ibox, int* flags) {
   int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (leaf >= n) return;
   int node = parent_leaf[leaf];
@@ -364,19 +393,36 @@ __global__ void k_refit_emit(int64_t n, int L, const int* left, const int* right
     __stcg(ibox + 2 * node, make_float4(fminf(lo0[0], lo1[0]), fminf(lo0[1], lo1[1]), fminf(lo0[2], lo1[2]), 0.f));
     __stcg(ibox + 2 * node + 1,
            make_float4(fmaxf(hi0[0], hi1[0]), fmaxf(hi0[1], hi1[1]), fmaxf(hi0[2], hi1[2]), 0.f));
-    if (last[node] - first[node] + 1 > L) {
-      int r0, c0, r1, c1;
-      child_meta(cl, first, last, L, r0, c0);
-      child_meta(cr, first, last, L, r1, c1);
-      BvhNode nd;
-      nd.f0 = make_float4(lo0[0], lo0[1], lo0[2], hi0[0]);
-      nd.f1 = make_float4(hi0[1], hi0[2], lo1[0], lo1[1]);
-      nd.f2 = make_float4(lo1[2], hi1[0], hi1[1], hi1[2]);
-      nd.ref = make_int4(r0, r1, c0, c1);
-      nodes[node] = nd;
-    }
     node = parent_int[node];
   }
+}
+
+// The 128-byte traversal node of every inner node covering more than L triangles: its
+// children, or their children where those are split further, so that the nodes reached from
+// the root skip every other level of the binary tree.  (The nodes of the skipped levels are
+// written too and never visited.)
+__global__ void k_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
+                       const float4* leafbox, const float4* ibox, BvhNode* nodes) {
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (node >= n - 1 || last[node] - first[node] + 1 <= L) return;
+  float lo0[3], hi0[3], lo1[3], hi1[3];
+  int cl = left[node], cr = right[node];
+  load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo0, hi0);
+  load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo1, hi1);
+  float lo[4][3], hi[4][3];
+  unsigned code[4];
+  wide_slots(cl, lo0, hi0, left, right, first, last, L, leafbox, ibox, lo, hi, code);
+  wide_slots(cr, lo1, hi1, left, right, first, last, L, leafbox, ibox, lo + 2, hi + 2, code + 2);
+  BvhNode nd;
+  nd.lox = make_float4(lo[0][0], lo[1][0], lo[2][0], lo[3][0]);
+  nd.loy = make_float4(lo[0][1], lo[1][1], lo[2][1], lo[3][1]);
+  nd.loz = make_float4(lo[0][2], lo[1][2], lo[2][2], lo[3][2]);
+  nd.hix = make_float4(hi[0][0], hi[1][0], hi[2][0], hi[3][0]);
+  nd.hiy = make_float4(hi[0][1], hi[1][1], hi[2][1], hi[3][1]);
+  nd.hiz = make_float4(hi[0][2], hi[1][2], hi[2][2], hi[3][2]);
+  nd.code = make_uint4(code[0], code[1], code[2], code[3]);
+  nd.pad = make_uint4(0, 0, 0, 0);
+  nodes[node] = nd;
 }
 
 // Root for n <= leaf_size: one node whose first child is the whole range.
@@ -390,11 +436,16 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
       hi[k] = fmaxf(hi[k], b[k]);
     }
   }
+  const float I = INFINITY;
   BvhNode nd;
-  nd.f0 = make_float4(lo[0], lo[1], lo[2], hi[0]);
-  nd.f1 = make_float4(hi[1], hi[2], INFINITY, INFINITY);
-  nd.f2 = make_float4(INFINITY, -INFINITY, -INFINITY, -INFINITY);
-  nd.ref = make_int4(0, 0, (int)n, -1);
+  nd.lox = make_float4(lo[0], I, I, I);
+  nd.loy = make_float4(lo[1], I, I, I);
+  nd.loz = make_float4(lo[2], I, I, I);
+  nd.hix = make_float4(hi[0], -I, -I, -I);
+  nd.hiy = make_float4(hi[1], -I, -I, -I);
+  nd.hiz = make_float4(hi[2], -I, -I, -I);
+  nd.code = make_uint4(node_code(0, (int)n), kNoChild, kNoChild, kNoChild);
+  nd.pad = make_uint4(0, 0, 0, 0);
   nodes[0] = nd;
 }
 
@@ -523,8 +574,9 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   if (n > o.leaf_size) {
     HD_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * n, s));
     k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last, pint, pleaf);
-    k_refit_emit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, pint, pleaf,
-                                                              leafbox, ibox, flags, h->nodes);
+    k_refit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, left, right, pint, pleaf, leafbox, ibox, flags);
+    k_emit<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, leafbox, ibox,
+                                                            h->nodes);
   } else {
     k_root_leaf<<<1, 1, 0, s>>>(n, leafbox, h->nodes);
   }

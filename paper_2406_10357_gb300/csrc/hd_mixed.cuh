@@ -275,7 +275,30 @@ struct NearestM {
 // certified point-triangle test thus runs with most lanes of the warp active, and the cheap
 // node steps absorb the divergence.  Stack entries pack a node index (count 0) or a leaf
 // range (first, count) into 32 bits: count in bits 27..31, index below (n_B < 2^27).
-__device__ inline unsigned pack_ref(int ref, int cnt) { return ((unsigned)cnt << 27) | (unsigned)ref; }
+// Compare-exchange of (distance, code) pairs, smaller distance first.
+__device__ inline void sort2(float& ea, unsigned& ca, float& eb, unsigned& cb) {
+  if (eb < ea) {
+    float e = ea;
+    ea = eb;
+    eb = e;
+    unsigned c = ca;
+    ca = cb;
+    cb = c;
+  }
+}
+
+// Push a child found within the radius (distance < +inf) onto the traversal stack.
+__device__ inline void push_code(unsigned* stack_code, float* stack_d, int& sp, unsigned code, float d,
+                                 Counters& c) {
+  if (!(d < INFINITY)) return;
+  if (sp < kStack) {
+    stack_code[sp] = code;
+    stack_d[sp] = d;
+    ++sp;
+  } else {
+    c.err = 1;  // stack overflow: the subtree is skipped and the error reported
+  }
+}
 
 // Must be called by all 32 lanes of the warp; inactive lanes start finished.
 __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, bool active) {
@@ -304,39 +327,42 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
         continue;
       }
       const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
-      float4 f0 = __ldg(np), f1 = __ldg(np + 1), f2 = __ldg(np + 2);
-      int4 ref = __ldg(reinterpret_cast<const int4*>(np + 3));
-      float d0 = box_lo2(t.P, f0.x, f0.y, f0.z, f0.w, f1.x, f1.y);
-      float d1 = box_lo2(t.P, f1.z, f1.w, f2.x, f2.y, f2.z, f2.w);
-      c.boxes += 2;
-      float r2 = t.radius2();
-      bool h0 = ref.z >= 0 && d0 <= r2, h1 = ref.w >= 0 && d1 <= r2;
-      int nr = 0, nc = -1;  // child taken now
-      if (h0 && h1) {
-        bool first0 = d0 <= d1;
-        int fr = first0 ? ref.y : ref.x, fc = first0 ? ref.w : ref.z;
-        if (sp < kStack) {
-          stack_code[sp] = pack_ref(fr, fc);
-          stack_d[sp] = first0 ? d1 : d0;
-          ++sp;
+      const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
+      const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
+      const uint4 cd = __ldg(reinterpret_cast<const uint4*>(np + 6));
+      const float r2 = t.radius2();
+      // children within the current radius (the others at +inf), nearest first
+      float e0 = box_lo2(t.P, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);
+      float e1 = box_lo2(t.P, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y);
+      float e2 = box_lo2(t.P, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
+      float e3 = box_lo2(t.P, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
+      unsigned c0 = cd.x, c1 = cd.y, c2 = cd.z, c3 = cd.w;
+      c.boxes += (c0 != kNoChild) + (c1 != kNoChild) + (c2 != kNoChild) + (c3 != kNoChild);
+      if (!(e0 <= r2) || c0 == kNoChild) e0 = INFINITY;
+      if (!(e1 <= r2) || c1 == kNoChild) e1 = INFINITY;
+      if (!(e2 <= r2) || c2 == kNoChild) e2 = INFINITY;
+      if (!(e3 <= r2) || c3 == kNoChild) e3 = INFINITY;
+      sort2(e0, c0, e1, c1);
+      sort2(e2, c2, e3, c3);
+      sort2(e0, c0, e2, c2);
+      sort2(e1, c1, e3, c3);
+      sort2(e1, c1, e2, c2);
+      // the farther hits go on the stack (farthest first, so the nearest of them is popped
+      // first); the nearest is taken now
+      push_code(stack_code, stack_d, sp, c3, e3, c);
+      push_code(stack_code, stack_d, sp, c2, e2, c);
+      push_code(stack_code, stack_d, sp, c1, e1, c);
+      if (e0 < INFINITY) {
+        const int cnt = code_count(c0), ref = code_ref(c0);
+        if (cnt > 0) {
+          lfirst = ref;
+          lcount = cnt;
+          node = -1;
         } else {
-          c.err = 1;  // stack overflow: the far subtree is skipped and the error reported
+          node = ref;
         }
-        nr = first0 ? ref.x : ref.y;
-        nc = first0 ? ref.z : ref.w;
-      } else if (h0) {
-        nr = ref.x;
-        nc = ref.z;
-      } else if (h1) {
-        nr = ref.y;
-        nc = ref.w;
-      }
-      if (nc > 0) {
-        lfirst = nr;
-        lcount = nc;
-        node = -1;
       } else {
-        node = nc == 0 ? nr : -1;
+        node = -1;
       }
     }
     if (__all_sync(0xffffffffu, lcount == 0)) break;
