@@ -44,9 +44,9 @@ SLICES = 16
 FLOPS_PER_LEAF_TEST = 80
 FLOPS_PER_BOX_TEST = 17
 FLOPS_PER_ITEM_BOUND = 100
-BYTES_PER_NODE = 64
-# device->host bytes per step besides results: build flags (8), bbox of A (64) and one
-# RunState (160 B) per round plus round 0
+BYTES_PER_NODE = 128
+# device->host bytes per step: build flags (8); with round 0 the device-side parameters (32)
+# and A's validity flag (8); one run state (160 B) per round plus round 0
 RUNSTATE_BYTES = 160
 
 
@@ -196,7 +196,7 @@ def profiled_traffic(kind: str, precision: str):
     return float(kv[f"{kind}.{precision}.bytes_per_launch"])
 
 
-def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 2) -> int:
+def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> int:
     """Kernels one hd_build_B + hd_hausdorff call launches (the library's launch sequence):
     build -- centroids, Morton codes, per sort pass a digit count and a scatter (plus a scan
     when B needs more than 64 sort tiles), the gather, then the radix tree, the refit and
@@ -318,7 +318,7 @@ def run_ours(args):
     e2e_total = sum(e2e_ts)
     e2e_total = multi.max_over_ranks(e2e_total, device=dev)
     h2d = p.VA.nbytes + p.FA.nbytes + p.VB.nbytes + p.FB.nbytes
-    d2h = 8 + 64 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
+    d2h = 8 + 32 + 8 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
 
     # roofline of the dominant kernel kind, from the trace of the timed steps
     stats = [r["stats"] for r in rs]
@@ -367,245 +367,6 @@ def run_ours(args):
     roof_other = roofline_of("query" if main_kind == "bound" else "bound")
 
     launches = sum(kernel_launches(len(p.FB), s, prec == hd.HD_MIXED) for s in stats)
-
-    line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=1e3 * total / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=workload_desc(p), sample=f"each step: 1/{SLICES} of A's faces (rotating bands)"),
-                cpu_baseline=dict(value=value, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
-                                  sample=f"each step is 1/{SLICES} of A's faces against all of B; value scaled to "
-                                         "whole pairs per second"),
-                e2e=dict(value=value, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
-    print(json.dumps(line), flush=True)
-
-
-# ----------------------------------------------------------------------------- clocks
-
-
-class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
-
-    def __init__(self, gpu_index: int):
-        self.rows, self.proc = [], None
-        try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "100", "-i", str(gpu_index)], stdout=subprocess.PIPE,
-                                         stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-        except (OSError, FileNotFoundError):
-            self.proc = None
-
-    def _read(self):
-        for line in self.proc.stdout:
-            self.rows.append([x.strip() for x in line.split(",")])
-
-    def stop(self):
-        if self.proc is None:
-            return None
-        time.sleep(0.25)
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.t.join(timeout=2)
-        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
-        if not sm:
-            return dict(sm_mhz=None, sm_max_mhz=None, reasons=[], samples=0)
-        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=max(mx) if mx else None, reasons=reasons,
-                    samples=len(sm))
-
-
-# ----------------------------------------------------------------------------- GPU arm
-
-
-def source_digest() -> str:
-    h = hashlib.sha256()
-    src = os.path.join(ROOT, "paper_2406_10357_gb300", "csrc")
-    for f in sorted(os.listdir(src)):
-        h.update(open(os.path.join(src, f), "rb").read())
-    return h.hexdigest()[:16]
-
-
-def profiled_traffic(kind: str, precision: str):
-    """DRAM bytes per launch of the dominant kernel from the committed ncu summary, if it was
-    taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    if not os.path.exists(path):
-        return None
-    kv = {}
-    for line in open(path):
-        if "=" in line and not line.startswith("#"):
-            k, v = line.strip().split("=", 1)
-            kv[k.strip()] = v.strip()
-    if kv.get("source_digest") != source_digest() or kv.get(f"{kind}.{precision}.bytes_per_launch") is None:
-        return None
-    return float(kv[f"{kind}.{precision}.bytes_per_launch"])
-
-
-def measured_peaks():
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        return json.load(open(path)), "measured"
-    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
-
-
-def run_ours(args):
-    import torch
-
-    import paper_2406_10357_gb300 as hd
-    from paper_2406_10357_gb300 import build as hb
-    from paper_2406_10357_gb300 import multi
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if rank == 0 or not hb.up_to_date():
-        hb.build()
-    if dist:
-        dist.barrier()
-
-    p = mg.workload(WORKLOAD)
-    VA = torch.from_numpy(p.VA).to(dev)
-    FA = torch.from_numpy(p.FA).to(dev)
-    VB = torch.from_numpy(p.VB).to(dev)
-    FB = torch.from_numpy(p.FB).to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    prec = hd.HD_MIXED if args.precision == "mixed" else hd.HD_FP64
-    opt = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=prec)
-
-    def step(o):
-        bvh = hd.hd_build_B(VB, FB)
-        r = hd.hd_hausdorff(bvh, VA, FA, p.tol, o)
-        if r["status"] != hd.HD_OK:
-            raise RuntimeError(f"step failed: {r}")
-        return r
-
-    def timed(o, k):
-        ts, rs = [], []
-        for _ in range(k):
-            flush.zero_()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            rs.append(step(o))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return ts, rs
-
-    for _ in range(args.warmup):
-        step(opt)
-    hd.hd_trace_read(reset=True)
-    hd.hd_trace_enable(True)
-    clocks = ClockSampler(local)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ts, rs = timed(opt, args.steps)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    hd.hd_trace_enable(False)
-    trace = hd.hd_trace_read(reset=True)
-
-    total_ms = sum(ts)
-    total_ms = multi.max_over_ranks(total_ms, device=dev)  # the slowest rank's time
-    value = world * args.steps / (total_ms / 1e3)
-
-    # mixed vs FP64 at the same tol (same workload, fewer steps)
-    fp64 = None
-    if not args.no_fp64_arm and prec == hd.HD_MIXED:
-        o64 = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64)
-        step(o64)
-        k64 = max(3, args.steps // 4)
-        t64, r64 = timed(o64, k64)
-        fp64 = dict(value=k64 / (sum(t64) / 1e3), ms_per_step=sum(t64) / k64, lower=r64[-1]["lower"],
-                    upper=r64[-1]["upper"])
-
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    e2e_ts, e2e_r = [], None
-    for _ in range(max(3, args.steps // 4)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        bvh = hd.hd_build_B(p.VB, p.FB)
-        e2e_r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, opt)
-        lo, up = e2e_r["lower"], e2e_r["upper"]  # result already on the host
-        e2e_ts.append(time.perf_counter() - t0)
-    e2e_total = sum(e2e_ts)
-    e2e_total = multi.max_over_ranks(e2e_total, device=dev)
-    h2d = p.VA.nbytes + p.FA.nbytes + p.VB.nbytes + p.FB.nbytes
-    d2h = 8 + 64 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
-
-    # roofline of the dominant kernel kind, from the trace of the timed steps
-    stats = [r["stats"] for r in rs]
-    leaf = sum(s["leaf_tests"] for s in stats)
-    boxes = sum(s["box_tests"] for s in stats)
-    evals = sum(s["pointtri_evals"] for s in stats)
-    dom = max(("query", "bound", "select", "build", "prep"), key=lambda k: trace[k]["ms"])
-    q = trace["query"]
-    peaks, src = measured_peaks()
-    clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    if prec == hd.HD_MIXED:
-        peak_tf = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12  # FP32 lanes x FMA x max SM clock
-        peak_note = f"FP32: 152 SMs x 128 lanes x 2 flops x {clock_mhz:.0f} MHz (derived, {src} clock)"
-    else:
-        peak_tf = 1.25  # FP64 nominal for GB300 (the pool's profiling recipe)
-        peak_note = "FP64 nominal 1.25 TFLOP/s"
-    share = {k: round(trace[k]["ms"] / max(1e-9, sum(v["ms"] for v in trace.values())), 4) for k in trace}
-    # traversal: 80 flops per leaf test + 17 per child box; cascade: 80 per point-triangle
-    # evaluation of u3 + 100 per bounded sub-triangle (exact case, u1, u2); bounded
-    # sub-triangles per step = faces of A + 4 per split
-    items = sum(len(p.FA) + 4 * s["splits"] for s in stats)
-    kinds = {
-        "query": dict(kernel="k_query (nearest-triangle traversal)",
-                      flops=FLOPS_PER_LEAF_TEST * leaf + FLOPS_PER_BOX_TEST * boxes,
-                      algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x leaf tests + {FLOPS_PER_BOX_TEST} flops x box tests",
-                      l2_bytes=BYTES_PER_NODE * boxes / 2 + 48 * leaf),
-        "bound": dict(kernel="k_bound_faces/k_bound_children (UpperBound cascade)",
-                      flops=FLOPS_PER_LEAF_TEST * (evals - leaf) + FLOPS_PER_ITEM_BOUND * items,
-                      algorithmic=f"{FLOPS_PER_LEAF_TEST} flops x u3 point-triangle evaluations + "
-                                  f"{FLOPS_PER_ITEM_BOUND} flops x bounded sub-triangles",
-                      l2_bytes=3 * 64 * items + 48 * (evals - leaf)),
-    }
-
-    def roofline_of(kind):
-        t, k = trace[kind], kinds[kind]
-        achieved = k["flops"] / (t["ms"] / 1e3) / 1e12 if t["ms"] > 0 else 0.0
-        return dict(kernel=k["kernel"], bound="alu", achieved=achieved, peak=peak_tf, unit="TFLOP/s",
-                    frac=achieved / peak_tf, traffic=profiled_traffic(kind, args.precision), peak_note=peak_note,
-                    algorithmic=k["algorithmic"], launches=t["launches"],
-                    ms_per_launch=t["ms"] / max(1, t["launches"]),
-                    l2_bytes_per_launch=k["l2_bytes"] / max(1, t["launches"]))
-
-    main_kind = "bound" if trace["bound"]["ms"] > trace["query"]["ms"] else "query"
-    roof = roofline_of(main_kind)
-    roof.update(dominant_kind=dom, share=share)
-    roof_other = roofline_of("query" if main_kind == "bound" else "bound")
-
-    # kernel launches in the timed region: build (24, or 22 when B fits one leaf), A's
-    # validation (2), pool init (1), round-0 query and bound (2), 4 per frontier round
-    nb = len(p.FB)
-    build_k = 24 if nb > 4 else 22
-    # (MIXED adds the u4 pass after every bound kernel)
-    per_round = 5 if prec == hd.HD_MIXED else 4
-    launches = sum(build_k + 5 + (prec == hd.HD_MIXED) + per_round * s["rounds"] for s in stats)
 
     line = dict(metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
                 ms_per_step=total_ms / args.steps, higher_is_better=True, scaling="weak", vs_baseline=None,

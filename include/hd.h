@@ -68,7 +68,7 @@ typedef struct {
   double max_face_factor;  /* m of Section 4: at most m * n_A faces are processed
                               (n_A + 4 per split); default 1e7                           */
   int64_t frontier_chunk;  /* most sub-triangles split in one round (0 = automatic)       */
-  int32_t leaf_size;       /* triangles per BVH leaf, 1..16 (default 2)                   */
+  int32_t leaf_size;       /* triangles per BVH leaf, 1..16 (default 1)                   */
   int32_t block_size;      /* threads per block of the round kernels (default 64)         */
   uint8_t bound_order[4];  /* cascade order, values 1..4 = u1..u4 (default 1,2,3,4)        */
   int32_t n_bounds;        /* how many entries of bound_order are used, 1..4 (default 4)  */

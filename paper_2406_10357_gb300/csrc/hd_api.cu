@@ -215,7 +215,7 @@ void hd_options_default(hd_options* o) {
   o->precision = HD_FP64;
   o->max_face_factor = 1e7;
   o->frontier_chunk = 0;
-  o->leaf_size = 2;
+  o->leaf_size = 1;
   o->block_size = 64;
   o->bound_order[0] = 1;
   o->bound_order[1] = 2;

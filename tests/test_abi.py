@@ -57,7 +57,7 @@ def test_options_default_and_status_strings(hd):
     o = hd.hd_options_default()
     assert o.tol_mode == hd.HD_TOL_ABS and o.precision == hd.HD_FP64
     assert o.max_face_factor == 1e7 and list(o.bound_order) == [1, 2, 3, 4] and o.n_bounds == 4
-    assert o.leaf_size == 2 and o.block_size == 64
+    assert o.leaf_size == 1 and o.block_size == 64
     assert hd.hd_status_str(hd.HD_ERR_CAPACITY) == "HD_ERR_CAPACITY"
     assert hd.hd_status_str(99) == "HD_UNKNOWN"
 
