@@ -81,7 +81,12 @@ typedef struct {
 /* hd_options.flags.  By default the UpperBound of a child sub-triangle is clamped to its
  * parent's: h(child, B) <= h(parent, B) <= U(parent) since the child lies inside the parent.
  * The paper's cascade (Section 4) has no such clamp; HD_FLAG_NO_PARENT_CLAMP turns it off. */
-enum { HD_FLAG_NO_PARENT_CLAMP = 1 };
+enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2 };
+/* HD_FLAG_ASYNC_BUILD (read by hd_build_B): return as soon as the build is queued on the
+ * stream, without waiting for it.  B's validity (indices in range, finite coordinates) is
+ * then known only on the device: hd_hausdorff and its variants check it with their first
+ * read-back and return HD_ERR_INVALID for an invalid B; hd_nearest, hd_nearest_noalloc and
+ * hd_upper_bounds give undefined values (but stay in bounds) on such a BVH. */
 
 typedef struct {
   int64_t rounds;            /* frontier rounds after round 0                              */

@@ -20,6 +20,7 @@ HD_F32, HD_F64 = 0, 1
 HD_TOL_ABS, HD_TOL_REL = 0, 1
 HD_FP64, HD_MIXED = 0, 1
 HD_FLAG_NO_PARENT_CLAMP = 1
+HD_FLAG_ASYNC_BUILD = 2
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 

@@ -121,8 +121,10 @@ __device__ inline double ordered_to_double(unsigned long long u) {
 }
 
 // dA, eps and the slack from A's bounding box, on the device (one thread).
-static __global__ void k_prep_finish(const unsigned long long* box, double tol, int tol_rel, double slack_scale,
-                                     DynParams* dyn, RunState* st, double l0) {
+static __global__ void k_prep_finish(unsigned long long* box, double tol, int tol_rel, double slack_scale,
+                                     DynParams* dyn, RunState* st, double l0, const float* b_meta) {
+  // B's validity flag (from its build) joins A's in the flag word the host reads with round 0
+  if (__float_as_uint(b_meta[1]) != 0u) ((unsigned*)(box + 6))[1] = 1u;
   if (l0 > 0.0) st->l_bits = (unsigned long long)__double_as_longlong(l0);  // warm start of l
   double v[6];
   for (int k = 0; k < 6; ++k) v[k] = ordered_to_double(k < 3 ? ~box[k] : box[k]);
@@ -480,7 +482,7 @@ struct RunIO {
   double l0;  // a known lower bound to start l from (0: none)
 };
 
-inline BvhDev bvh_dev(const hd_bvh* B) { return {B->nodes, B->tri32, B->tri64, B->tri_vid, B->nF, B->eta}; }
+inline BvhDev bvh_dev(const hd_bvh* B) { return {B->nodes, B->tri32, B->tri64, B->tri_vid, B->nF, B->meta}; }
 
 inline double bits_to_double(unsigned long long b) {
   double d;
@@ -504,7 +506,8 @@ int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams*
     k_check_init<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad, pool);
   else
     k_check_init<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad, pool);
-  k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0);
+  k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0,
+                                io.B->meta);
   HD_TRY_LAUNCH();
   return HD_OK;
 }
@@ -797,7 +800,7 @@ int run_bnb(const RunIO& io) {
   HD_TRY(cudaMemcpyAsync(&hb->dyn, dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
   HD_TRY(cudaMemcpyAsync(&hb->bad, box + 6, 8, cudaMemcpyDeviceToHost, s));
   HD_TRY(cudaStreamSynchronize(s));
-  if (hb->bad & 0xffffffffull) {  // invalid A: nothing of round 0 is used
+  if (hb->bad != 0ull) {  // invalid A (low word) or B (high word): nothing of round 0 is used
     free_rounds(R, s);
     cudaFreeAsync(small, s);
     return HD_ERR_INVALID;

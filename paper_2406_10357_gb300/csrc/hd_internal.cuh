@@ -54,7 +54,9 @@ struct hd_bvh {
   double* tri64;       // 9 per triangle: a, b, c (exact input values)
   int4* tri_vid;       // per triangle: the F_B row (vertex indices) and the original face index
   int* inv;            // original face index -> sorted position
-  float eta;           // max distance between a float vertex of tri32 and its input value (0 for f32 input)
+  float eta;           // max distance between a float vertex of tri32 and its input value (0 for f32
+                       // input); the host copy, valid once the build has been waited for
+  float* meta;         // device: [0] eta as above, [1] nonzero if B was invalid (as bits)
 };
 
 namespace hd {
@@ -121,7 +123,7 @@ struct BvhDev {
   const double* tri64;
   const int4* tri_vid;
   int64_t nF;
-  float eta;
+  const float* meta;  // [0] eta: max distance between a float vertex of tri32 and its input
 };
 
 // Per-run values that are only known on the device (they depend on A's bounding box):

@@ -12,6 +12,7 @@
 //      grandchildren); subtrees of at most leaf_size triangles become leaf ranges.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include "hd_internal.cuh"
@@ -36,26 +37,32 @@ __global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, dou
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   if (f < nF) {
     int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
-    if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV) {
-      atomicExch(bad, 1);
-    } else {
-      D3 a = load_vertex(V, i0), b = load_vertex(V, i1), c = load_vertex(V, i2);
-      double* t = tri_unsorted + 9 * f;
-      t[0] = a.x; t[1] = a.y; t[2] = a.z;
-      t[3] = b.x; t[4] = b.y; t[5] = b.z;
-      t[6] = c.x; t[7] = c.y; t[8] = c.z;
-      bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
-                 isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
-      if (!fin) {
-        atomicExch(bad, 1);
-      } else {
-        D3 m = (1.0 / 3.0) * (a + b + c);
-        lo[0] = hi[0] = (float)m.x;
-        lo[1] = hi[1] = (float)m.y;
-        lo[2] = hi[2] = (float)m.z;
-        cent[f] = make_float4(lo[0], lo[1], lo[2], 0.f);
-      }
+    const bool in_range = !(i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV);
+    D3 a = {0, 0, 0}, b = {0, 0, 0}, c = {0, 0, 0};
+    if (in_range) {
+      a = load_vertex(V, i0);
+      b = load_vertex(V, i1);
+      c = load_vertex(V, i2);
     }
+    const bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
+                     isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
+    if (!in_range || !fin) {
+      // flagged; the face becomes a point at the origin, so that the tree stays finite and
+      // every later kernel stays in bounds until the flag is read
+      atomicExch(bad, 1);
+      a = b = c = {0, 0, 0};
+      cent[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      D3 m = (1.0 / 3.0) * (a + b + c);
+      lo[0] = hi[0] = (float)m.x;
+      lo[1] = hi[1] = (float)m.y;
+      lo[2] = hi[2] = (float)m.z;
+      cent[f] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    }
+    double* t = tri_unsorted + 9 * f;
+    t[0] = a.x; t[1] = a.y; t[2] = a.z;
+    t[3] = b.x; t[4] = b.y; t[5] = b.z;
+    t[6] = c.x; t[7] = c.y; t[8] = c.z;
   }
   // block reduction of the centroid box, then one atomic per block and axis
   for (int k = 0; k < 3; ++k) {
@@ -449,6 +456,16 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
   nodes[0] = nd;
 }
 
+// eta (the largest distance between a float vertex of tri32 and its input value, the
+// square root of the gathered squared maximum, rounded up) and the validity flag of B.
+__global__ void k_build_meta(const unsigned* misc, float* meta) {
+  const double r = sqrt((double)__uint_as_float(misc[7])) * (1.0 + 1e-15);
+  meta[0] = __double2float_ru(r);
+  meta[1] = __uint_as_float(misc[6] != 0u ? 1u : 0u);
+  meta[2] = 0.f;
+  meta[3] = 0.f;
+}
+
 template <typename T>
 int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, float4* cent, unsigned* cbox,
                 int* bad, cudaStream_t s) {
@@ -482,6 +499,8 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
 
   hd_bvh* h = new hd_bvh();
   h->block = nullptr;
+  h->meta = nullptr;
+  h->eta = 0.f;
   h->device = dev;
   h->nF = n;
   h->leaf_size = o.leaf_size;
@@ -491,8 +510,9 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     // the BVH's own arrays: one allocation from the device's stream-ordered pool
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     const size_t b_nodes = up(sizeof(BvhNode) * h->n_nodes), b_t32 = up(sizeof(float4) * 3 * n),
-                 b_t64 = up(sizeof(double) * 9 * n), b_vid = up(sizeof(int4) * n), b_inv = up(sizeof(int) * n);
-    cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv, s);
+                 b_t64 = up(sizeof(double) * 9 * n), b_vid = up(sizeof(int4) * n), b_inv = up(sizeof(int) * n),
+                 b_meta = up(4 * sizeof(float));
+    cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta, s);
     if (e != cudaSuccess) {
       delete h;
       return set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -503,6 +523,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     h->tri64 = (double*)(c + b_nodes + b_t32);
     h->tri_vid = (int4*)(c + b_nodes + b_t32 + b_t64);
     h->inv = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid);
+    h->meta = (float*)(c + b_nodes + b_t32 + b_t64 + b_vid + b_inv);
   }
 
   // scratch: one block, carved up
@@ -582,23 +603,22 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   }
   HD_TRY_LAUNCH();
 
-  unsigned flags_host[2] = {0, 0};
-  HD_TRY(cudaMemcpyAsync(flags_host, misc + 6, 8, cudaMemcpyDeviceToHost, s));
+  k_build_meta<<<1, 1, 0, s>>>(misc, h->meta);
+  HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(scratch, s));
   if (Vtmp) HD_TRY(cudaFreeAsync(Vtmp, s));
   if (Ftmp) HD_TRY(cudaFreeAsync(Ftmp, s));
-  HD_TRY(cudaStreamSynchronize(s));
-  uint32_t e2_bits = flags_host[1];
-  float e2;
-  memcpy(&e2, &e2_bits, 4);
-  // eta = sqrt(e2), rounded up
-  double r = std::sqrt((double)e2) * (1.0 + 1e-15);
-  float eta = (float)r;
-  if ((double)eta < r) eta = std::nextafter(eta, INFINITY);
-  h->eta = eta;
-  if (flags_host[0]) {
-    hd_free_B(h);
-    return HD_ERR_INVALID;
+  if (!(o.flags & HD_FLAG_ASYNC_BUILD)) {
+    float meta[2] = {0.f, 0.f};
+    HD_TRY(cudaMemcpyAsync(meta, h->meta, sizeof meta, cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaStreamSynchronize(s));
+    h->eta = meta[0];
+    uint32_t bad_bits;
+    memcpy(&bad_bits, &meta[1], 4);
+    if (bad_bits != 0u) {
+      hd_free_B(h);
+      return HD_ERR_INVALID;
+    }
   }
   *out = h;
   return HD_OK;

@@ -728,12 +728,13 @@ struct PolicyM {
     c.leaf += t.evals;
     c.escalations += t.esc;
     v.tri = t.best;
-    v.dhi = __fadd_ru(t.best_hi, B.eta);
-    v.dlo = fmaxf(__fsub_rd(fminf(t.dlo, t.best_hi), B.eta), 0.f);
+    const float eta = __ldg(B.meta);
+    v.dhi = __fadd_ru(t.best_hi, eta);
+    v.dlo = fmaxf(__fsub_rd(fminf(t.dlo, t.best_hi), eta), 0.f);
     v.qx = t.q.x;
     v.qy = t.q.y;
     v.qz = t.q.z;
-    v.qerr = __fadd_ru(t.qerr, B.eta);
+    v.qerr = __fadd_ru(t.qerr, eta);
   }
   __device__ static double lower(const Vtx& v) { return v.dlo; }
   __device__ static double out_dist(const Vtx& v) { return v.dhi; }

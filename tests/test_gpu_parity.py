@@ -242,6 +242,46 @@ def test_face_split_pair_gpu(hd, orc, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_async_build_matches_sync(hd, orc, precision):
+    """HD_FLAG_ASYNC_BUILD returns before the build ends; the run that follows on the stream
+    gives a bracket within eps that meets the synchronous build's and the oracle's."""
+    p = mg.workload(2, 0.02)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    oa = hd.hd_options_default(tol_mode=p.tol_mode, precision=prec, flags=hd.HD_FLAG_ASYNC_BUILD)
+    os_ = hd.hd_options_default(tol_mode=p.tol_mode, precision=prec)
+    ra = hd.hd_hausdorff(hd.hd_build_B(p.VB, p.FB, oa), p.VA, p.FA, p.tol, oa)
+    rs = hd.hd_hausdorff(hd.hd_build_B(p.VB, p.FB, os_), p.VA, p.FA, p.tol, os_)
+    ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    eps = p.tol * _dA(p.VA, p.FA)
+    for r in (ra, rs):
+        assert r["status"] == hd.HD_OK and r["upper"] - r["lower"] <= eps * (1 + 1e-12)
+        assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + 1e-12 * eps
+    # float64 B: eta comes from the device in both modes
+    V64 = np.asarray(p.VB, np.float64) + 1e-9
+    for o in (oa, os_):
+        r = hd.hd_hausdorff(hd.hd_build_B(V64, p.FB, o), p.VA, p.FA, p.tol, o)
+        assert r["status"] == hd.HD_OK
+
+
+@pytest.mark.parametrize("what", ["index", "nan"])
+def test_async_build_invalid_B_reported_by_the_run(hd, what):
+    """An invalid B built asynchronously is reported by the first bracket call that uses it
+    (the synchronous build reports it itself)."""
+    p = mg.workload(1)
+    VB, FB = np.array(p.VB, dtype=np.float64), np.array(p.FB, copy=True)
+    if what == "index":
+        FB[3, 1] = len(VB) + 7
+    else:
+        VB[FB[5, 0], 2] = np.nan
+    oa = hd.hd_options_default(tol_mode=hd.HD_TOL_ABS, flags=hd.HD_FLAG_ASYNC_BUILD)
+    bvh = hd.hd_build_B(VB, FB, oa)  # queued, not checked yet
+    with pytest.raises(hd.HdError):
+        hd.hd_hausdorff(bvh, p.VA, p.FA, 1e-4, oa)
+    with pytest.raises(hd.HdError):
+        hd.hd_build_B(VB, FB)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_parent_clamp_on_and_off(hd, orc, precision):
     """Clamping a child's U to its parent's is sound (the child lies inside the parent): with
     and without it the bracket is within eps and meets the oracle's."""
