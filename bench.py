@@ -45,9 +45,10 @@ FLOPS_PER_LEAF_TEST = 80
 FLOPS_PER_BOX_TEST = 17
 FLOPS_PER_ITEM_BOUND = 100
 BYTES_PER_NODE = 128
-# device->host bytes per step: build flags (8); with round 0 the device-side parameters (32)
-# and A's validity flag (8); one run state (160 B) per round plus round 0
-RUNSTATE_BYTES = 160
+# device->host bytes per step (the build is queued without a read-back): a run-state
+# snapshot (216 B) and the device-side parameters (32 B) per queued frontier round, plus the
+# final state after a round queued past the last (runs of 3 or more rounds)
+RUNSTATE_BYTES = 216
 
 
 def parse():
@@ -202,8 +203,9 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> in
     when B needs more than 64 sort tiles), the gather, then the radix tree, the refit and
     the node emission (one root kernel instead when B fits in one leaf); A's referenced vertices,
     validation with pool set-up, and the tolerance (3), round 0 (query, bound faces), 4 per
-    frontier round (reset, select, query, bound children), and in MIXED the u4 pass after
-    every bound kernel."""
+    frontier round (control, select, query, bound children), and in MIXED the u4 pass after
+    every bound kernel; runs of 3 or more rounds also queue one round after the last, whose
+    kernels find the loop stopped and return at once."""
     bits = 10
     while bits < 16 and (1 << (3 * (bits - 4))) < nB:
         bits += 1
@@ -212,7 +214,8 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> in
     fused = -(-nB // tile) <= 64
     build = 2 + passes * (2 if fused else 3) + 1 + (3 if nB > leaf_size else 1)
     rounds = stats["rounds"]
-    run = 3 + 2 + 4 * rounds + ((1 + rounds) if mixed else 0)
+    full = rounds + 1 if rounds >= 3 else max(rounds, 1)
+    run = 3 + 2 + (1 if mixed else 0) + (5 if mixed else 4) * full
     return build + run
 
 
@@ -320,7 +323,9 @@ def run_ours(args):
     e2e_total = sum(e2e_ts)
     e2e_total = multi.max_over_ranks(e2e_total, device=dev)
     h2d = p.VA.nbytes + p.FA.nbytes + p.VB.nbytes + p.FB.nbytes
-    d2h = 8 + 32 + 8 + (e2e_r["stats"]["rounds"] + 1) * RUNSTATE_BYTES
+    rnd = e2e_r["stats"]["rounds"]
+    d2h = ((rnd + 1 if rnd >= 3 else max(rnd, 1)) * (RUNSTATE_BYTES + 32) +
+           ((RUNSTATE_BYTES + 32) if rnd >= 3 else 0))
 
     # roofline of the dominant kernel kind, from the trace of the timed steps
     stats = [r["stats"] for r in rs]

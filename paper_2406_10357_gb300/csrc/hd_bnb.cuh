@@ -144,10 +144,17 @@ static __global__ void k_prep_finish(unsigned long long* box, double tol, int to
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.
 template <class P>
 __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
-                        RunState* st, double slack_in, const DynParams* dyn) {
-  const double slack = dyn ? dyn->slack : slack_in;
+                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints) {
   int count = cap;
-  if (count_ptr) count = min(*count_ptr * mult, cap);
+  if (round_midpoints) {
+    // the midpoints of this frontier round: 3 per split, from the pool size at its start
+    if (st->stop) return;  // the loop ended before this round (uniform over the grid)
+    beg = st->n_pool;
+    count = 3 * min(st->n_split, st->K);
+  } else if (count_ptr) {
+    count = min(*count_ptr * mult, cap);
+  }
+  const double slack = dyn ? dyn->slack : slack_in;
   Counters c;
   double lmax = 0.0;
   int nq = 0;
@@ -330,6 +337,7 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
 template <class P>
 __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
                            RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
+  if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const RunParams rp = with_dyn(rp_in);
   int n = min(*(volatile int*)&st->n_u4, cap);
   const Level<P> lv = block_level<P>(st, rp.eps);
@@ -353,23 +361,24 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
 // rest (three midpoints each into the pool at mbase), carry the others over.
 template <class P>
-__global__ void k_select(const typename P::Item* front, int n_front, RunState* st, RunParams rp_in, int K,
-                         int4* split_par, typename P::Vtx* pool, int mbase, typename P::Item* next, int next_cap,
-                         typename P::Item* promo, int promo_cap) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_select(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
+                         typename P::Vtx* pool, typename P::Item* next, int next_cap, typename P::Item* promo,
+                         int promo_cap) {
+  if (st->stop) return;  // the loop ended before this round (uniform over the grid)
+  const int n_front = st->n_front, K = st->K, mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
   const Level<P> lv = block_level<P>(st, rp.eps);
   const Thresholds<P>& th = lv.th;
   const double l = lv.l;
   Tally<P> ty;
-  if (i < n_front) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_front; i += gridDim.x * blockDim.x) {
     typename P::Item it = front[i];
     double U = (double)it.U;
     if (it.U < th.lo) {
       ty.discard(5);
     } else if (it.U <= th.hi) {
-      ty.uret = it.U;
-      ty.retired = 1;
+      ty.uret = ty.uret > it.U ? ty.uret : it.U;
+      ++ty.retired;
     } else {
       typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
       if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
@@ -395,7 +404,7 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
           int j = warp_slot(&st->n_next);
           if (j < next_cap) {
             next[j] = it;
-            ty.umax = it.U;
+            ty.umax = ty.umax > it.U ? ty.umax : it.U;
           } else {
             atomicExch(&st->overflow, 1);
           }
@@ -409,11 +418,12 @@ __global__ void k_select(const typename P::Item* front, int n_front, RunState* s
 // The four children of every split (Section 4, midpoint subdivision):
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
 template <class P>
-__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par, int K, int mbase,
-                                 RunState* st, RunParams rp_in, typename P::Item* next, int next_cap,
-                                 typename P::Item* u4list) {
+__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par, RunState* st,
+                                 RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
+  if (st->stop) return;  // the loop ended before this round (uniform over the grid)
+  const int mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
-  int S = min(*(volatile int*)&st->n_split, K);
+  int S = min(*(volatile int*)&st->n_split, st->K);
   const Level<P> lv = block_level<P>(st, rp.eps);
   const Thresholds<P>& th = lv.th;
   Counters c;
@@ -442,13 +452,97 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
   flush_tally(st, ty);
 }
 
-static __global__ void k_round_reset(RunState* st, int n_front) {
-  st->n_front = n_front;
+// Per-loop constants of the round control.
+struct RoundCtl {
+  long long chunk, pool_cap, front_cap;
+  long long splits_left;  // splits allowed by the face cap m n_A (Section 4) for this loop
+  long long rounds_left;  // rounds before HD_ERR_TIMEOUT for this loop
+  const unsigned long long* bad;  // A's and B's invalid-input flags
+};
+
+__host__ __device__ inline double state_bits_to_double(unsigned long long b) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)b);
+#else
+  double d;
+  memcpy(&d, &b, 8);
+  return d;
+#endif
+}
+__host__ __device__ inline unsigned long long state_double_to_bits(double d) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(d);
+#else
+  unsigned long long b;
+  memcpy(&b, &d, 8);
+  return b;
+#endif
+}
+
+// The end of a frontier round, on a run state: its splits and pool growth, the new frontier,
+// and u as the running minimum of max(l, retired U, frontier U, promoted U).  Returns why the
+// loop ends (HD_OK when the frontier is empty, Section 3.1; CAPACITY, TIMEOUT, NUMERIC,
+// INVALID), or -1 to go on.  Run by k_round_ctl on the device, and by the host on the last
+// state it read when no round was queued after it.
+__host__ __device__ inline int close_round(RunState& st, long long rounds_left) {
+  if (st.in_round) {
+    const int S = st.n_split < st.K ? st.n_split : st.K;
+    st.rounds += 1;
+    st.splits += S;
+    st.n_pool += 3 * S;
+    st.in_round = 0;
+  }
+  const int n_front = st.n_next;
+  st.n_front = n_front;
+  if (n_front > st.peak) st.peak = n_front;
+  double u = fmax(state_bits_to_double(st.l_bits), state_bits_to_double(st.uret_bits));
+  if (n_front) u = fmax(u, state_bits_to_double(st.umax_bits));
+  if (st.n_promote) u = fmax(u, state_bits_to_double(st.upro_bits));
+  if (u < state_bits_to_double(st.urun_bits)) st.urun_bits = state_double_to_bits(u);
+  if (st.bad) return HD_ERR_INVALID;
+  if (st.err) return HD_ERR_NUMERIC;
+  if (st.overflow) return HD_ERR_CAPACITY;
+  if (n_front == 0) return HD_OK;
+  if (st.rounds >= rounds_left) return HD_ERR_TIMEOUT;
+  return -1;
+}
+
+// Start of a frontier round, on the device: closes the round before it, decides whether the
+// loop goes on, and if so sizes and opens the round.  With init set it first starts the loop
+// (pool entries [0, n_pool0), after the bounds of its first items -- the faces of A, or the
+// promoted items -- were launched).  Once stopped, later rounds find `stop` set and do
+// nothing, so the host may queue a round before it has read the previous one.
+static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_pool0) {
+  if (init) {
+    st->stop = 0;
+    st->status = HD_OK;
+    st->in_round = 0;
+    st->rounds = st->splits = st->peak = 0;
+    st->urun_bits = (unsigned long long)__double_as_longlong(INFINITY);
+    st->n_pool = n_pool0;
+  }
+  if (st->stop) return;
+  st->bad = *c.bad;
+  int status = close_round(*st, c.rounds_left);
+  long long K = 0;
+  if (status < 0) {
+    K = min(c.chunk, (c.pool_cap - (long long)st->n_pool) / 3);
+    K = min(K, (c.front_cap - (long long)st->n_front) / 3);
+    K = min(K, c.splits_left - st->splits);
+    if (K <= 0) status = HD_ERR_CAPACITY;
+  }
+  if (status >= 0) {
+    st->status = status;
+    st->stop = 1;
+    return;
+  }
+  st->K = (int)K;
   st->n_next = 0;
   st->n_split = 0;
   st->n_u4 = 0;
   st->umax_bits = 0;
   st->overflow = 0;
+  st->in_round = 1;
 }
 
 // Nearest queries for external points (hd_nearest): P as double rows.
@@ -567,18 +661,45 @@ void free_rounds(Rounds<P>& R, cudaStream_t s) {
   R.base = nullptr;
 }
 
-inline double round_upper(const RunState* h, int64_t n_front) {
-  double u = std::max(bits_to_double(h->l_bits), bits_to_double(h->uret_bits));
-  if (n_front) u = std::max(u, bits_to_double(h->umax_bits));
-  if (h->n_promote) u = std::max(u, bits_to_double(h->upro_bits));
-  return u;
+// Pinned host memory the round loop reads into: the final run state and parameters, and a
+// ring of two per-round snapshots, with the events that mark them complete.  Kept for the
+// thread's lifetime and released when it exits.
+struct HostBlock {
+  RunState st;
+  RunState ring[2];
+  DynParams dyn;
+};
+struct HostRes {
+  HostBlock* hb = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  ~HostRes() {
+    if (hb) cudaFreeHost(hb);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+  }
+};
+inline int host_res(HostRes*& out) {
+  static thread_local HostRes r;
+  if (!r.hb) HD_TRY(cudaMallocHost((void**)&r.hb, sizeof(HostBlock)));
+  for (cudaEvent_t& e : r.ev)
+    if (!e) HD_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  out = &r;
+  return HD_OK;
 }
 
-// Frontier rounds of policy P until the frontier is empty, the capacity or round limit is
-// reached, or an error is flagged.  *status receives HD_OK/CAPACITY/TIMEOUT/NUMERIC.
+// Frontier rounds of policy P over the items that the bound kernel before it left in
+// R.front[R.cur] (their count in st->n_next), until the frontier is empty, the capacity or
+// round limit is reached, or an error is flagged.  Each round starts with k_round_ctl, which
+// closes the previous round and sizes this one on the device.  The first two rounds are
+// queued one at a time, with grids sized from the frontier the host has just read; from the
+// third on (runs with many rounds), the host keeps one round queued ahead of the one it is
+// reading, so the GPU does not wait for the host between rounds, with grids sized from a
+// bound on the frontier (4 children per item); the round queued after the last one finds
+// the loop stopped and does nothing.  On return hr.hb->st and ->dyn hold the final state, T
+// is updated and *status says why the loop ended.
 template <class P>
-int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, RunState* hst, const RunParams& rp, Totals& T,
-                int* status) {
+int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const RunParams& rp, Totals& T,
+                int* status, const unsigned long long* bad, int n_pool0, int64_t first_front_bound) {
   const Opts& o = *io.o;
   cudaStream_t s = io.s;
   BvhDev B = bvh_dev(io.B);
@@ -587,55 +708,90 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, RunState* hst, cons
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const unsigned max_grid = (unsigned)sms * 16;
-  const double face_cap = o.max_face_factor * (double)io.nFA;
-  while (*status == HD_OK && R.n_front > 0) {
-    if (T.rounds >= o.max_rounds) {
-      *status = HD_ERR_TIMEOUT;
-      break;
-    }
-    int64_t K = std::min<int64_t>(R.chunk, (R.pool_cap - R.n_pool) / 3);
-    K = std::min<int64_t>(K, (R.front_cap - R.n_front) / 3);
-    double cap_left = std::floor((face_cap - (double)io.nFA) / 4.0) - (double)T.splits;
-    K = std::min<int64_t>(K, (int64_t)std::max(0.0, std::min(cap_left, 9.0e18)));
-    if (K <= 0) {
-      *status = HD_ERR_CAPACITY;
-      break;
-    }
+  RoundCtl c;
+  c.chunk = R.chunk;
+  c.pool_cap = R.pool_cap;
+  c.front_cap = R.front_cap;
+  const double cap_splits = std::floor((o.max_face_factor * (double)io.nFA - (double)io.nFA) / 4.0);
+  c.splits_left = (long long)std::max(0.0, std::min(cap_splits - (double)T.splits, 9.0e18));
+  c.rounds_left = std::max<long long>(0, o.max_rounds - T.rounds);
+  c.bad = bad;
+  int64_t front_bound = first_front_bound;  // the first round is queued without a wait
+  int cur = R.cur;
+  bool init = true;
+  auto issue = [&](int slot, int64_t nf) -> int {
+    // grids for a frontier of at most nf items (grid-stride kernels: any size is correct)
+    const int64_t k = std::max<int64_t>(1, std::min<int64_t>(nf, R.chunk));
+    const unsigned g_sel = std::min(blocks_for(std::max<int64_t>(nf, 1), 256), (unsigned)sms * 8);
+    const unsigned g_q = std::min(blocks_for(3 * k, bs), max_grid), g_b = std::min(blocks_for(4 * k, bs), max_grid);
     {
       TraceScope tr(HD_K_SELECT, s);
-      k_round_reset<<<1, 1, 0, s>>>(st, (int)R.n_front);
-      k_select<P><<<blocks_for(R.n_front, 256), 256, 0, s>>>(R.front[R.cur], (int)R.n_front, st, rp, (int)K,
-                                                             R.split_par, R.pool, (int)R.n_pool, R.front[R.cur ^ 1],
-                                                             (int)R.front_cap, R.promo, (int)R.promo_cap);
+      k_round_ctl<<<1, 1, 0, s>>>(st, c, init ? 1 : 0, n_pool0);
+      init = false;
+      k_select<P><<<g_sel, 256, 0, s>>>(R.front[cur], st, rp, R.split_par, R.pool, R.front[cur ^ 1],
+                                        (int)R.front_cap, R.promo, (int)R.promo_cap);
     }
     {
       TraceScope tr(HD_K_QUERY, s);
-      unsigned gq = std::min(blocks_for(3 * K, bs), max_grid);
-      k_query<P><<<gq, bs, 0, s>>>(B, R.pool, (int)R.n_pool, &st->n_split, 3, (int)(3 * K), st, rp.slack, rp.dyn);
+      k_query<P><<<g_q, bs, 0, s>>>(B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true);
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      unsigned gb = std::min(blocks_for(4 * K, bs), max_grid);
-      k_bound_children<P><<<gb, bs, 0, s>>>(B, R.pool, R.split_par, (int)K, (int)R.n_pool, st, rp,
-                                            R.front[R.cur ^ 1], (int)R.front_cap, R.u4list);
+      k_bound_children<P><<<g_b, bs, 0, s>>>(B, R.pool, R.split_par, st, rp, R.front[cur ^ 1], (int)R.front_cap,
+                                             R.u4list);
       if (R.u4list)
-        k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[R.cur ^ 1],
-                                              (int)R.front_cap);
+        k_bound_u4<P><<<g_b, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
+                                         (int)R.front_cap);
     }
     HD_TRY_LAUNCH();
-    HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
-    HD_TRY(cudaStreamSynchronize(s));
-    int64_t S = std::min<int64_t>(hst->n_split, K);
-    ++T.rounds;
-    T.splits += S;
-    R.n_pool += 3 * S;
-    R.cur ^= 1;
-    R.n_front = hst->n_next;
-    T.peak = std::max(T.peak, R.n_front);
-    T.u_run = std::min(T.u_run, round_upper(hst, R.n_front));
-    if (hst->overflow) *status = HD_ERR_CAPACITY;
-    if (hst->err) *status = HD_ERR_NUMERIC;
+    cur ^= 1;
+    HD_TRY(cudaMemcpyAsync(&hr.hb->ring[slot], st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaEventRecord(hr.ev[slot], s));
+    return HD_OK;
+  };
+  long long issued = 0, seen = 0;
+  for (;;) {
+    const long long ahead = seen >= 2 ? 2 : 1;  // rounds in flight, the one being read included
+    while (issued < seen + ahead) {
+      int rc = issue((int)(issued & 1), front_bound);
+      if (rc != HD_OK) return rc;
+      ++issued;
+      front_bound = std::min<int64_t>(4 * front_bound, R.front_cap);  // for a round queued ahead
+    }
+    HD_TRY(cudaEventSynchronize(hr.ev[seen & 1]));
+    const RunState& h = hr.hb->ring[seen & 1];
+    ++seen;
+    // the next round's frontier is h.n_next; one more round ahead may have up to 4x as many
+    front_bound = issued == seen ? (int64_t)h.n_next : std::min<int64_t>(4 * (int64_t)h.n_next, R.front_cap);
+    // over once a round stopped, or when the next round's control will stop it
+    const bool done = h.stop || h.n_next == 0 || h.overflow || h.err || h.bad ||
+                      h.rounds + (h.in_round ? 1 : 0) >= c.rounds_left;
+    if (done) break;
   }
+  if (issued == seen) {
+    // nothing queued after the last round read: that state is final once the round is closed
+    // (the same closing step k_round_ctl would take); the parameters were read with it
+    hr.hb->st = hr.hb->ring[(seen - 1) & 1];
+    RunState& f = hr.hb->st;
+    if (!f.stop) {
+      const int r = close_round(f, c.rounds_left);
+      f.status = r >= 0 ? r : HD_ERR_CAPACITY;  // -1 cannot happen here: the loop was done
+      f.stop = 1;
+    }
+  } else {
+    HD_TRY(cudaMemcpyAsync(&hr.hb->st, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaStreamSynchronize(s));
+  }
+  const RunState& f = hr.hb->st;
+  T.rounds += f.rounds;
+  T.splits += f.splits;
+  T.peak = std::max<int64_t>(T.peak, f.peak);
+  T.u_run = std::min(T.u_run, bits_to_double(f.urun_bits));
+  R.n_pool = f.n_pool;
+  R.n_front = f.n_front;
+  *status = f.status;
   return HD_OK;
 }
 
@@ -663,9 +819,20 @@ __global__ void k_promote_init(const typename P::Item* promo, int n, const typen
 
 // Final certification (a7): sub-triangles whose gap the FP32 error radius cannot resolve are
 // re-queried and bounded in FP64 (with the same slack margin) and refined to the end there.
+// Start of the FP64 phase: an empty next frontier and no promotions.
+static __global__ void k_phase_reset(RunState* st) {
+  st->n_next = 0;
+  st->n_split = 0;
+  st->n_u4 = 0;
+  st->umax_bits = 0;
+  st->overflow = 0;
+  st->upro_bits = 0;
+  st->n_promote = 0;
+}
+
 template <class P>
-int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, RunState* hst, const RunParams& rp,
-                   Totals& T, int* status) {
+int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, HostRes& hr, const RunParams& rp,
+                   Totals& T, int* status, const unsigned long long* bad) {
   cudaStream_t s = io.s;
   const Opts& o = *io.o;
   BvhDev B = bvh_dev(io.B);
@@ -681,16 +848,13 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   {
     TraceScope tr(HD_K_PREP, s);
     k_promote_init<P><<<blocks_for(n_pro, 256), 256, 0, s>>>(RM.promo, (int)n_pro, RM.pool, D.pool, tris);
-    k_round_reset<<<1, 1, 0, s>>>(st, 0);
+    k_phase_reset<<<1, 1, 0, s>>>(st);
   }
   HD_TRY_LAUNCH();
-  HD_TRY(cudaMemsetAsync(&st->upro_bits, 0, sizeof(unsigned long long), s));
-  HD_TRY(cudaMemsetAsync(&st->n_promote, 0, sizeof(int), s));
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, 0, nullptr, 1,
-                                                                                 (int)(3 * n_pro), st, rp.slack,
-                                                                                 rp.dyn);
+    k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(
+        B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false);
   }
   {
     TraceScope tr(HD_K_BOUND, s);
@@ -701,14 +865,8 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
                                                                                    nullptr, 3 * n_pro);
   }
   HD_TRY_LAUNCH();
-  HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
-  HD_TRY(cudaStreamSynchronize(s));
-  D.n_pool = 3 * n_pro;
-  D.n_front = hst->n_next;
   D.cur = 1;
-  T.u_run = std::min(T.u_run, round_upper(hst, D.n_front));
-  if (hst->overflow) *status = HD_ERR_CAPACITY;
-  rc = loop_rounds<PolicyD>(io, D, st, hst, rp, T, status);
+  rc = loop_rounds<PolicyD>(io, D, st, hr, rp, T, status, bad, (int)(3 * n_pro), n_pro);
   cudaFreeAsync(tris, s);
   free_rounds(D, s);
   return rc;
@@ -721,21 +879,11 @@ int run_bnb(const RunIO& io) {
   hd_result& res = *io.out;
   memset(&res, 0, sizeof res);
 
-  struct HostBlock {
-    RunState st;
-    DynParams dyn;
-    unsigned long long bad;
-  };
-  // pinned read-back buffer, kept for the thread's lifetime and released when it exits
-  struct Holder {
-    HostBlock* p = nullptr;
-    ~Holder() {
-      if (p) cudaFreeHost(p);
-    }
-  };
-  static thread_local Holder holder;
-  if (!holder.p) HD_TRY(cudaMallocHost((void**)&holder.p, sizeof(HostBlock)));
-  HostBlock* hb = holder.p;
+  HostRes* hr = nullptr;
+  {
+    const int rh = host_res(hr);
+    if (rh != HD_OK) return rh;
+  }
 
   // small per-call device block: referenced-vertex flags, A's bbox + invalid flag, the
   // device-side parameters, and the run state
@@ -762,7 +910,6 @@ int run_bnb(const RunIO& io) {
     cudaFreeAsync(small, s);
     return rc;
   }
-  RunState* hst = &hb->st;
 
   BvhDev B = bvh_dev(io.B);
   RunParams rp;
@@ -784,7 +931,7 @@ int run_bnb(const RunIO& io) {
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
-                                                                       rp.slack, rp.dyn);
+                                                                       rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
   {
@@ -796,37 +943,26 @@ int run_bnb(const RunIO& io) {
                                             (int)R.front_cap);
   }
   HD_TRY_LAUNCH();
-  HD_TRY(cudaMemcpyAsync(hst, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
-  HD_TRY(cudaMemcpyAsync(&hb->dyn, dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
-  HD_TRY(cudaMemcpyAsync(&hb->bad, box + 6, 8, cudaMemcpyDeviceToHost, s));
-  HD_TRY(cudaStreamSynchronize(s));
-  if (hb->bad != 0ull) {  // invalid A (low word) or B (high word): nothing of round 0 is used
-    free_rounds(R, s);
-    cudaFreeAsync(small, s);
-    return HD_ERR_INVALID;
-  }
-  res.stats.dA = hb->dyn.dA;
-  res.stats.eps_abs = hb->dyn.eps;
-  rp.eps = hb->dyn.eps;  // host copies, for the FP64 phase's own parameter block
-  rp.slack = hb->dyn.slack;
-  rp.slack_f = hb->dyn.slack_f;
 
+  // frontier rounds; A's and B's validity is read with the first of them (their results are
+  // not used when either is invalid)
+  const unsigned long long* bad = box + 6;
   Totals T;
   R.cur = 1;
-  R.n_pool = io.nVA;
-  R.n_front = hst->n_next;
-  T.peak = R.n_front;
-  T.u_run = round_upper(hst, R.n_front);
-  int status = hst->overflow ? HD_ERR_CAPACITY : HD_OK;
-  rc = loop_rounds<P>(io, R, st, hst, rp, T, &status);
-  int64_t n_pro = hst->n_promote;
+  int status = HD_OK;
+  rc = loop_rounds<P>(io, R, st, *hr, rp, T, &status, bad, (int)io.nVA, io.nFA);
+  if (rc == HD_OK && status == HD_ERR_INVALID) rc = HD_ERR_INVALID;
+  const int64_t n_pro = hr->hb->st.n_promote;
   if (rc == HD_OK && status == HD_OK && n_pro > 0)
-    rc = finish_in_fp64<P>(io, R, std::min<int64_t>(n_pro, R.promo_cap), st, hst, rp, T, &status);
+    rc = finish_in_fp64<P>(io, R, std::min<int64_t>(n_pro, R.promo_cap), st, *hr, rp, T, &status, bad);
   if (rc != HD_OK) {
     free_rounds(R, s);
     cudaFreeAsync(small, s);
     return rc;
   }
+  const RunState* hst = &hr->hb->st;
+  res.stats.dA = hr->hb->dyn.dA;
+  res.stats.eps_abs = hr->hb->dyn.eps;
 
   double l = bits_to_double(hst->l_bits);
   double uret = bits_to_double(hst->uret_bits);
@@ -851,7 +987,7 @@ int run_bnb(const RunIO& io) {
   S.retired = (int64_t)hst->retired;
   S.fp64_escalations = (int64_t)hst->escalations + n_pro;
   S.peak_frontier = T.peak;
-  S.pool_vertices = R.n_pool;
+  S.pool_vertices = io.nVA + 3 * T.splits;
 
   free_rounds(R, s);
   cudaFreeAsync(small, s);

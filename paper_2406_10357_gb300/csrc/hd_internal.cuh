@@ -114,6 +114,15 @@ struct RunState {
   unsigned long long upro_bits;  // max U of those items (double bits)
   unsigned long long evals, box_tests, queries, retired, escalations, leaf_tests;
   unsigned long long discards[6];
+  // round control on the device (k_round_ctl), so that the host can queue a round before it
+  // has read the previous one
+  int K;                         // items that may be split this round
+  int stop;                      // set when the loop is over; later rounds do nothing
+  int status;                    // HD_OK, or why the loop stopped (CAPACITY, TIMEOUT, NUMERIC)
+  int in_round;                  // a frontier round has been opened (its splits are counted)
+  long long rounds, splits, peak;  // of this loop
+  unsigned long long urun_bits;  // running minimum of the round upper bounds (double bits)
+  unsigned long long bad;        // invalid-input flags of A (low word) and B (high word)
 };
 
 // Device view of hd_bvh, passed to kernels by value.
