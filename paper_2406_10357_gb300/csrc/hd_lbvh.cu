@@ -7,7 +7,8 @@
 //   3. a stable LSD radix sort of (code, triangle) pairs, 8-bit digits;
 //   4. the binary radix tree of Karras (HPG 2012) over the sorted codes, ties broken by
 //      position;
-//   5. bottom-up boxes (float, rounded outward so they contain the exact triangles);
+//   5. node boxes (float, rounded outward so they contain the exact triangles), each the
+//      union of the aligned power-of-two blocks of leaves that tile its range;
 //   6. traversal nodes: 128 B each, holding up to four child boxes (a binary node with its
 //      grandchildren); subtrees of at most leaf_size triangles become leaf ranges.
 #include <cmath>
@@ -288,10 +289,8 @@ __device__ inline int delta(const uint64_t* k, int64_t n, int64_t i, int64_t j) 
 }
 
 // Internal node i covers the sorted range [first, last]; its children are encoded as
-// c >= 0 internal, c < 0 leaf ~c.  Parents of internal nodes and leaves are recorded for
-// the bottom-up pass (-1 for the root).
-__global__ void k_karras(const uint64_t* keys, int64_t n, int* left, int* right, int* first, int* last,
-                         int* parent_int, int* parent_leaf) {
+// c >= 0 internal, c < 0 leaf ~c.
+__global__ void k_karras(const uint64_t* keys, int64_t n, int* left, int* right, int* first, int* last) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1) >= 0 ? 1 : -1;
@@ -316,23 +315,12 @@ __global__ void k_karras(const uint64_t* keys, int64_t n, int* left, int* right,
   right[i] = cr;
   first[i] = (int)lo;
   last[i] = (int)hi;
-  if (cl >= 0) parent_int[cl] = (int)i; else parent_leaf[~cl] = (int)i;
-  if (cr >= 0) parent_int[cr] = (int)i; else parent_leaf[~cr] = (int)i;
-  if (i == 0) parent_int[0] = -1;
 }
 
 __device__ inline void load_box(const float4* b, float lo[3], float hi[3]) {
   float4 a = __ldcg(b), c = __ldcg(b + 1);
   lo[0] = a.x; lo[1] = a.y; lo[2] = a.z;
   hi[0] = c.x; hi[1] = c.y; hi[2] = c.z;
-}
-
-// atomicAdd with acquire-release ordering at device scope: the box a thread stored before
-// its update is visible to the thread whose update comes second.
-__device__ inline int atomic_add_acq_rel(int* p, int v) {
-  int old;
-  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
 }
 
 // Traversal reference of child c: a leaf range (first triangle, count <= L) or an inner
@@ -383,25 +371,72 @@ __device__ inline void wide_slots(int c, const float clo[3], const float chi[3],
   }
 }
 
-// Bottom-up boxes: the second child to arrive at a node computes its box.  (Only the box:
-// this pass is a chain of dependent steps as deep as the tree, so it is kept short; the
-// nodes are written afterwards in parallel by k_emit.)
-__global__ void k_refit(int64_t n, const int* left, const int* right, const int* parent_int, const int* parent_leaf,
-                        const float4* leafbox, float4* ibox, int* flags) {
-  int64_t leaf = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (leaf >= n) return;
-  int node = parent_leaf[leaf];
-  while (node >= 0) {
-    if (atomic_add_acq_rel(&flags[node], 1) == 0) return;
-    float lo0[3], hi0[3], lo1[3], hi1[3];
-    int cl = left[node], cr = right[node];
-    load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo0, hi0);
-    load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo1, hi1);
-    __stcg(ibox + 2 * node, make_float4(fminf(lo0[0], lo1[0]), fminf(lo0[1], lo1[1]), fminf(lo0[2], lo1[2]), 0.f));
-    __stcg(ibox + 2 * node + 1,
-           make_float4(fmaxf(hi0[0], hi1[0]), fmaxf(hi0[1], hi1[1]), fmaxf(hi0[2], hi1[2]), 0.f));
-    node = parent_int[node];
+// Boxes of aligned blocks of leaves: level k holds count[k] = ceil(n / 2^k) boxes, box i of
+// level k covering leaves [i 2^k, (i + 1) 2^k) (level 0: the leaf boxes themselves).  Any
+// node's range [first, last] is then the union of at most 2 log2(n) such blocks, so every
+// node's box is found independently (k_node_box) instead of through a bottom-up chain of
+// dependent steps as long as the tree is deep.
+struct LevelOffsets {
+  int off[32];    // first box of level k in the level array (k >= 1)
+  int count[32];  // boxes at level k
+  int levels;     // the top level (count 1)
+};
+
+// Levels k0 + 1 .. k0 + 8 from the m boxes of level k0 at `in`: a block of 256 threads
+// reduces 256 consecutive boxes pairwise in shared memory.
+__global__ void k_levels(const float4* in, int m, float4* lv, LevelOffsets L, int k0) {
+  __shared__ float sb[6][256];
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * 256 + t;
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  if (i < m) load_box(in + 2 * (int64_t)i, lo, hi);
+  for (int a = 0; a < 3; ++a) {
+    sb[a][t] = lo[a];
+    sb[3 + a][t] = hi[a];
   }
+  for (int j = 1; j <= 8 && k0 + j <= L.levels; ++j) {
+    const int width = 256 >> j, k = k0 + j;
+    __syncthreads();
+    float u[6];
+    if (t < width)
+      for (int a = 0; a < 3; ++a) {
+        u[a] = fminf(sb[a][2 * t], sb[a][2 * t + 1]);
+        u[3 + a] = fmaxf(sb[3 + a][2 * t], sb[3 + a][2 * t + 1]);
+      }
+    __syncthreads();
+    if (t < width) {
+      for (int a = 0; a < 6; ++a) sb[a][t] = u[a];
+      const int g = blockIdx.x * width + t;
+      if (g < L.count[k]) {
+        lv[2 * ((int64_t)L.off[k] + g)] = make_float4(u[0], u[1], u[2], 0.f);
+        lv[2 * ((int64_t)L.off[k] + g) + 1] = make_float4(u[3], u[4], u[5], 0.f);
+      }
+    }
+  }
+}
+
+// The box of every inner node, as the union of the aligned blocks that tile its range.
+__global__ void k_node_box(int64_t n, const int* first, const int* last, const float4* leafbox, const float4* lv,
+                           LevelOffsets L, float4* ibox) {
+  int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= n - 1) return;
+  int f = first[x];
+  const int l = last[x];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  while (f <= l) {
+    // the largest aligned block that starts at f and ends by l
+    const int align = f ? __ffs(f) - 1 : 30, span = 31 - __clz(l - f + 1);
+    const int k = min(min(align, span), L.levels);
+    float a[3], b[3];
+    load_box(k ? lv + 2 * ((int64_t)L.off[k] + (f >> k)) : leafbox + 2 * (int64_t)f, a, b);
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = fminf(lo[c], a[c]);
+      hi[c] = fmaxf(hi[c], b[c]);
+    }
+    f += 1 << k;
+  }
+  ibox[2 * x] = make_float4(lo[0], lo[1], lo[2], 0.f);
+  ibox[2 * x + 1] = make_float4(hi[0], hi[1], hi[2], 0.f);
 }
 
 // The 128-byte traversal node of every inner node covering more than L triangles: its
@@ -541,7 +576,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   };
   size_t o_tri = carve(sizeof(double) * 9 * n), o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
          o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
-         o_ibox = carve(32 * n), o_int = carve(4 * 7 * n + 64), o_misc = carve(64);
+         o_ibox = carve(32 * n), o_lv = carve(32 * (n + 64)), o_int = carve(4 * 4 * n + 64), o_misc = carve(64);
   char* scratch = nullptr;
   HD_TRY(cudaMallocAsync((void**)&scratch, off, s));
   double* tri_unsorted = (double*)(scratch + o_tri);
@@ -553,9 +588,9 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   unsigned* hist = (unsigned*)(scratch + o_hist);
   float4* leafbox = (float4*)(scratch + o_leafbox);
   float4* ibox = (float4*)(scratch + o_ibox);
+  float4* lv = (float4*)(scratch + o_lv);
   int* ints = (int*)(scratch + o_int);
-  int *left = ints, *right = ints + n, *first = ints + 2 * n, *last = ints + 3 * n, *pint = ints + 4 * n,
-      *pleaf = ints + 5 * n, *flags = ints + 6 * n;
+  int *left = ints, *right = ints + n, *first = ints + 2 * n, *last = ints + 3 * n;
   // [0..5] centroid box (ordered bits: minima start at all ones), [6] bad, [7] squared eta bits
   unsigned* misc = (unsigned*)(scratch + o_misc);
 
@@ -593,9 +628,23 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
                                                         leafbox, misc + 7);
   HD_TRY_LAUNCH();
   if (n > o.leaf_size) {
-    HD_TRY(cudaMemsetAsync(flags, 0, sizeof(int) * n, s));
-    k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last, pint, pleaf);
-    k_refit<<<blocks_for(n, kThreads), kThreads, 0, s>>>(n, left, right, pint, pleaf, leafbox, ibox, flags);
+    k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last);
+    // aligned-block boxes, 8 levels per launch, then every node's box
+    LevelOffsets L;
+    memset(&L, 0, sizeof L);
+    L.count[0] = (int)n;
+    int total = 0;
+    while (L.count[L.levels] > 1) {
+      const int k = ++L.levels;
+      L.count[k] = (L.count[k - 1] + 1) / 2;
+      L.off[k] = total;
+      total += L.count[k];
+    }
+    for (int k0 = 0; k0 < L.levels; k0 += 8) {
+      const float4* in = k0 ? lv + 2 * (int64_t)L.off[k0] : leafbox;
+      k_levels<<<blocks_for(L.count[k0], 256), 256, 0, s>>>(in, L.count[k0], lv, L, k0);
+    }
+    k_node_box<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, first, last, leafbox, lv, L, ibox);
     k_emit<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, leafbox, ibox,
                                                             h->nodes);
   } else {
