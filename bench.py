@@ -202,7 +202,7 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> in
     build -- centroids, Morton codes, per sort pass a digit count and a scatter (plus a scan
     when B needs more than 64 sort tiles), the gather, then the radix tree, the aligned-block
     boxes (one launch per 8 levels), the node boxes and the node emission (one root kernel
-    instead when B fits in one leaf); A's referenced vertices,
+    instead when B fits in one leaf), and B's eta and validity; A's referenced vertices,
     validation with pool set-up, and the tolerance (3), round 0 (query, bound faces), 4 per
     frontier round (control, select, query, bound children), and in MIXED the u4 pass after
     every bound kernel; runs of 3 or more rounds also queue one round after the last, whose
@@ -214,7 +214,7 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> in
     tile = 256 * (4 if nB <= 64 * 256 * 4 else 16)
     fused = -(-nB // tile) <= 64
     levels = max(1, (nB - 1).bit_length())  # aligned-block levels, 8 per launch
-    build = 2 + passes * (2 if fused else 3) + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1)
+    build = 2 + passes * (2 if fused else 3) + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1) + 1
     rounds = stats["rounds"]
     full = rounds + 1 if rounds >= 3 else max(rounds, 1)
     run = 3 + 2 + (1 if mixed else 0) + (5 if mixed else 4) * full
