@@ -37,6 +37,15 @@ __device__ inline double warp_max(double v) {
   return v;
 }
 
+// The next batch of 32 consecutive items for the calling warp (every lane must call it):
+// warps of a persistent grid take batches until `count` is reached, so the grid's last
+// wave is not left to a few blocks.
+__device__ inline int warp_batch(int* counter) {
+  int base = 0;
+  if ((threadIdx.x & 31) == 0) base = atomicAdd(counter, 32);
+  return __shfl_sync(0xffffffffu, base, 0);
+}
+
 // Flush per-thread counters with one atomic per warp.  Every lane of the warp must call it.
 __device__ inline void flush_counters(RunState* st, const Counters& c) {
   unsigned long long e = warp_sum(c.evals), b = warp_sum(c.boxes), lf = warp_sum(c.leaf),
@@ -158,9 +167,11 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
   Counters c;
   double lmax = 0.0;
   int nq = 0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
+  for (;;) {
+    const int base = warp_batch(&st->q_next);
+    if (base >= count) break;
+    const int t = base + (threadIdx.x & 31);
     bool active = t < count;
-    if (__all_sync(0xffffffffu, !active)) break;
     // every lane of the warp enters the query (the MIXED traversal votes across the warp);
     // lanes without a vertex to query take part as already finished
     typename P::Vtx v;
@@ -304,26 +315,23 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
                               RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list,
                               int64_t n_pool_valid) {
   const RunParams rp = with_dyn(rp_in);
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const Level<P> lv = block_level<P>(st, rp.eps);
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
-  if (f < nFA) {
+  for (;;) {
+    const int64_t base = warp_batch(&st->b_next);
+    if (base >= nFA) break;
+    const int64_t f = base + (threadIdx.x & 31);
+    if (f >= nFA) continue;
     typename P::Item it;
     it.v[0] = FA[3 * f];
     it.v[1] = FA[3 * f + 1];
     it.v[2] = FA[3 * f + 2];
-    // A is validated concurrently (the host checks the flag after round 0): skip bad rows
-    bool ok = it.v[0] >= 0 && it.v[1] >= 0 && it.v[2] >= 0 && it.v[0] < n_pool_valid && it.v[1] < n_pool_valid &&
-              it.v[2] < n_pool_valid;
-    if (!ok) f = nFA;
-  }
-  if (f < nFA) {
-    typename P::Item it;
-    it.v[0] = FA[3 * f];
-    it.v[1] = FA[3 * f + 1];
-    it.v[2] = FA[3 * f + 2];
+    // A is validated concurrently (the host checks the flag with the first round): skip bad rows
+    if (!(it.v[0] >= 0 && it.v[1] >= 0 && it.v[2] >= 0 && it.v[0] < n_pool_valid && it.v[1] < n_pool_valid &&
+          it.v[2] < n_pool_valid))
+      continue;
     int code;
     it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
     classify<P>(st, it, th, code, next, next_cap, u4list, ty);
@@ -428,10 +436,11 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
-    bool active = t < 4 * (int64_t)S;
-    if (__all_sync(0xffffffffu, !active)) break;
-    if (active) {
+  for (;;) {
+    const int64_t base = warp_batch(&st->b_next);
+    if (base >= 4 * (int64_t)S) break;
+    const int64_t t = base + (threadIdx.x & 31);
+    if (t < 4 * (int64_t)S) {
       int s = (int)(t >> 2), k = (int)(t & 3);
       int4 par = split_par[s];
       int m12 = mbase + 3 * s, m23 = m12 + 1, m31 = m12 + 2;
@@ -542,6 +551,8 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
   st->n_u4 = 0;
   st->umax_bits = 0;
   st->overflow = 0;
+  st->q_next = 0;
+  st->b_next = 0;
   st->in_round = 1;
 }
 
@@ -661,6 +672,15 @@ void free_rounds(Rounds<P>& R, cudaStream_t s) {
   R.base = nullptr;
 }
 
+// Blocks of `bs` threads that fill every SM once with `kernel` (at least one per SM): the
+// grid of the persistent kernels, whose warps take batches of work (warp_batch).
+template <typename K>
+unsigned persistent_grid(K kernel, int bs, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return (unsigned)(per_sm * sms);
+}
+
 // Pinned host memory the round loop reads into: the final run state and parameters, and a
 // ring of two per-round snapshots, with the events that mark them complete.  Kept for the
 // thread's lifetime and released when it exits.
@@ -716,6 +736,8 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   c.splits_left = (long long)std::max(0.0, std::min(cap_splits - (double)T.splits, 9.0e18));
   c.rounds_left = std::max<long long>(0, o.max_rounds - T.rounds);
   c.bad = bad;
+  static const unsigned grid_q = persistent_grid(k_query<P>, bs, sms);
+  static const unsigned grid_b = persistent_grid(k_bound_children<P>, bs, sms);
   int64_t front_bound = first_front_bound;  // the first round is queued without a wait
   int cur = R.cur;
   bool init = true;
@@ -723,7 +745,8 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     // grids for a frontier of at most nf items (grid-stride kernels: any size is correct)
     const int64_t k = std::max<int64_t>(1, std::min<int64_t>(nf, R.chunk));
     const unsigned g_sel = std::min(blocks_for(std::max<int64_t>(nf, 1), 256), (unsigned)sms * 8);
-    const unsigned g_q = std::min(blocks_for(3 * k, bs), max_grid), g_b = std::min(blocks_for(4 * k, bs), max_grid);
+    const unsigned g_q = std::min(blocks_for(3 * k, bs), grid_q), g_b = std::min(blocks_for(4 * k, bs), grid_b);
+    const unsigned g_u4 = std::min(blocks_for(4 * k, bs), max_grid);
     {
       TraceScope tr(HD_K_SELECT, s);
       k_round_ctl<<<1, 1, 0, s>>>(st, c, init ? 1 : 0, n_pool0);
@@ -740,8 +763,8 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
       k_bound_children<P><<<g_b, bs, 0, s>>>(B, R.pool, R.split_par, st, rp, R.front[cur ^ 1], (int)R.front_cap,
                                              R.u4list);
       if (R.u4list)
-        k_bound_u4<P><<<g_b, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
-                                         (int)R.front_cap);
+        k_bound_u4<P><<<g_u4, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
+                                          (int)R.front_cap);
     }
     HD_TRY_LAUNCH();
     cur ^= 1;
@@ -821,6 +844,8 @@ __global__ void k_promote_init(const typename P::Item* promo, int n, const typen
 // re-queried and bounded in FP64 (with the same slack margin) and refined to the end there.
 // Start of the FP64 phase: an empty next frontier and no promotions.
 static __global__ void k_phase_reset(RunState* st) {
+  st->q_next = 0;
+  st->b_next = 0;
   st->n_next = 0;
   st->n_split = 0;
   st->n_u4 = 0;
@@ -930,13 +955,15 @@ int run_bnb(const RunIO& io) {
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query<P><<<std::min(blocks_for(io.nVA, bs), max_grid), bs, 0, s>>>(B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
+    k_query<P><<<std::min(blocks_for(io.nVA, bs), persistent_grid(k_query<P>, bs, sms)), bs, 0, s>>>(
+        B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
                                                                        rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_BOUND, s);
-    k_bound_faces<P><<<blocks_for(io.nFA, bs), bs, 0, s>>>(B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
+    k_bound_faces<P><<<std::min(blocks_for(io.nFA, bs), persistent_grid(k_bound_faces<P>, bs, sms)), bs, 0, s>>>(
+        B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
                                                            (int)R.front_cap, R.u4list, io.nVA);
     if (R.u4list)
       k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[1],

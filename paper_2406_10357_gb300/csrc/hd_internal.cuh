@@ -123,6 +123,8 @@ struct RunState {
   long long rounds, splits, peak;  // of this loop
   unsigned long long urun_bits;  // running minimum of the round upper bounds (double bits)
   unsigned long long bad;        // invalid-input flags of A (low word) and B (high word)
+  int q_next, b_next;            // work counters of the query and bound kernels (warps take
+                                 // batches of 32 items until none are left)
 };
 
 // Device view of hd_bvh, passed to kernels by value.
