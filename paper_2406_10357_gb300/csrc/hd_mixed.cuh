@@ -232,11 +232,12 @@ __device__ inline void pt_cert(const FFP& P, float4 a4, float4 b4, float4 c4, bo
   if (__fsub_rd(nq, lo) > __fmul_ru(256.f * kU, M)) pt_escalate(P, a4, b4, c4, M, o);
 }
 
-// Lower bound of |p - box|^2 (downward rounding).
-__device__ inline float box_lo2(const FFP& P, float lx, float ly, float lz, float hx, float hy, float hz) {
-  float gx = fmaxf(fmaxf(__fsub_rd(__fsub_rd(lx, P.h.x), P.l.x), __fadd_rd(__fsub_rd(P.h.x, hx), P.l.x)), 0.f);
-  float gy = fmaxf(fmaxf(__fsub_rd(__fsub_rd(ly, P.h.y), P.l.y), __fadd_rd(__fsub_rd(P.h.y, hy), P.l.y)), 0.f);
-  float gz = fmaxf(fmaxf(__fsub_rd(__fsub_rd(lz, P.h.z), P.l.z), __fadd_rd(__fsub_rd(P.h.z, hz), P.l.z)), 0.f);
+// Lower bound of |p - box|^2 (downward rounding), with p given by an enclosure
+// [plo, phi] of the float pair h + l on each axis (h + l rounded down and up).
+__device__ inline float box_lo2(F3 plo, F3 phi, float lx, float ly, float lz, float hx, float hy, float hz) {
+  float gx = fmaxf(fmaxf(__fsub_rd(lx, phi.x), __fsub_rd(plo.x, hx)), 0.f);
+  float gy = fmaxf(fmaxf(__fsub_rd(ly, phi.y), __fsub_rd(plo.y, hy)), 0.f);
+  float gz = fmaxf(fmaxf(__fsub_rd(lz, phi.z), __fsub_rd(plo.z, hz)), 0.f);
   return __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
 }
 
@@ -308,6 +309,9 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
   int node = active ? 0 : -1;  // inner node to expand next, -1 = none
   int lfirst = 0, lcount = 0;
   bool done = !active;
+  // an enclosure of the query point h + l, for the box bounds
+  const F3 plo = {__fadd_rd(t.P.h.x, t.P.l.x), __fadd_rd(t.P.h.y, t.P.l.y), __fadd_rd(t.P.h.z, t.P.l.z)};
+  const F3 phi = {__fadd_ru(t.P.h.x, t.P.l.x), __fadd_ru(t.P.h.y, t.P.l.y), __fadd_ru(t.P.h.z, t.P.l.z)};
   for (;;) {
     while (!done && lcount == 0) {
       if (node < 0) {
@@ -332,10 +336,10 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
       const uint4 cd = __ldg(reinterpret_cast<const uint4*>(np + 6));
       const float r2 = t.radius2();
       // children within the current radius (the others at +inf), nearest first
-      float e0 = box_lo2(t.P, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);
-      float e1 = box_lo2(t.P, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y);
-      float e2 = box_lo2(t.P, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
-      float e3 = box_lo2(t.P, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
+      float e0 = box_lo2(plo, phi, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);
+      float e1 = box_lo2(plo, phi, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y);
+      float e2 = box_lo2(plo, phi, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z);
+      float e3 = box_lo2(plo, phi, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
       unsigned c0 = cd.x, c1 = cd.y, c2 = cd.z, c3 = cd.w;
       c.boxes += (c0 != kNoChild) + (c1 != kNoChild) + (c2 != kNoChild) + (c3 != kNoChild);
       if (!(e0 <= r2) || c0 == kNoChild) e0 = INFINITY;
