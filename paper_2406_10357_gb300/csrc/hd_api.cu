@@ -158,7 +158,7 @@ __global__ void k_upper_bounds(BvhDev B, const int* inv, const double* T, const 
     }
     t[k] = {{v[0], v[1], v[2]}, Td[3 * i + k], inv[I], {q[0], q[1], q[2]}};
   }
-  unsigned long long ev = 0;
+  unsigned ev = 0;
   int c;
   U[i] = upper_bound_d(B, t, l, rp.order, rp.n_bounds, c, ev);
   code[i] = c;

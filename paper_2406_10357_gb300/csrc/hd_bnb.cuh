@@ -48,8 +48,8 @@ __device__ inline int warp_batch(int* counter) {
 
 // Flush per-thread counters with one atomic per warp.  Every lane of the warp must call it.
 __device__ inline void flush_counters(RunState* st, const Counters& c) {
-  unsigned long long e = warp_sum(c.evals), b = warp_sum(c.boxes), lf = warp_sum(c.leaf),
-                     x = warp_sum(c.escalations);
+  unsigned long long e = warp_sum((unsigned long long)c.evals), b = warp_sum((unsigned long long)c.boxes),
+                     lf = warp_sum((unsigned long long)c.leaf), x = warp_sum((unsigned long long)c.escalations);
   if ((threadIdx.x & 31) == 0) {
     if (e + lf) atomicAdd(&st->evals, e + lf);
     if (lf) atomicAdd(&st->leaf_tests, lf);

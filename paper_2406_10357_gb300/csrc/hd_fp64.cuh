@@ -91,7 +91,7 @@ struct NearestD {
   double best2 = INFINITY;
   int best = -1;
   D3 q = {0, 0, 0};
-  unsigned long long evals = 0;
+  unsigned evals = 0;
   __device__ double radius2() const { return best2; }
   __device__ void test1(int j) {
     D3 a, b, c;
@@ -194,7 +194,7 @@ __device__ inline D3 tri_vertex(const BvhDev& B, int j, int slot) {
 }
 
 // Kang et al. 2018 bound, Eqs. (Kang2018_case1) and (Kang2018_case2).
-__device__ inline double ub_u3(const BvhDev& B, const VI t[3], unsigned long long& evals) {
+__device__ inline double ub_u3(const BvhDev& B, const VI t[3], unsigned& evals) {
   int lone = -1;
   if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
     if (t[1].I == t[2].I) lone = 0;
@@ -296,7 +296,7 @@ __device__ inline double ub_u4(const VI t[3]) {
 
 // UpperBound(T, l) of Section 4.
 __device__ inline double upper_bound_d(const BvhDev& B, const VI t[3], double l, const uint8_t* order, int nb,
-                                       int& code, unsigned long long& evals) {
+                                       int& code, unsigned& evals) {
   if (t[0].I == t[1].I && t[1].I == t[2].I) {
     code = 0;
     return ub_exact(t);

@@ -174,8 +174,10 @@ __device__ inline RunParams with_dyn(RunParams rp) {
 constexpr int kDeferU4 = 6;
 
 // Per-thread statistics, flushed with one atomic per warp.
+// Per-thread work counters, summed over the warp and flushed with 64-bit atomics; 32 bits
+// per thread are ample (a thread handles a few thousand items at most).
 struct Counters {
-  unsigned long long evals = 0, boxes = 0, escalations = 0, leaf = 0;
+  unsigned evals = 0, boxes = 0, escalations = 0, leaf = 0;
   int err = 0;
 };
 

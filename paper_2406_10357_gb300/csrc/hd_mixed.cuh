@@ -249,7 +249,7 @@ struct NearestM {
   int best = -1;
   F3 q = {0.f, 0.f, 0.f};
   float qerr = 0.f;
-  unsigned long long evals = 0, esc = 0;
+  unsigned evals = 0, esc = 0;
   __device__ float radius2() const { return __fmul_ru(best_hi, best_hi); }
   __device__ void test1(int j) {
     const float4* t = tri32 + 3 * (size_t)j;
@@ -485,7 +485,7 @@ __device__ inline FFP along(const VM& base, F3 e, float s, float& beta) {
 // point-triangle distances that are laid out as six evaluation slots, so that the lanes of a
 // warp run the same code whichever case each item is in: case 1 fills four slots, (b1, S1),
 // (b2, S1), (b1, S2), (b2, S2); case 2 fills all six with (v_j, S_i), j != i.
-__device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned long long& evals) {
+__device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned& evals) {
   int lone = -1;
   if (!(t[0].I == t[1].I && t[1].I == t[2].I)) {
     if (t[1].I == t[2].I) lone = 0;
