@@ -48,8 +48,18 @@ __device__ inline float amax3(F3 a) { return fmaxf(fabsf(a.x), fmaxf(fabsf(a.y),
 // Square root and quotient with outward rounding: the correctly rounded (round-to-nearest)
 // result is within half an ulp, so one multiplication by 1 +- 2^-23, rounded outward, bounds
 // the exact value.
-__device__ inline float sqrt_up(float x) { return __fmul_ru(__fsqrt_rn(x), 1.f + 2.f * kU); }
-__device__ inline float sqrt_dn(float x) { return __fmul_rd(__fsqrt_rn(x), 1.f - 2.f * kU); }
+// Square roots rounded up / down, from x * rsqrtf(x): rsqrtf is within 2 ulp (4u relative,
+// the CUDA math library's documented bound) and the product adds u, so the result is within
+// 5u of sqrt(x); one multiplication by 1 +- 8u in the matching direction covers that.  Tiny
+// and infinite arguments take the safe branch (the product would be 0 * inf there).
+__device__ inline float sqrt_up(float x) {
+  if (!(x >= 1e-30f && x < INFINITY)) return x < 1e-30f ? 1e-15f : x;
+  return __fmul_ru(x * rsqrtf(x), 1.f + 8.f * kU);
+}
+__device__ inline float sqrt_dn(float x) {
+  if (!(x >= 1e-30f && x < INFINITY)) return x < 1e-30f ? 0.f : x;
+  return __fmul_rd(x * rsqrtf(x), 1.f - 8.f * kU);
+}
 __device__ inline float div_up(float a, float b) { return __fmul_ru(__fdiv_rn(a, b), 1.f + 2.f * kU); }
 __device__ inline float div_dn(float a, float b) { return __fmul_rz(__fdiv_rn(a, b), 1.f - 2.f * kU); }
 __device__ inline float norm_ru(F3 a) { return sqrt_up(__fmaf_ru(a.x, a.x, __fmaf_ru(a.y, a.y, __fmul_ru(a.z, a.z)))); }
@@ -511,21 +521,24 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned
     const float4* T2 = B.tri32 + 3 * (size_t)S2;
     float4 P0 = __ldg(T1 + fs0), P1 = __ldg(T1 + fs1), O1 = __ldg(T1 + fo), O2 = __ldg(T2 + go);
     F3 p0 = {P0.x, P0.y, P0.z}, ed = F3{P1.x, P1.y, P1.z} - p0;
-    float el = sqrtf(dotf(ed, ed));
-    if (el > 0.f) {
-      F3 eh = {ed.x / el, ed.y / el, ed.z / el};
+    // (plain fast arithmetic: any split parameter in [0, 1] gives a valid bound)
+    const float ee = dotf(ed, ed);
+    if (ee > 0.f) {
+      const float ie = rsqrtf(ee);
+      F3 eh = {ed.x * ie, ed.y * ie, ed.z * ie};
       F3 a1 = F3{O1.x, O1.y, O1.z} - p0, a2 = F3{O2.x, O2.y, O2.z} - p0;
       float k1 = dotf(a1, eh), k2 = dotf(a2, eh);
       F3 w1 = {a1.x - k1 * eh.x, a1.y - k1 * eh.y, a1.z - k1 * eh.z};
       F3 w2 = {a2.x - k2 * eh.x, a2.y - k2 * eh.y, a2.z - k2 * eh.z};
-      float n1 = sqrtf(dotf(w1, w1)), n2 = sqrtf(dotf(w2, w2));
-      if (n1 > 0.f && n2 > 0.f) {
-        F3 nb = {w1.x / n1 - w2.x / n2, w1.y / n1 - w2.y / n2, w1.z / n1 - w2.z / n2};
+      const float q1 = dotf(w1, w1), q2 = dotf(w2, w2);
+      if (q1 > 0.f && q2 > 0.f) {
+        const float i1 = rsqrtf(q1), i2 = rsqrtf(q2);
+        F3 nb = {w1.x * i1 - w2.x * i2, w1.y * i1 - w2.y * i2, w1.z * i1 - w2.z * i2};
         F3 r1 = (v1.p.h - p0) + v1.p.l;
         float sv1 = dotf(nb, r1), sv2 = sv1 + dotf(nb, e12), sv3 = sv1 + dotf(nb, e13);
         if (sv1 >= 0.f && sv2 <= 0.f && sv3 <= 0.f && sv1 - sv2 > 0.f && sv1 - sv3 > 0.f) {
-          s2 = fminf(fmaxf(sv1 / (sv1 - sv2), 0.f), 1.f);
-          s3 = fminf(fmaxf(sv1 / (sv1 - sv3), 0.f), 1.f);
+          s2 = __saturatef(__fdividef(sv1, sv1 - sv2));
+          s3 = __saturatef(__fdividef(sv1, sv1 - sv3));
         }
       }
     }
