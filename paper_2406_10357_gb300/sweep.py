@@ -1,0 +1,100 @@
+"""Timed sweeps over the method's parameters, on one GPU.
+
+orders -- every cascade order of every non-empty subset of {u1, u2, u3, u4} (64 orders; the
+          paper compares cascades in Section 5), timed on a batch of workload-4 pairs.
+tol    -- runtime against the tolerance, from 1e-1 to 1e-8 relative (the paper's runtime
+          versus epsilon study, Section 5), on workloads 2 and 5.
+
+    python -m paper_2406_10357_gb300.sweep orders [--pairs 64] [--precision mixed]
+    python -m paper_2406_10357_gb300.sweep tol [--workloads 2 5] [--scale 1.0]
+
+Each line printed is one JSON record; the inputs are the seeded synthetic workloads of
+``meshgen``.
+"""
+from __future__ import annotations
+
+import argparse
+import itertools
+import json
+import time
+
+
+def all_orders():
+    """The 64 cascade orders: every permutation of every non-empty subset of the four bounds."""
+    return [o for k in range(1, 5) for o in itertools.permutations((1, 2, 3, 4), k)]
+
+
+def _timed(fn, reps: int):
+    import torch
+
+    fn()  # warm-up
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        out = fn()
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+    ts.sort()
+    return ts[len(ts) // 2], out
+
+
+def sweep_orders(n_pairs: int, precision: int, reps: int = 3):
+    import torch
+
+    import meshgen as mg
+    import paper_2406_10357_gb300 as hd
+
+    pairs = mg.batch_workload(n_pairs=n_pairs)
+    dev = [(torch.from_numpy(p.VA).cuda(), torch.from_numpy(p.FA).cuda()) for p in pairs]
+    bvhs = [hd.hd_build_B(torch.from_numpy(p.VB).cuda(), torch.from_numpy(p.FB).cuda()) for p in pairs]
+    for order in all_orders():
+        o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=precision, bound_order=order)
+        t, rs = _timed(lambda: hd.hd_hausdorff_batched(bvhs, dev, pairs[0].tol, o), reps)
+        st = [r["stats"] for r in rs]
+        yield dict(sweep="orders", order=list(order), pairs=n_pairs, seconds=t, pairs_per_s=n_pairs / t,
+                   ok=sum(r["status"] == hd.HD_OK for r in rs), splits=sum(s["splits"] for s in st),
+                   pointtri_evals=sum(s["pointtri_evals"] for s in st),
+                   discards={k: sum(s["discards"][k] for s in st) for k in st[0]["discards"]})
+
+
+def sweep_tol(workloads, scale: float, precision: int, reps: int = 3):
+    import torch
+
+    import meshgen as mg
+    import paper_2406_10357_gb300 as hd
+
+    for k in workloads:
+        p = mg.workload(k, scale)
+        VA, FA = torch.from_numpy(p.VA).cuda(), torch.from_numpy(p.FA).cuda()
+        bvh = hd.hd_build_B(torch.from_numpy(p.VB).cuda(), torch.from_numpy(p.FB).cuda())
+        for e in range(1, 9):
+            tol = 10.0 ** -e
+            o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=precision)
+            t, r = _timed(lambda: hd.hd_hausdorff(bvh, VA, FA, tol, o), reps)
+            yield dict(sweep="tol", workload=k, scale=scale, faces_A=len(p.FA), faces_B=len(p.FB), tol=tol,
+                       seconds=t, lower=r["lower"], upper=r["upper"], status=r["status_str"],
+                       rounds=r["stats"]["rounds"], splits=r["stats"]["splits"],
+                       pointtri_evals=r["stats"]["pointtri_evals"])
+
+
+def main(argv=None):
+    import paper_2406_10357_gb300 as hd
+
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("what", choices=["orders", "tol"])
+    ap.add_argument("--pairs", type=int, default=64)
+    ap.add_argument("--workloads", type=int, nargs="+", default=[2, 5])
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    prec = hd.HD_MIXED if a.precision == "mixed" else hd.HD_FP64
+    rows = sweep_orders(a.pairs, prec, a.reps) if a.what == "orders" else sweep_tol(a.workloads, a.scale, prec, a.reps)
+    for row in rows:
+        row["precision"] = a.precision
+        print(json.dumps(row), flush=True)
+
+
+if __name__ == "__main__":
+    main()
