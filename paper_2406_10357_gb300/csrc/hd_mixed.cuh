@@ -403,42 +403,58 @@ __device__ inline F3 edge(const VM& a, const VM& b) { return (b.p.h - a.p.h) + (
 __device__ inline float len_hi(F3 e) { return __fmul_ru(norm_ru(e), 1.f + 4.f * kU); }
 __device__ inline float len_lo(F3 e) { return __fmul_rd(norm_rd(e), 1.f - 4.f * kU); }
 
-// u1, Eq. (u1), with edge lengths rounded up
-__device__ inline float ubm_u1(const VM t[3]) {
-  float u = INFINITY;
+// The edges of T, e[i] opposite vertex i (v2 - v1, v0 - v2, v1 - v0), and their lengths
+// rounded up: computed once per item for u1 and u2.
+struct EdgesM {
+  F3 e[3];
+  float hi[3];
+  __device__ explicit EdgesM(const VM t[3]) {
+    e[0] = edge(t[1], t[2]);
+    e[1] = edge(t[2], t[0]);
+    e[2] = edge(t[0], t[1]);
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    float e1 = len_hi(edge(t[i], t[(i + 1) % 3])), e2 = len_hi(edge(t[i], t[(i + 2) % 3]));
-    u = fminf(u, __fadd_ru(fmaxf(e1, e2), t[i].dhi));
+    for (int i = 0; i < 3; ++i) hi[i] = len_hi(e[i]);
   }
-  return u;
+};
+
+// u1, Eq. (u1), with edge lengths rounded up: vertex i's two edges are the two not opposite it
+__device__ inline float ubm_u1(const VM t[3], const EdgesM& E) {
+  const float u0 = __fadd_ru(fmaxf(E.hi[1], E.hi[2]), t[0].dhi);
+  const float u1 = __fadd_ru(fmaxf(E.hi[2], E.hi[0]), t[1].dhi);
+  const float u2 = __fadd_ru(fmaxf(E.hi[0], E.hi[1]), t[2].dhi);
+  return fminf(u0, fminf(u1, u2));
 }
 
 // u2, Eq. (u2): g is half the longest edge when T is certainly obtuse (longest edge squared,
 // rounded down, above the sum of the other two squared, rounded up), else the circumradius
 // with the area rounded down.  Acute <=> s - r > 2R, so this is the paper's g wherever the
 // sign of the test is certain, and the circumradius (always a valid g) elsewhere.
-__device__ inline float ubm_u2(const VM t[3]) {
-  F3 e[3] = {edge(t[1], t[2]), edge(t[2], t[0]), edge(t[0], t[1])};
-  float hi[3], lo[3];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    hi[i] = len_hi(e[i]);
-    lo[i] = len_lo(e[i]);
+__device__ inline float ubm_u2(const VM t[3], const EdgesM& E) {
+  // the longest edge k and the other two, selected by branches (no runtime array index, so
+  // the edges stay in registers)
+  F3 ek = E.e[0];
+  float hk = E.hi[0], h1 = E.hi[1], h2 = E.hi[2];
+  if (E.hi[1] > hk && E.hi[1] >= E.hi[2]) {
+    ek = E.e[1];
+    hk = E.hi[1];
+    h1 = E.hi[2];
+    h2 = E.hi[0];
+  } else if (E.hi[2] > hk && E.hi[2] > E.hi[1]) {
+    ek = E.e[2];
+    hk = E.hi[2];
+    h1 = E.hi[0];
+    h2 = E.hi[1];
   }
-  int k = 0;
-  if (hi[1] > hi[k]) k = 1;
-  if (hi[2] > hi[k]) k = 2;
-  int i1 = (k + 1) % 3, i2 = (k + 2) % 3;
+  const float lok = len_lo(ek);
   float g;
-  if (__fmul_rd(lo[k], lo[k]) > __fmaf_ru(hi[i1], hi[i1], __fmul_ru(hi[i2], hi[i2]))) {
-    g = __fmul_ru(0.5f, hi[k]);
+  if (__fmul_rd(lok, lok) > __fmaf_ru(h1, h1, __fmul_ru(h2, h2))) {
+    g = __fmul_ru(0.5f, hk);
   } else {
-    F3 a = e[2], b = {-e[1].x, -e[1].y, -e[1].z};  // v2 - v1 and v3 - v1
+    F3 a = E.e[2], b = {-E.e[1].x, -E.e[1].y, -E.e[1].z};  // v1 - v0 and v2 - v0
     F3 cr = {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
     float err = __fmul_ru(__fmul_ru(32.f * kU, amax3(a)), amax3(b));
     float c2 = __fsub_rd(norm_rd(cr), err);  // lower bound of 2|T|
-    g = c2 > 0.f ? div_up(__fmul_ru(__fmul_ru(hi[0], hi[1]), hi[2]), __fmul_rd(2.f, c2)) : INFINITY;
+    g = c2 > 0.f ? div_up(__fmul_ru(__fmul_ru(E.hi[0], E.hi[1]), E.hi[2]), __fmul_rd(2.f, c2)) : INFINITY;
   }
   return __fadd_ru(g, fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi)));
 }
@@ -659,6 +675,7 @@ __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], float lf, 
   } else {
     U = INFINITY;
     code = 5;
+    const EdgesM E(t);  // shared by u1 and u2
     for (int k = 0; k < rp.n_bounds; ++k) {
       if (rp.order[k] == 4 && k == rp.n_bounds - 1 && rp.defer_u4) {
         // u4 (FP64) is evaluated for all such items together in the u4 pass, with full
@@ -668,8 +685,8 @@ __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], float lf, 
       }
       float u;
       switch (rp.order[k]) {
-        case 1: u = ubm_u1(t); break;
-        case 2: u = ubm_u2(t); break;
+        case 1: u = ubm_u1(t, E); break;
+        case 2: u = ubm_u2(t, E); break;
         case 3: u = ubm_u3(B, t, lf, c.evals); break;
         default: u = ubm_u4(t, rp.slack); break;
       }
