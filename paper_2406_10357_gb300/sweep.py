@@ -4,9 +4,12 @@ orders -- every cascade order of every non-empty subset of {u1, u2, u3, u4} (64 
           paper compares cascades in Section 5), timed on a batch of workload-4 pairs.
 tol    -- runtime against the tolerance, from 1e-1 to 1e-8 relative (the paper's runtime
           versus epsilon study, Section 5), on workloads 2 and 5.
+batch  -- workload 4: the batched call untuned and autotuned (MIXED), against sequential
+          per-pair calls in FP64 at the same tolerance.
 
     python -m paper_2406_10357_gb300.sweep orders [--pairs 64] [--precision mixed]
     python -m paper_2406_10357_gb300.sweep tol [--workloads 2 5] [--scale 1.0]
+    python -m paper_2406_10357_gb300.sweep batch [--pairs 1024] [--tune-pairs 32]
 
 Each line printed is one JSON record; the inputs are the seeded synthetic workloads of
 ``meshgen``.
@@ -78,11 +81,55 @@ def sweep_tol(workloads, scale: float, precision: int, reps: int = 3):
                        pointtri_evals=r["stats"]["pointtri_evals"])
 
 
+def sweep_batch(n_pairs: int, tune_pairs: int, reps: int = 2):
+    """Workload 4: the batched call untuned and autotuned (MIXED), against sequential per-pair
+    calls in FP64, all at the same tolerance."""
+    import torch
+
+    import meshgen as mg
+    import paper_2406_10357_gb300 as hd
+    from paper_2406_10357_gb300 import autotune as at
+
+    pairs = mg.batch_workload(n_pairs=n_pairs)
+    dev = [tuple(torch.from_numpy(x).cuda() for x in (p.VA, p.FA, p.VB, p.FB)) for p in pairs]
+    tol = pairs[0].tol
+    t0 = time.perf_counter()
+    opt_t, table = at.autotune(dev[:tune_pairs], tol, hd.HD_MIXED, tune_order=False)
+    t_tune = time.perf_counter() - t0
+    best = min(table, key=lambda r: r["seconds"])
+    yield dict(sweep="batch", what="autotune", tune_pairs=tune_pairs, seconds=t_tune, candidates=len(table),
+               best={k: best[k] for k in ("block_size", "leaf_size", "frontier_chunk", "bound_order")})
+
+    def run(opt, leaf, batched):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bvhs = [hd.hd_build_B(VB, FB, hd.hd_options_default(leaf_size=leaf)) for (_, _, VB, FB) in dev]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        if batched:
+            rs = hd.hd_hausdorff_batched(bvhs, [(VA, FA) for (VA, FA, _, _) in dev], tol, opt)
+        else:
+            rs = [hd.hd_hausdorff(b, VA, FA, tol, opt) for b, (VA, FA, _, _) in zip(bvhs, dev)]
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        return t1 - t0, t2 - t1, sum(r["status"] == hd.HD_OK for r in rs)
+
+    arms = [("batched MIXED, untuned", hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED), 1, True),
+            ("batched MIXED, autotuned", opt_t, best["leaf_size"], True),
+            ("sequential per-pair FP64", hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64), 1, False)]
+    for name, opt, leaf, batched in arms:
+        res = [run(opt, leaf, batched) for _ in range(reps)]
+        tb, tr, ok = min(res, key=lambda x: x[1])
+        yield dict(sweep="batch", what=name, pairs=n_pairs, build_seconds=tb, run_seconds=tr, pairs_per_s=n_pairs / tr,
+                   pairs_per_s_with_build=n_pairs / (tb + tr), ok=ok)
+
+
 def main(argv=None):
     import paper_2406_10357_gb300 as hd
 
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["orders", "tol"])
+    ap.add_argument("what", choices=["orders", "tol", "batch"])
+    ap.add_argument("--tune-pairs", type=int, default=32)
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--workloads", type=int, nargs="+", default=[2, 5])
     ap.add_argument("--scale", type=float, default=1.0)
@@ -90,7 +137,12 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     a = ap.parse_args(argv)
     prec = hd.HD_MIXED if a.precision == "mixed" else hd.HD_FP64
-    rows = sweep_orders(a.pairs, prec, a.reps) if a.what == "orders" else sweep_tol(a.workloads, a.scale, prec, a.reps)
+    if a.what == "orders":
+        rows = sweep_orders(a.pairs, prec, a.reps)
+    elif a.what == "tol":
+        rows = sweep_tol(a.workloads, a.scale, prec, a.reps)
+    else:
+        rows = sweep_batch(a.pairs, a.tune_pairs, a.reps)
     for row in rows:
         row["precision"] = a.precision
         print(json.dumps(row), flush=True)
