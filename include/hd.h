@@ -164,12 +164,14 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
                      const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba);
 
 /* npairs independent problems h(As[i], Bs[i]) with one tolerance and one option set;
- * outs[i] receives each result.  Up to 8 host threads, each with its own non-blocking
- * stream on the current device, take the pairs in turn, so that the kernels of several
- * small pairs run on the GPU at the same time; they start after the work already queued on
- * `stream`, and every pair is complete when the call returns.  All Bs[i] must live on the
- * current device.  Returns HD_ERR_INVALID (nothing launched) or the first HD_ERR_CUDA, else
- * HD_OK; per-pair CAPACITY/TIMEOUT/NUMERIC are reported in outs[i].status. */
+ * outs[i] receives each result.  Host threads (two per host core, 8 to 64), each with its
+ * own non-blocking stream on the current device, take the pairs in turn, so that the
+ * kernels of several small pairs run on the GPU at the same time; they start after the work
+ * already queued on `stream`, and every pair is complete when the call returns.  All Bs[i]
+ * must live on the current device.  Returns HD_ERR_INVALID when the arguments are invalid
+ * (checked before anything is launched) or a pair's mesh is found invalid on the device,
+ * HD_ERR_CUDA on a CUDA failure, else HD_OK; per-pair CAPACITY/TIMEOUT/NUMERIC are reported
+ * in outs[i].status. */
 int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
                          const hd_options* opt, void* stream, hd_result* outs);
 

@@ -347,12 +347,14 @@ int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npa
   HD_TRY(cudaGetDevice(&dev));
   for (int64_t i = 0; i < npairs; ++i)
     if (!Bs[i] || Bs[i]->device != dev || check_mesh(&As[i]) != HD_OK) return HD_ERR_INVALID;
-  // Pairs are independent: kBatchStreams host threads, each with its own non-blocking
-  // stream, take pairs in turn, so that the kernels of several small pairs share the GPU.
-  // The streams start after the work queued so far on the caller's stream; every pair is
-  // complete when the call returns.
-  constexpr int kBatchStreams = 8;
-  const int nw = (int)std::min<int64_t>(npairs, kBatchStreams);
+  // Pairs are independent: host threads, each with its own non-blocking stream, take pairs
+  // in turn, so that the kernels of several small pairs share the GPU (two threads per host
+  // core, 8 to 64: each thread spends much of a pair waiting for its stream).  The streams
+  // start after the work queued so far on the caller's stream; every pair is complete when
+  // the call returns.
+  const unsigned cores = std::max(1u, std::thread::hardware_concurrency());
+  const int streams = (int)std::min(64u, std::max(8u, 2 * cores));
+  const int nw = (int)std::min<int64_t>(npairs, streams);
   cudaEvent_t start;
   HD_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   cudaError_t e = cudaEventRecord(start, (cudaStream_t)stream);
