@@ -81,7 +81,12 @@ typedef struct {
 /* hd_options.flags.  By default the UpperBound of a child sub-triangle is clamped to its
  * parent's: h(child, B) <= h(parent, B) <= U(parent) since the child lies inside the parent.
  * The paper's cascade (Section 4) has no such clamp; HD_FLAG_NO_PARENT_CLAMP turns it off. */
-enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2 };
+enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2, HD_FLAG_SHARE_MIDPOINTS = 4 };
+/* HD_FLAG_SHARE_MIDPOINTS: an edge split by two sub-triangles in the same round gets one
+ * midpoint vertex (and one nearest query) instead of two, through a per-round hash table of
+ * split edges.  Results are the same up to the order of floating-point maxima; it pays where
+ * neighbouring sub-triangles split together (deep refinement), and costs a little where
+ * splits are sparse.  The table also caps the splits per round at about the faces of A. */
 /* HD_FLAG_ASYNC_BUILD (read by hd_build_B): return as soon as the build is queued on the
  * stream, without waiting for it.  B's validity (indices in range, finite coordinates) is
  * then known only on the device: hd_hausdorff and its variants check it with their first
@@ -100,7 +105,8 @@ typedef struct {
   int64_t retired;           /* sub-triangles kept but never split again: l <= U <= l + eps */
   int64_t fp64_escalations;  /* MIXED: point-triangle tests redone in FP64 (slivers)        */
   int64_t peak_frontier;     /* largest live frontier                                       */
-  int64_t pool_vertices;     /* vertices created (referenced vertices of A + 3 per split)  */
+  int64_t pool_vertices;     /* vertices of A + midpoints made (an edge split by two
+                                sub-triangles in one round gets one midpoint)             */
   double eps_abs;            /* absolute tolerance used                                     */
   double dA;                 /* bbox diagonal of A's referenced vertices                    */
 } hd_stats;

@@ -6,8 +6,10 @@
 //   select   every live item with U > l + eps is split (up to a chunk per round); items with
 //            U < l are discarded, items with l <= U <= l + eps are retired (they can never
 //            again make u - l exceed eps, so they are not refined; their U is kept in a max);
-//   split    three midpoints per split item go to the vertex pool (Section 4: W_A), four
-//            children (G_A) are implied by the parent's vertices and the midpoints;
+//   split    the midpoints of each split item's three edges go to the vertex pool (Section 4:
+//            W_A) -- optionally one per edge where two split neighbours share it (a hash
+//            table of the round's edges); four children (G_A) are implied by the parent's
+//            vertices and the midpoints;
 //   query    nearest triangle of B for each new vertex, through the BVH (D, I, C);
 //   raise l  atomic max of the new vertex distances (Section 3.1);
 //   bound    UpperBound(child, l) for the four children of each split (Section 4) and
@@ -149,17 +151,30 @@ static __global__ void k_prep_finish(unsigned long long* box, double tol, int to
   dyn->pad = 0;
 }
 
+// The round's table of split edges (Section 4's midpoint subdivision, with the midpoint of an
+// edge shared by two split sub-triangles made once): open addressing on the key
+// (the edge's two pool indices, smaller first, under a set top bit); val = pool slot + 1 once
+// published; qhash[slot] = the entry a slot came from (-1: none), so that the query of that
+// midpoint clears the entry for the next round.  Key and val are all zero between rounds.
+// A null key pointer: midpoints are not shared (three per split, at 3 s + e).
+struct MidTable {
+  unsigned long long* key;
+  int* val;
+  int* qhash;
+  unsigned mask;  // entries - 1 (a power of two)
+};
+
 // Nearest-triangle queries for pool vertices [beg, beg + count); count = min(*count_ptr *
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.
 template <class P>
 __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
-                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints) {
+                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab) {
   int count = cap;
   if (round_midpoints) {
-    // the midpoints of this frontier round: 3 per split, from the pool size at its start
+    // the midpoints made by this frontier round, from the pool size at its start
     if (st->stop) return;  // the loop ended before this round (uniform over the grid)
     beg = st->n_pool;
-    count = 3 * min(st->n_split, st->K);
+    count = st->share_mid ? st->n_mid : 3 * min(st->n_split, st->K);
   } else if (count_ptr) {
     count = min(*count_ptr * mult, cap);
   }
@@ -175,7 +190,16 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
     // every lane of the warp enters the query (the MIXED traversal votes across the warp);
     // lanes without a vertex to query take part as already finished
     typename P::Vtx v;
-    if (active) v = pool[beg + t];
+    if (active) {
+      v = pool[beg + t];
+      if (tab.key) {  // its edge's entry is no longer needed: clear it for the next round
+        const int h = tab.qhash[t];
+        if (h >= 0) {
+          tab.key[h] = 0ull;
+          tab.val[h] = 0;
+        }
+      }
+    }
     bool q = active && v.tri != -1;
     P::query(B, v, c, q);
     if (q) {
@@ -366,12 +390,84 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
   flush_tally(st, ty);
 }
 
+__device__ inline unsigned edge_hash(unsigned long long k, unsigned mask) {
+  k ^= k >> 31;
+  k *= 0x9E3779B97F4A7C15ull;
+  return (unsigned)(k >> 32) & mask;
+}
+
+// Midpoint of edge e of split s, per active lane; without a table at mbase + 3 s + e.  With
+// one, it is called by every lane of the warp: the
+// first lane of the round to insert an edge makes its midpoint in a new slot and publishes it;
+// the others take that slot, waiting (bounded) for it to be published, and after a timeout
+// make a duplicate of their own (a separate pool vertex at the same position: only the
+// sharing is lost).  Returns the pool index (mbase + slot), or -1 for inactive lanes.
+template <class P>
+__device__ inline int mid_slot(bool active, int s, int e, int ia, int ib, const typename P::Vtx& va,
+                               const typename P::Vtx& vb, const MidTable& tab, RunState* st, typename P::Vtx* pool,
+                               int mbase) {
+  if (!tab.key) {  // uniform over the grid
+    if (!active) return -1;
+    typename P::Vtx m;
+    P::midpoint(va, vb, m);
+    pool[mbase + 3 * s + e] = m;
+    return mbase + 3 * s + e;
+  }
+  bool win = false, found = false;
+  unsigned h = 0;
+  if (active) {
+    const unsigned long long lo = (unsigned)min(ia, ib), hi = (unsigned)max(ia, ib);
+    const unsigned long long key = (1ull << 63) | (lo << 32) | hi;  // never 0 (the empty key)
+    h = edge_hash(key, tab.mask);
+    for (unsigned p = 0; p <= tab.mask; ++p) {
+      const unsigned long long prev = atomicCAS(&tab.key[h], 0ull, key);
+      if (prev == 0ull) {
+        win = true;
+        break;
+      }
+      if (prev == key) {
+        found = true;
+        break;
+      }
+      h = (h + 1) & tab.mask;
+    }
+  }
+  int slot = -1;
+  if (win) {
+    slot = warp_slot(&st->n_mid);
+    typename P::Vtx m;
+    P::midpoint(va, vb, m);
+    pool[mbase + slot] = m;
+    tab.qhash[slot] = (int)h;
+    atomicExch(&tab.val[h], slot + 1);
+  }
+  __syncwarp();  // this warp's new edges are published before its lanes look them up
+  if (found) {
+    for (int it = 0; it < 4096; ++it) {
+      const int v = *(volatile int*)&tab.val[h];
+      if (v) {
+        slot = v - 1;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  if (active && slot < 0) {  // not published in time (or no free entry): a duplicate
+    slot = warp_slot(&st->n_mid);
+    typename P::Vtx m;
+    P::midpoint(va, vb, m);
+    pool[mbase + slot] = m;
+    tab.qhash[slot] = -1;
+  }
+  return active ? mbase + slot : -1;
+}
+
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
 // rest (three midpoints each into the pool at mbase), carry the others over.
 template <class P>
 __global__ void k_select(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
-                         typename P::Vtx* pool, typename P::Item* next, int next_cap, typename P::Item* promo,
-                         int promo_cap) {
+                         int4* split_mid, MidTable tab, typename P::Vtx* pool, typename P::Item* next, int next_cap,
+                         typename P::Item* promo, int promo_cap) {
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const int n_front = st->n_front, K = st->K, mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
@@ -379,46 +475,56 @@ __global__ void k_select(const typename P::Item* front, RunState* st, RunParams 
   const Thresholds<P>& th = lv.th;
   const double l = lv.l;
   Tally<P> ty;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_front; i += gridDim.x * blockDim.x) {
-    typename P::Item it = front[i];
-    double U = (double)it.U;
-    if (it.U < th.lo) {
-      ty.discard(5);
-    } else if (it.U <= th.hi) {
-      ty.uret = ty.uret > it.U ? ty.uret : it.U;
-      ++ty.retired;
-    } else {
-      typename P::Vtx a = pool[it.v[0]], b = pool[it.v[1]], c = pool[it.v[2]], m;
-      if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
-        int j = atomicAdd(&st->n_promote, 1);
-        if (j < promo_cap) {
-          promo[j] = it;
-          atomic_max_nonneg(&st->upro_bits, U);
-        } else {
-          atomicExch(&st->overflow, 1);
-        }
+  // warp-uniform loop: the midpoint step below is taken by whole warps
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x;; i += gridDim.x * blockDim.x) {
+    const bool valid = i < n_front;
+    if (__all_sync(0xffffffffu, !valid)) break;
+    typename P::Item it;
+    typename P::Vtx a, b, c;
+    int s = -1;  // split slot of this lane's item
+    if (valid) {
+      it = front[i];
+      const double U = (double)it.U;
+      if (it.U < th.lo) {
+        ty.discard(5);
+      } else if (it.U <= th.hi) {
+        ty.uret = ty.uret > it.U ? ty.uret : it.U;
+        ++ty.retired;
       } else {
-        int s = warp_slot(&st->n_split);
-        if (s < K) {
-          // the parent's U, rounded up to float, for the children's clamp
-          split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], __float_as_int(__double2float_ru(U)));
-          P::midpoint(a, b, m);
-          pool[mbase + 3 * s] = m;
-          P::midpoint(b, c, m);
-          pool[mbase + 3 * s + 1] = m;
-          P::midpoint(c, a, m);
-          pool[mbase + 3 * s + 2] = m;
-        } else {
-          int j = warp_slot(&st->n_next);
-          if (j < next_cap) {
-            next[j] = it;
-            ty.umax = ty.umax > it.U ? ty.umax : it.U;
+        a = pool[it.v[0]];
+        b = pool[it.v[1]];
+        c = pool[it.v[2]];
+        if (promo && P::promote(a, b, c, U, l)) {  // below the policy's resolution: FP64 phase
+          int j = atomicAdd(&st->n_promote, 1);
+          if (j < promo_cap) {
+            promo[j] = it;
+            atomic_max_nonneg(&st->upro_bits, U);
           } else {
             atomicExch(&st->overflow, 1);
+          }
+        } else {
+          s = warp_slot(&st->n_split);
+          if (s < K) {
+            // the parent's U, rounded up to float, for the children's clamp
+            split_par[s] = make_int4(it.v[0], it.v[1], it.v[2], __float_as_int(__double2float_ru(U)));
+          } else {
+            s = -1;
+            int j = warp_slot(&st->n_next);
+            if (j < next_cap) {
+              next[j] = it;
+              ty.umax = ty.umax > it.U ? ty.umax : it.U;
+            } else {
+              atomicExch(&st->overflow, 1);
+            }
           }
         }
       }
     }
+    const bool sp = s >= 0;
+    const int m01 = mid_slot<P>(sp, s, 0, it.v[0], it.v[1], a, b, tab, st, pool, mbase);
+    const int m12 = mid_slot<P>(sp, s, 1, it.v[1], it.v[2], b, c, tab, st, pool, mbase);
+    const int m20 = mid_slot<P>(sp, s, 2, it.v[2], it.v[0], c, a, tab, st, pool, mbase);
+    if (sp && tab.key) split_mid[s] = make_int4(m01, m12, m20, 0);
   }
   flush_tally(st, ty);
 }
@@ -426,11 +532,11 @@ __global__ void k_select(const typename P::Item* front, RunState* st, RunParams 
 // The four children of every split (Section 4, midpoint subdivision):
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
 template <class P>
-__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par, RunState* st,
-                                 RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
+__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
+                                 const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
-  const int mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
+  const int mbase = st->n_pool, share = st->share_mid;
   int S = min(*(volatile int*)&st->n_split, st->K);
   const Level<P> lv = block_level<P>(st, rp.eps);
   const Thresholds<P>& th = lv.th;
@@ -442,8 +548,9 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
     const int64_t t = base + (threadIdx.x & 31);
     if (t < 4 * (int64_t)S) {
       int s = (int)(t >> 2), k = (int)(t & 3);
-      int4 par = split_par[s];
-      int m12 = mbase + 3 * s, m23 = m12 + 1, m31 = m12 + 2;
+      const int4 par = split_par[s];
+      const int4 mid = share ? split_mid[s] : make_int4(mbase + 3 * s, mbase + 3 * s + 1, mbase + 3 * s + 2, 0);
+      const int m12 = mid.x, m23 = mid.y, m31 = mid.z;
       typename P::Item it;
       if (k == 0) { it.v[0] = par.x; it.v[1] = m12; it.v[2] = m31; }
       else if (k == 1) { it.v[0] = m12; it.v[1] = par.y; it.v[2] = m23; }
@@ -464,6 +571,7 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
 // Per-loop constants of the round control.
 struct RoundCtl {
   long long chunk, pool_cap, front_cap;
+  int share;  // midpoints shared through the table
   long long splits_left;  // splits allowed by the face cap m n_A (Section 4) for this loop
   long long rounds_left;  // rounds before HD_ERR_TIMEOUT for this loop
   const unsigned long long* bad;  // A's and B's invalid-input flags
@@ -498,7 +606,7 @@ __host__ __device__ inline int close_round(RunState& st, long long rounds_left) 
     const int S = st.n_split < st.K ? st.n_split : st.K;
     st.rounds += 1;
     st.splits += S;
-    st.n_pool += 3 * S;
+    st.n_pool += st.share_mid ? st.n_mid : 3 * S;
     st.in_round = 0;
   }
   const int n_front = st.n_next;
@@ -529,6 +637,7 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
     st->rounds = st->splits = st->peak = 0;
     st->urun_bits = (unsigned long long)__double_as_longlong(INFINITY);
     st->n_pool = n_pool0;
+    st->share_mid = c.share;
   }
   if (st->stop) return;
   st->bad = *c.bad;
@@ -553,6 +662,7 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
   st->overflow = 0;
   st->q_next = 0;
   st->b_next = 0;
+  st->n_mid = 0;
   st->in_round = 1;
 }
 
@@ -626,6 +736,8 @@ struct Rounds {
   typename P::Item* promo = nullptr;   // items handed to the FP64 phase (MIXED only)
   typename P::Item* u4list = nullptr;  // items waiting for the u4 pass (MIXED only)
   int4* split_par = nullptr;
+  int4* split_mid = nullptr;  // the three midpoint pool indices of every split
+  MidTable tab = {nullptr, nullptr, nullptr, 0};
   int64_t pool_cap = 0, front_cap = 0, chunk = 0, promo_cap = 0;
   int64_t n_pool = 0, n_front = 0;
   int cur = 1;  // front[cur] holds the current frontier
@@ -633,6 +745,7 @@ struct Rounds {
 
 struct Totals {
   int64_t rounds = 0, splits = 0, peak = 0;
+  int64_t mids = 0;  // midpoints made (shared split edges counted once)
   double u_run = INFINITY;
 };
 
@@ -647,22 +760,49 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
       std::max<int64_t>(min_front + 4, (int64_t)((promo ? 0.1 : 0.15) * budget) / (int64_t)sizeof(Item)), INT32_MAX / 4);
   R.chunk = o.frontier_chunk > 0 ? o.frontier_chunk : std::max<int64_t>(R.front_cap / 4, 1024);
   R.chunk = std::min<int64_t>(R.chunk, R.front_cap);
+  // the midpoint table (shared midpoints only): a power of two of entries, at most half full
+  // with the 3 edges of each of a round's splits; the chunk is cut to what it holds (rounds
+  // of more splits than the faces of A are rare, and only split over more rounds)
+  const bool share = (o.flags & HD_FLAG_SHARE_MIDPOINTS) != 0;
+  int64_t n_tab = 0;
+  if (share) {
+    n_tab = 1 << 12;
+    const int64_t want = 6 * std::min<int64_t>(R.chunk, std::max<int64_t>(min_front, 4096));
+    while (n_tab < want && n_tab < ((int64_t)1 << 23)) n_tab <<= 1;
+    R.chunk = std::max<int64_t>(1, std::min<int64_t>(R.chunk, n_tab / 6));
+  }
   R.promo_cap = promo ? R.front_cap : 0;
   // one stream-ordered allocation, carved into the buffers (256-byte aligned)
   auto round_up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t b_pool = round_up(sizeof(Vtx) * R.pool_cap), b_front = round_up(sizeof(Item) * R.front_cap),
-               b_split = round_up(sizeof(int4) * R.chunk), b_promo = promo ? b_front : 0;
+               b_split = round_up(sizeof(int4) * R.chunk), b_promo = promo ? b_front : 0,
+               b_key = round_up(sizeof(unsigned long long) * n_tab), b_val = round_up(sizeof(int) * n_tab),
+               b_qh = share ? round_up(sizeof(int) * 3 * R.chunk) : 0;
   char* base = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&base, b_pool + 2 * b_front + b_split + 2 * b_promo, s));
+  HD_TRY(cudaMallocAsync((void**)&base, b_pool + 2 * b_front + 2 * b_split + 2 * b_promo + b_key + b_val + b_qh, s));
   R.base = base;
-  R.pool = (Vtx*)base;
-  R.front[0] = (Item*)(base + b_pool);
-  R.front[1] = (Item*)(base + b_pool + b_front);
-  R.split_par = (int4*)(base + b_pool + 2 * b_front);
-  if (promo) {
-    R.promo = (Item*)(base + b_pool + 2 * b_front + b_split);
-    R.u4list = (Item*)(base + b_pool + 2 * b_front + b_split + b_promo);
+  char* p = base;
+  auto carve = [&p](size_t b) {
+    char* q = p;
+    p += b;
+    return q;
+  };
+  R.pool = (Vtx*)carve(b_pool);
+  R.front[0] = (Item*)carve(b_front);
+  R.front[1] = (Item*)carve(b_front);
+  R.split_par = (int4*)carve(b_split);
+  R.split_mid = (int4*)carve(b_split);
+  if (share) {
+    R.tab.key = (unsigned long long*)carve(b_key);
+    R.tab.val = (int*)carve(b_val);
+    R.tab.qhash = (int*)carve(b_qh);
+    R.tab.mask = (unsigned)(n_tab - 1);
   }
+  if (promo) {
+    R.promo = (Item*)carve(b_promo);
+    R.u4list = (Item*)carve(b_promo);
+  }
+  if (share) HD_TRY(cudaMemsetAsync(R.tab.key, 0, b_key + b_val, s));  // key and val are adjacent
   return HD_OK;
 }
 
@@ -732,6 +872,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   c.chunk = R.chunk;
   c.pool_cap = R.pool_cap;
   c.front_cap = R.front_cap;
+  c.share = R.tab.key ? 1 : 0;
   const double cap_splits = std::floor((o.max_face_factor * (double)io.nFA - (double)io.nFA) / 4.0);
   c.splits_left = (long long)std::max(0.0, std::min(cap_splits - (double)T.splits, 9.0e18));
   c.rounds_left = std::max<long long>(0, o.max_rounds - T.rounds);
@@ -751,16 +892,17 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
       TraceScope tr(HD_K_SELECT, s);
       k_round_ctl<<<1, 1, 0, s>>>(st, c, init ? 1 : 0, n_pool0);
       init = false;
-      k_select<P><<<g_sel, 256, 0, s>>>(R.front[cur], st, rp, R.split_par, R.pool, R.front[cur ^ 1],
+      k_select<P><<<g_sel, 256, 0, s>>>(R.front[cur], st, rp, R.split_par, R.split_mid, R.tab, R.pool,
+                                        R.front[cur ^ 1],
                                         (int)R.front_cap, R.promo, (int)R.promo_cap);
     }
     {
       TraceScope tr(HD_K_QUERY, s);
-      k_query<P><<<g_q, bs, 0, s>>>(B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true);
+      k_query<P><<<g_q, bs, 0, s>>>(B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, R.tab);
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      k_bound_children<P><<<g_b, bs, 0, s>>>(B, R.pool, R.split_par, st, rp, R.front[cur ^ 1], (int)R.front_cap,
+      k_bound_children<P><<<g_b, bs, 0, s>>>(B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1], (int)R.front_cap,
                                              R.u4list);
       if (R.u4list)
         k_bound_u4<P><<<g_u4, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
@@ -810,6 +952,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   const RunState& f = hr.hb->st;
   T.rounds += f.rounds;
   T.splits += f.splits;
+  T.mids += f.n_pool - n_pool0;
   T.peak = std::max<int64_t>(T.peak, f.peak);
   T.u_run = std::min(T.u_run, bits_to_double(f.urun_bits));
   R.n_pool = f.n_pool;
@@ -853,6 +996,7 @@ static __global__ void k_phase_reset(RunState* st) {
   st->overflow = 0;
   st->upro_bits = 0;
   st->n_promote = 0;
+  st->n_mid = 0;
 }
 
 template <class P>
@@ -879,7 +1023,7 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(
-        B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false);
+        B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0});
   }
   {
     TraceScope tr(HD_K_BOUND, s);
@@ -957,7 +1101,7 @@ int run_bnb(const RunIO& io) {
     TraceScope tr(HD_K_QUERY, s);
     k_query<P><<<std::min(blocks_for(io.nVA, bs), persistent_grid(k_query<P>, bs, sms)), bs, 0, s>>>(
         B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
-                                                                       rp.slack, rp.dyn, false);
+                                                                       rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0});
   }
   HD_TRY_LAUNCH();
   {
@@ -1014,7 +1158,7 @@ int run_bnb(const RunIO& io) {
   S.retired = (int64_t)hst->retired;
   S.fp64_escalations = (int64_t)hst->escalations + n_pro;
   S.peak_frontier = T.peak;
-  S.pool_vertices = io.nVA + 3 * T.splits;
+  S.pool_vertices = io.nVA + T.mids;
 
   free_rounds(R, s);
   cudaFreeAsync(small, s);

@@ -125,6 +125,8 @@ struct RunState {
   unsigned long long bad;        // invalid-input flags of A (low word) and B (high word)
   int q_next, b_next;            // work counters of the query and bound kernels (warps take
                                  // batches of 32 items until none are left)
+  int n_mid;                     // midpoints made this round, when shared (else 3 per split)
+  int share_mid;                 // split edges share midpoints (HD_FLAG_SHARE_MIDPOINTS)
 };
 
 // Device view of hd_bvh, passed to kernels by value.

@@ -23,6 +23,7 @@ if not torch.cuda.is_available():
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "closed_forms.json")
 REL = 1e-6
+SHARED_MAX_PER_SPLIT = 2.6  # midpoints per split on workload 3 with shared midpoints (2.03 measured at full size)
 
 
 @pytest.fixture(scope="module")
@@ -292,6 +293,30 @@ def test_parent_clamp_on_and_off(hd, orc, precision):
                                                                   flags=hd.HD_FLAG_NO_PARENT_CLAMP))[0]
     assert on["stats"]["splits"] > 0 and off["stats"]["splits"] > 0
     assert max(on["lower"], off["lower"]) <= min(on["upper"], off["upper"]) + 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("k,scale,chunk", [(1, 1.0, 0), (2, 0.02, 0), (3, 0.01, 0), (3, 0.01, 256)])
+def test_shared_midpoints(hd, orc, precision, k, scale, chunk):
+    """HD_FLAG_SHARE_MIDPOINTS: an edge split by two sub-triangles of one round gets one
+    midpoint.  The bracket stays within eps and meets the oracle's; the run makes no more
+    midpoints (and queries) than without sharing, and fewer where neighbours split together
+    (workload 3 splits each face of A a few times); a small chunk (many rounds, the table
+    cleared and reused between them) too."""
+    p = mg.workload(k, scale)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    mk = lambda f: hd.hd_options_default(tol_mode=p.tol_mode, precision=prec, frontier_chunk=chunk, flags=f)
+    on = _bracket_parity(hd, orc, p, opt=mk(hd.HD_FLAG_SHARE_MIDPOINTS), tight=(k != 3))[0]
+    off = _bracket_parity(hd, orc, p, opt=mk(0), tight=(k != 3))[0]
+    assert max(on["lower"], off["lower"]) <= min(on["upper"], off["upper"]) + 1e-12
+    s_on, s_off = on["stats"], off["stats"]
+    assert s_off["pool_vertices"] - len(p.VA) == 3 * s_off["splits"]
+    made = s_on["pool_vertices"] - len(p.VA)
+    assert 0 < made <= 3 * s_on["splits"]
+    if k == 3:
+        print("shared midpoints: splits", s_on["splits"], "made", made, "queries", s_on["queries"], s_off["queries"])
+        assert made < SHARED_MAX_PER_SPLIT * s_on["splits"], (made, s_on["splits"])
+        assert s_on["queries"] < s_off["queries"]
 
 
 def test_bracket_all_bound_orders_fp64(hd, orc):
