@@ -69,7 +69,9 @@ typedef struct {
                               (n_A + 4 per split); default 1e7                           */
   int64_t frontier_chunk;  /* most sub-triangles split in one round (0 = automatic)       */
   int32_t leaf_size;       /* triangles per BVH leaf, 1..16 (default 1)                   */
-  int32_t block_size;      /* threads per block of the round kernels (default 64)         */
+  int32_t block_size;      /* threads per block of the round kernels, a multiple of 32
+                              (default 64); above what the kernels' register use allows
+                              (a few hundred) hd_hausdorff returns HD_ERR_INVALID       */
   uint8_t bound_order[4];  /* cascade order, values 1..4 = u1..u4 (default 1,2,3,4)        */
   int32_t n_bounds;        /* how many entries of bound_order are used, 1..4 (default 4)  */
   int64_t max_rounds;      /* frontier rounds before HD_ERR_TIMEOUT (default 1e6)         */
@@ -109,6 +111,8 @@ typedef struct {
                                 sub-triangles in one round gets one midpoint)             */
   double eps_abs;            /* absolute tolerance used                                     */
   double dA;                 /* bbox diagonal of A's referenced vertices                    */
+  int64_t long_queries;      /* queries whose traversal a whole warp finished (part of
+                                queries: those with many BVH boxes within their distance)  */
 } hd_stats;
 
 typedef struct {

@@ -41,7 +41,7 @@ class HdStats(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("splits", C.c_int64), ("queries", C.c_int64), ("pointtri_evals", C.c_int64),
                 ("leaf_tests", C.c_int64), ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
-                ("eps_abs", C.c_double), ("dA", C.c_double)]
+                ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64)]
 
 
 class HdResult(C.Structure):
@@ -212,7 +212,8 @@ def _result(r: HdResult) -> dict:
                            leaf_tests=s.leaf_tests,
                            box_tests=s.box_tests, discards={BOUND_NAMES[k]: s.discards[k] for k in range(6)},
                            retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
-                           pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA))
+                           pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA,
+                           long_queries=s.long_queries))
 
 
 def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:

@@ -332,6 +332,7 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
   S.fp64_escalations = X.fp64_escalations + Y.fp64_escalations;
   S.peak_frontier = std::max(X.peak_frontier, Y.peak_frontier);
   S.pool_vertices = X.pool_vertices + Y.pool_vertices;
+  S.long_queries = X.long_queries + Y.long_queries;
   S.eps_abs = X.eps_abs;
   S.dA = X.dA;
   return HD_OK;

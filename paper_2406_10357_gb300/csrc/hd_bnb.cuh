@@ -22,6 +22,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -66,6 +67,8 @@ __device__ inline void flush_counters(RunState* st, const Counters& c) {
 // Referenced vertices of A (the paper assumes every vertex is referenced, Section 3; l and
 // dA use only referenced ones, Section 5.3) and the validity of F_A.
 static __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t* ref, int* bad) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= 3 * nFA) return;
   int32_t v = FA[i];
@@ -85,6 +88,8 @@ __device__ inline unsigned long long double_to_ordered(double d) {
 template <class P, typename T>
 __global__ void k_check_init(const T* VA, int64_t nVA, const uint8_t* ref, unsigned long long* box, int* bad,
                              typename P::Vtx* pool) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long m[6] = {0, 0, 0, 0, 0, 0};  // ~lo xyz, hi xyz
   if (i < nVA) {
@@ -134,6 +139,8 @@ __device__ inline double ordered_to_double(unsigned long long u) {
 // dA, eps and the slack from A's bounding box, on the device (one thread).
 static __global__ void k_prep_finish(unsigned long long* box, double tol, int tol_rel, double slack_scale,
                                      DynParams* dyn, RunState* st, double l0, const float* b_meta) {
+  grid_dep_wait();
+  grid_dep_launch();
   // B's validity flag (from its build) joins A's in the flag word the host reads with round 0
   if (__float_as_uint(b_meta[1]) != 0u) ((unsigned*)(box + 6))[1] = 1u;
   if (l0 > 0.0) st->l_bits = (unsigned long long)__double_as_longlong(l0);  // warm start of l
@@ -164,11 +171,34 @@ struct MidTable {
   unsigned mask;  // entries - 1 (a power of two)
 };
 
+// A slot in a device-side list for each calling lane: one atomic per warp (the lanes that
+// reach the call together share it).
+__device__ inline int warp_slot(int* counter) {
+  namespace cg = cooperative_groups;
+  cg::coalesced_group g = cg::coalesced_threads();
+  int base = 0;
+  if (g.thread_rank() == 0) base = atomicAdd(counter, (int)g.size());
+  return g.shfl(base, 0) + (int)g.thread_rank();
+}
+
+// The queries a launch of k_query hands to k_query_long: pool indices, with room for as many
+// as the launch has queries.  A null list: every lane finishes its own query.
+struct LongList {
+  int* idx;
+  int cap;
+};
+
 // Nearest-triangle queries for pool vertices [beg, beg + count); count = min(*count_ptr *
-// mult, cap) when count_ptr is given (device-side counts), else `cap`.
+// mult, cap) when count_ptr is given (device-side counts), else `cap`.  Warps take batches of
+// 32 consecutive vertices, one per lane, each lane traversing on its own (the while-while
+// traversal).  With a list, a lane whose traversal tests more than kLongBudget triangles
+// stops and hands its query to k_query_long, which runs next and counts it.
 template <class P>
 __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
-                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab) {
+                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
+                        LongList ll) {
+  grid_dep_wait();
+  grid_dep_launch();
   int count = cap;
   if (round_midpoints) {
     // the midpoints made by this frontier round, from the pool size at its start
@@ -201,11 +231,20 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
       }
     }
     bool q = active && v.tri != -1;
-    P::query(B, v, c, q);
+    bool over = false;
+    P::query(B, v, c, q, ll.idx ? kLongBudget : INT_MAX, &over);
     if (q) {
       pool[beg + t] = v;
-      lmax = fmax(lmax, P::lower(v) - slack);
-      ++nq;
+      if (over) {
+        const int j = warp_slot(&st->n_long);
+        if (j < ll.cap)
+          ll.idx[j] = beg + t;
+        else
+          atomicExch(&st->overflow, 1);  // cannot happen: the list has room for every query
+      } else {
+        lmax = fmax(lmax, P::lower(v) - slack);
+        ++nq;
+      }
     }
   }
   lmax = warp_max(lmax);
@@ -217,14 +256,48 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
   flush_counters(st, c);
 }
 
-// A slot in a device-side list for each calling lane: one atomic per warp (the lanes that
-// reach the call together share it).
-__device__ inline int warp_slot(int* counter) {
-  namespace cg = cooperative_groups;
-  cg::coalesced_group g = cg::coalesced_threads();
-  int base = 0;
-  if (g.thread_rank() == 0) base = atomicAdd(counter, (int)g.size());
-  return g.shfl(base, 0) + (int)g.thread_rank();
+// The queries k_query handed off, one warp each (traverse_coop, with this warp's stack in
+// shared memory), taken one at a time from a counter since their costs vary widely; with
+// their contribution to l and to the query counts.
+template <class P>
+__global__ void __launch_bounds__(32 * kCoopWarps) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
+                                                                RunState* st, double slack_in, const DynParams* dyn,
+                                                                bool round_midpoints) {
+  __shared__ unsigned s_code[kCoopWarps][kCoopStack];
+  __shared__ float s_e[kCoopWarps][kCoopStack];
+  grid_dep_wait();
+  grid_dep_launch();
+  if (round_midpoints && st->stop) return;  // as k_query (uniform over the grid)
+  const int n = min(st->n_long, ll.cap);
+  if (n == 0) return;  // uniform over the grid
+  const double slack = dyn ? dyn->slack : slack_in;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Counters c;
+  double lmax = 0.0;
+  int nq = 0;
+  for (;;) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&st->long_next, 1);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= n) break;
+    const int k = ll.idx[i];
+    typename P::Vtx v = pool[k];
+    P::query_coop(B, v, c, s_code[w], s_e[w]);
+    if (lane == 0) {
+      pool[k] = v;
+      lmax = fmax(lmax, P::lower(v) - slack);
+      ++nq;
+    }
+  }
+  lmax = warp_max(lmax);
+  if (lane == 0) {
+    atomic_max_nonneg(&st->l_bits, lmax);
+    if (nq) {
+      atomicAdd(&st->queries, (unsigned long long)nq);
+      atomicAdd(&st->long_queries, (unsigned long long)nq);
+    }
+  }
+  flush_counters(st, c);
 }
 
 // Per-thread outcome counts and maxima of classified items, flushed once per warp.
@@ -338,6 +411,8 @@ template <class P>
 __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
                               RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list,
                               int64_t n_pool_valid) {
+  grid_dep_wait();
+  grid_dep_launch();
   const RunParams rp = with_dyn(rp_in);
   const Level<P> lv = block_level<P>(st, rp.eps);
   const Thresholds<P>& th = lv.th;
@@ -369,6 +444,8 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
 template <class P>
 __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
                            RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
+  grid_dep_wait();
+  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const RunParams rp = with_dyn(rp_in);
   int n = min(*(volatile int*)&st->n_u4, cap);
@@ -468,6 +545,8 @@ template <class P>
 __global__ void k_select(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
                          int4* split_mid, MidTable tab, typename P::Vtx* pool, typename P::Item* next, int next_cap,
                          typename P::Item* promo, int promo_cap) {
+  grid_dep_wait();
+  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const int n_front = st->n_front, K = st->K, mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
@@ -534,6 +613,8 @@ __global__ void k_select(const typename P::Item* front, RunState* st, RunParams 
 template <class P>
 __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
                                  const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
+  grid_dep_wait();
+  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const RunParams rp = with_dyn(rp_in);
   const int mbase = st->n_pool, share = st->share_mid;
@@ -630,6 +711,8 @@ __host__ __device__ inline int close_round(RunState& st, long long rounds_left) 
 // promoted items -- were launched).  Once stopped, later rounds find `stop` set and do
 // nothing, so the host may queue a round before it has read the previous one.
 static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_pool0) {
+  grid_dep_wait();
+  grid_dep_launch();
   if (init) {
     st->stop = 0;
     st->status = HD_OK;
@@ -663,12 +746,16 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
   st->q_next = 0;
   st->b_next = 0;
   st->n_mid = 0;
+  st->n_long = 0;
+  st->long_next = 0;
   st->in_round = 1;
 }
 
 // Nearest queries for external points (hd_nearest): P as double rows.
 template <class P>
 __global__ void k_query_points(BvhDev B, typename P::Vtx* tmp, int64_t n, RunState* st) {
+  grid_dep_wait();
+  grid_dep_launch();
   Counters c;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;; t += (int64_t)gridDim.x * blockDim.x) {
     bool active = t < n;
@@ -716,12 +803,12 @@ int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams*
   cudaStream_t s = io.s;
   int* bad = (int*)(box + 6);
   TraceScope tr(HD_K_PREP, s);
-  k_mark_ref<<<blocks_for(3 * io.nFA, 256), 256, 0, s>>>(io.FA, io.nFA, io.nVA, ref, bad);
+  launch_chained(k_mark_ref, blocks_for(3 * io.nFA, 256), 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad);
   if (io.vtype == HD_F64)
-    k_check_init<P, double><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const double*)io.VA, io.nVA, ref, box, bad, pool);
+    launch_chained(k_check_init<P, double>, blocks_for(io.nVA, 256), 256, 0, s, (const double*)io.VA, io.nVA, ref, box, bad, pool);
   else
-    k_check_init<P, float><<<blocks_for(io.nVA, 256), 256, 0, s>>>((const float*)io.VA, io.nVA, ref, box, bad, pool);
-  k_prep_finish<<<1, 1, 0, s>>>(box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0,
+    launch_chained(k_check_init<P, float>, blocks_for(io.nVA, 256), 256, 0, s, (const float*)io.VA, io.nVA, ref, box, bad, pool);
+  launch_chained(k_prep_finish, 1, 1, 0, s, box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0,
                                 io.B->meta);
   HD_TRY_LAUNCH();
   return HD_OK;
@@ -738,10 +825,65 @@ struct Rounds {
   int4* split_par = nullptr;
   int4* split_mid = nullptr;  // the three midpoint pool indices of every split
   MidTable tab = {nullptr, nullptr, nullptr, 0};
+  LongList longq = {nullptr, 0};  // queries handed to k_query_long
   int64_t pool_cap = 0, front_cap = 0, chunk = 0, promo_cap = 0;
   int64_t n_pool = 0, n_front = 0;
   int cur = 1;  // front[cur] holds the current frontier
 };
+
+// The largest block the round kernels of policy P launch with (their register use limits it
+// below 1024 threads).
+template <class P>
+int round_block_limit() {
+  static std::atomic<int> cached{0};
+  int m = cached.load(std::memory_order_relaxed);
+  if (!m) {
+    m = 1024;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_query<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+    if (cudaFuncGetAttributes(&fa, k_bound_faces<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+    if (cudaFuncGetAttributes(&fa, k_bound_children<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+    if (cudaFuncGetAttributes(&fa, k_bound_u4<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+    m &= ~31;
+    cached.store(m, std::memory_order_relaxed);
+  }
+  return m;
+}
+
+// Blocks of `bs` threads that fill every SM once with `kernel` (at least one per SM): the
+// grid of the persistent kernels, whose warps take batches of work (warp_batch).
+template <typename K>
+unsigned persistent_grid(K kernel, int bs, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return (unsigned)(per_sm * sms);
+}
+
+// persistent_grid, remembered per block size (32 to 1024 threads, a multiple of 32).
+template <typename K>
+unsigned persistent_grid_bs(K kernel, int bs, std::atomic<unsigned> (&cache)[33]) {
+  unsigned g = cache[bs / 32].load(std::memory_order_relaxed);
+  if (!g) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g = persistent_grid(kernel, bs, sms);
+    cache[bs / 32].store(g, std::memory_order_relaxed);
+  }
+  return g;
+}
+
+// The persistent grids of k_query (per block size) and of k_query_long.
+template <class P>
+unsigned query_grid(int bs) {
+  static std::atomic<unsigned> cache[33];
+  return persistent_grid_bs(k_query<P>, bs, cache);
+}
+template <class P>
+unsigned long_grid() {
+  static std::atomic<unsigned> cache[33];
+  return persistent_grid_bs(k_query_long<P>, 32 * kCoopWarps, cache);
+}
 
 struct Totals {
   int64_t rounds = 0, splits = 0, peak = 0;
@@ -777,9 +919,11 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
   const size_t b_pool = round_up(sizeof(Vtx) * R.pool_cap), b_front = round_up(sizeof(Item) * R.front_cap),
                b_split = round_up(sizeof(int4) * R.chunk), b_promo = promo ? b_front : 0,
                b_key = round_up(sizeof(unsigned long long) * n_tab), b_val = round_up(sizeof(int) * n_tab),
-               b_qh = share ? round_up(sizeof(int) * 3 * R.chunk) : 0;
+               b_qh = share ? round_up(sizeof(int) * 3 * R.chunk) : 0,
+               b_long = round_up(sizeof(int) * std::max<int64_t>(min_pool, 3 * R.chunk));
   char* base = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&base, b_pool + 2 * b_front + 2 * b_split + 2 * b_promo + b_key + b_val + b_qh, s));
+  HD_TRY(cudaMallocAsync((void**)&base,
+                         b_pool + 2 * b_front + 2 * b_split + 2 * b_promo + b_key + b_val + b_qh + b_long, s));
   R.base = base;
   char* p = base;
   auto carve = [&p](size_t b) {
@@ -792,6 +936,7 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
   R.front[1] = (Item*)carve(b_front);
   R.split_par = (int4*)carve(b_split);
   R.split_mid = (int4*)carve(b_split);
+  R.longq = {(int*)carve(b_long), (int)std::max<int64_t>(min_pool, 3 * R.chunk)};
   if (share) {
     R.tab.key = (unsigned long long*)carve(b_key);
     R.tab.val = (int*)carve(b_val);
@@ -810,15 +955,6 @@ template <class P>
 void free_rounds(Rounds<P>& R, cudaStream_t s) {
   if (R.base) cudaFreeAsync(R.base, s);
   R.base = nullptr;
-}
-
-// Blocks of `bs` threads that fill every SM once with `kernel` (at least one per SM): the
-// grid of the persistent kernels, whose warps take batches of work (warp_batch).
-template <typename K>
-unsigned persistent_grid(K kernel, int bs, int sms) {
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
-  return (unsigned)(per_sm * sms);
 }
 
 // Pinned host memory the round loop reads into: the final run state and parameters, and a
@@ -877,8 +1013,9 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   c.splits_left = (long long)std::max(0.0, std::min(cap_splits - (double)T.splits, 9.0e18));
   c.rounds_left = std::max<long long>(0, o.max_rounds - T.rounds);
   c.bad = bad;
-  static const unsigned grid_q = persistent_grid(k_query<P>, bs, sms);
-  static const unsigned grid_b = persistent_grid(k_bound_children<P>, bs, sms);
+  static std::atomic<unsigned> grid_b_cache[33];
+  const unsigned grid_q = query_grid<P>(bs), grid_b = persistent_grid_bs(k_bound_children<P>, bs, grid_b_cache);
+  const unsigned grid_long = long_grid<P>();
   int64_t front_bound = first_front_bound;  // the first round is queued without a wait
   int cur = R.cur;
   bool init = true;
@@ -890,22 +1027,23 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     const unsigned g_u4 = std::min(blocks_for(4 * k, bs), max_grid);
     {
       TraceScope tr(HD_K_SELECT, s);
-      k_round_ctl<<<1, 1, 0, s>>>(st, c, init ? 1 : 0, n_pool0);
+      launch_chained(k_round_ctl, 1, 1, 0, s, st, c, init ? 1 : 0, n_pool0);
       init = false;
-      k_select<P><<<g_sel, 256, 0, s>>>(R.front[cur], st, rp, R.split_par, R.split_mid, R.tab, R.pool,
+      launch_chained(k_select<P>, g_sel, 256, 0, s, R.front[cur], st, rp, R.split_par, R.split_mid, R.tab, R.pool,
                                         R.front[cur ^ 1],
                                         (int)R.front_cap, R.promo, (int)R.promo_cap);
     }
     {
       TraceScope tr(HD_K_QUERY, s);
-      k_query<P><<<g_q, bs, 0, s>>>(B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, R.tab);
+      launch_chained(k_query<P>, g_q, bs, 0, s, B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, R.tab, R.longq);
+      launch_chained(k_query_long<P>, grid_long, 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, true);
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      k_bound_children<P><<<g_b, bs, 0, s>>>(B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1], (int)R.front_cap,
+      launch_chained(k_bound_children<P>, g_b, bs, 0, s, B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1], (int)R.front_cap,
                                              R.u4list);
       if (R.u4list)
-        k_bound_u4<P><<<g_u4, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
+        launch_chained(k_bound_u4<P>, g_u4, bs, 0, s, B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
                                           (int)R.front_cap);
     }
     HD_TRY_LAUNCH();
@@ -965,6 +1103,8 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
 template <class P>
 __global__ void k_promote_init(const typename P::Item* promo, int n, const typename P::Vtx* pool, VtxD* poolD,
                                int32_t* tris) {
+  grid_dep_wait();
+  grid_dep_launch();
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   typename P::Item it = promo[i];
@@ -987,6 +1127,8 @@ __global__ void k_promote_init(const typename P::Item* promo, int n, const typen
 // re-queried and bounded in FP64 (with the same slack margin) and refined to the end there.
 // Start of the FP64 phase: an empty next frontier and no promotions.
 static __global__ void k_phase_reset(RunState* st) {
+  grid_dep_wait();
+  grid_dep_launch();
   st->q_next = 0;
   st->b_next = 0;
   st->n_next = 0;
@@ -997,6 +1139,8 @@ static __global__ void k_phase_reset(RunState* st) {
   st->upro_bits = 0;
   st->n_promote = 0;
   st->n_mid = 0;
+  st->n_long = 0;
+  st->long_next = 0;
 }
 
 template <class P>
@@ -1016,20 +1160,23 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   }
   {
     TraceScope tr(HD_K_PREP, s);
-    k_promote_init<P><<<blocks_for(n_pro, 256), 256, 0, s>>>(RM.promo, (int)n_pro, RM.pool, D.pool, tris);
-    k_phase_reset<<<1, 1, 0, s>>>(st);
+    launch_chained(k_promote_init<P>, blocks_for(n_pro, 256), 256, 0, s, RM.promo, (int)n_pro, RM.pool, D.pool, tris);
+    launch_chained(k_phase_reset, 1, 1, 0, s, st);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query<PolicyD><<<blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s>>>(
-        B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0});
+    launch_chained(k_query<PolicyD>, blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s, 
+        B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0},
+        D.longq);
+    launch_chained(k_query_long<PolicyD>, long_grid<PolicyD>(), 32 * kCoopWarps, 0, s, B, D.pool, D.longq, st, rp.slack, rp.dyn,
+                                                                         false);
   }
   {
     TraceScope tr(HD_K_BOUND, s);
     RunParams rpd = rp;
     rpd.defer_u4 = 0;
-    k_bound_faces<PolicyD><<<blocks_for(n_pro, o.block_size), o.block_size, 0, s>>>(B, D.pool, tris, n_pro, st, rpd,
+    launch_chained(k_bound_faces<PolicyD>, blocks_for(n_pro, o.block_size), o.block_size, 0, s, B, D.pool, tris, n_pro, st, rpd,
                                                                                    D.front[1], (int)D.front_cap,
                                                                                    nullptr, 3 * n_pro);
   }
@@ -1047,6 +1194,9 @@ int run_bnb(const RunIO& io) {
   cudaStream_t s = io.s;
   hd_result& res = *io.out;
   memset(&res, 0, sizeof res);
+  // a block the round kernels cannot launch with (MIXED also runs the FP64 ones)
+  if (o.block_size > round_block_limit<P>() || (!P::kFp64 && o.block_size > round_block_limit<PolicyD>()))
+    return HD_ERR_INVALID;
 
   HostRes* hr = nullptr;
   {
@@ -1099,18 +1249,19 @@ int run_bnb(const RunIO& io) {
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query<P><<<std::min(blocks_for(io.nVA, bs), persistent_grid(k_query<P>, bs, sms)), bs, 0, s>>>(
-        B, R.pool, 0, nullptr, 1, (int)io.nVA, st,
-                                                                       rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0});
+    launch_chained(k_query<P>, std::min(blocks_for(io.nVA, bs), query_grid<P>(bs)), bs, 0, s, 
+        B, R.pool, 0, nullptr, 1, (int)io.nVA, st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0},
+        R.longq);
+    launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_BOUND, s);
-    k_bound_faces<P><<<std::min(blocks_for(io.nFA, bs), persistent_grid(k_bound_faces<P>, bs, sms)), bs, 0, s>>>(
+    launch_chained(k_bound_faces<P>, std::min(blocks_for(io.nFA, bs), persistent_grid(k_bound_faces<P>, bs, sms)), bs, 0, s, 
         B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
                                                            (int)R.front_cap, R.u4list, io.nVA);
     if (R.u4list)
-      k_bound_u4<P><<<max_grid, bs, 0, s>>>(B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[1],
+      launch_chained(k_bound_u4<P>, max_grid, bs, 0, s, B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[1],
                                             (int)R.front_cap);
   }
   HD_TRY_LAUNCH();
@@ -1151,6 +1302,7 @@ int run_bnb(const RunIO& io) {
   S.rounds = T.rounds;
   S.splits = T.splits;
   S.queries = (int64_t)hst->queries;
+  S.long_queries = (int64_t)hst->long_queries;
   S.pointtri_evals = (int64_t)hst->evals;
   S.leaf_tests = (int64_t)hst->leaf_tests;
   S.box_tests = (int64_t)hst->box_tests;
@@ -1169,6 +1321,8 @@ int run_bnb(const RunIO& io) {
 
 template <class P, typename T>
 __global__ void k_points_in(const T* P_, int64_t n, typename P::Vtx* v) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   typename P::Vtx x;
@@ -1182,6 +1336,8 @@ __global__ void k_points_in(const T* P_, int64_t n, typename P::Vtx* v) {
 template <class P>
 __global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tri_vid, double* dist, int32_t* idx,
                              double* foot, double* dlo) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   typename P::Vtx x = v[i];
@@ -1204,14 +1360,14 @@ int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaS
   HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
   if (ptype == HD_F64)
-    k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, tmp);
+    launch_chained(k_points_in<P, double>, blocks_for(n, 256), 256, 0, s, (const double*)Pts, n, tmp);
   else
-    k_points_in<P, float><<<blocks_for(n, 256), 256, 0, s>>>((const float*)Pts, n, tmp);
+    launch_chained(k_points_in<P, float>, blocks_for(n, 256), 256, 0, s, (const float*)Pts, n, tmp);
   {
     TraceScope tr(HD_K_QUERY, s);
     k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), tmp, n, st);
   }
-  k_points_out<P><<<blocks_for(n, 256), 256, 0, s>>>(tmp, n, B->tri_vid, dist, idx, foot, dlo);
+  launch_chained(k_points_out<P>, blocks_for(n, 256), 256, 0, s, tmp, n, B->tri_vid, dist, idx, foot, dlo);
   HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(tmp, s));
   HD_TRY(cudaFreeAsync(st, s));

@@ -1,0 +1,98 @@
+// Warp-cooperative nearest-triangle traversal, for the queries that a lane's own traversal
+// does not finish within a budget of triangle tests.
+//
+// A query point far from B (a sub-triangle vertex deep inside a closed surface, say) has many
+// BVH boxes within its nearest distance, and a one-lane depth-first traversal visits them one
+// dependent node fetch at a time while the other lanes of its warp wait.  Here the whole warp
+// works on one query: every step pops up to eight inner nodes from a stack in shared memory,
+// each group of four lanes fetches one node (the four lanes read the four child boxes of the
+// same 128-byte node), each lane bounds one child box, tests a leaf child's triangles at once,
+// and the inner children still within the warp's radius are pushed back (ballot compaction).
+// Pruning is order-independent: a subtree is dropped only when its box bound exceeds the
+// smallest triangle distance bound found so far by any lane, which is what the lane
+// traversal also guarantees, so the result (the nearest triangle, and the certified lower
+// bound) has the same meaning.
+#pragma once
+
+#include "hd_internal.cuh"
+
+namespace hd {
+
+#ifndef HD_LONG_BUDGET
+#define HD_LONG_BUDGET 10
+#endif
+#ifndef HD_COOP_STACK
+#define HD_COOP_STACK 1024
+#endif
+constexpr int kCoopStack = HD_COOP_STACK;  // stack entries per warp (8 bytes each, shared memory)
+constexpr int kCoopWarps = 4;              // warps per block of k_query_long
+// Triangles a lane's traversal tests before it hands its query to a warp.  The hand-off
+// restarts the traversal from the root with the best triangle found so far as the radius,
+// so a small budget wastes little; most queries finish well within it (a point near B tests
+// a few triangles).
+constexpr int kLongBudget = HD_LONG_BUDGET;
+
+__device__ inline float warp_min_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Must be called by all 32 lanes of the warp with the same query.  `t` is each lane's own
+// nearest state (test1 / range over triangle indices; r2(): its squared radius rounded up to
+// float); `box(lx, ly, lz, hx, hy, hz)` returns a lower bound of the squared distance from the
+// query point to a box, rounded down to float.  s_code / s_e: this warp's kCoopStack entries
+// (node index, box bound).
+template <class Near, class Box>
+__device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, unsigned* s_code, float* s_e,
+                                     Counters& c) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, ch = lane & 3;
+  if (lane == 0) {
+    s_code[0] = 0u;  // the root, an inner node
+    s_e[0] = 0.f;
+  }
+  int sp = 1;
+  __syncwarp();
+  float r2 = warp_min_f(t.coop_r2());
+  while (sp > 0) {
+    // pop up to 8 nodes, leaving room for their 4 children each (sp - P + 4 P <= capacity)
+    int P = min(sp, 8);
+    const int room = (kCoopStack - sp) / 3;
+    if (P > room) P = max(room, 1);
+    int node = -1;
+    if (g < P) {
+      const int k = sp - 1 - g;
+      if (s_e[k] <= r2) node = (int)s_code[k];
+    }
+    __syncwarp();  // the popped entries are read before the pushes below overwrite them
+    sp -= P;
+    unsigned code = kNoChild;
+    float e = INFINITY;
+    if (node >= 0) {
+      const float* nf = reinterpret_cast<const float*>(B.nodes + node);
+      code = __ldg(reinterpret_cast<const unsigned*>(nf) + 24 + ch);
+      if (code != kNoChild) {
+        ++c.boxes;
+        e = box(__ldg(nf + ch), __ldg(nf + 4 + ch), __ldg(nf + 8 + ch), __ldg(nf + 12 + ch), __ldg(nf + 16 + ch),
+                __ldg(nf + 20 + ch));
+      }
+    }
+    const bool hit = code != kNoChild && e <= r2;
+    if (hit && code_count(code) > 0) t.range(code_ref(code), code_count(code));
+    r2 = warp_min_f(t.coop_r2());
+    const bool push = hit && code_count(code) == 0 && e <= r2;
+    const unsigned m = __ballot_sync(0xffffffffu, push);
+    if (push) {
+      const int k = sp + __popc(m & ((1u << lane) - 1u));
+      if (k < kCoopStack) {
+        s_code[k] = (unsigned)code_ref(code);
+        s_e[k] = e;
+      } else {
+        c.err = 1;  // stack overflow: the subtree is skipped and the error reported
+      }
+    }
+    sp = min(sp + __popc(m), kCoopStack);
+    __syncwarp();
+  }
+}
+
+}  // namespace hd

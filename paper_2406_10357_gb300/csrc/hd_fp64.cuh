@@ -2,6 +2,7 @@
 // arithmetic of the paper's implementation (Section 4).
 #pragma once
 
+#include "hd_coop.cuh"
 #include "hd_internal.cuh"
 
 namespace hd {
@@ -12,13 +13,16 @@ constexpr int kStack = 96;  // up to 3 pushes per 4-wide node
 // boxes come with one node fetch, leaf children are tested at once, the nearer internal
 // child is entered and the farther one pushed with its box distance, which is re-checked
 // when popped.  `Test` gets a triangle range and may shrink the pruning radius it holds.
+// Returns false once `test` has tested more than `budget` triangles, with the traversal
+// unfinished (what `test` holds is then the best triangle found so far).
 template <class Test>
-__device__ inline void traverse(const BvhDev& B, D3 p, Test& test, Counters& c) {
+__device__ inline bool traverse(const BvhDev& B, D3 p, Test& test, Counters& c, int budget = INT_MAX) {
   int stack_node[kStack];
   double stack_d[kStack];
   int sp = 0;
   int node = 0;
   for (;;) {
+    if ((int)test.evals > budget) return false;
     const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
     const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
     const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
@@ -83,6 +87,7 @@ __device__ inline void traverse(const BvhDev& B, D3 p, Test& test, Counters& c) 
     }
     if (!found) break;
   }
+  return true;
 }
 
 struct NearestD {
@@ -93,6 +98,7 @@ struct NearestD {
   D3 q = {0, 0, 0};
   unsigned evals = 0;
   __device__ double radius2() const { return best2; }
+  __device__ float coop_r2() const { return __double2float_ru(best2); }
   __device__ void test1(int j) {
     D3 a, b, c;
     load_tri64(tri64, j, a, b, c);
@@ -328,19 +334,62 @@ struct PolicyD {
   using UT = double;
   static constexpr bool kFp64 = true;
 
-  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active) {
+  // Nearest triangle of v.  With `over` given, a traversal that tests more than `budget`
+  // triangles stops, sets *over and leaves its best triangle so far in v (hint, d = its
+  // squared distance, q) for query_coop to finish.
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active, int budget = INT_MAX,
+                               bool* over = nullptr) {
     if (!active) return;  // no warp-collective operations below
     NearestD t;
     t.p = {v.x, v.y, v.z};
     t.tri64 = B.tri64;
     if (v.hint >= 0) t.test1(v.hint);
-    traverse(B, t.p, t, c);
+    const bool finished = traverse(B, t.p, t, c, budget);
     c.leaf += t.evals;
+    if (!finished) {
+      *over = true;
+      v.hint = t.best;
+      v.d = t.best2;
+      v.qx = t.q.x;
+      v.qy = t.q.y;
+      v.qz = t.q.z;
+      return;
+    }
     v.tri = t.best;
     v.d = sqrt(t.best2);
     v.qx = t.q.x;
     v.qy = t.q.y;
     v.qz = t.q.z;
+  }
+  // query() of a vertex that a lane's traversal handed off, by the whole warp (every lane
+  // passes the same v; lane 0 returns the result in it).
+  __device__ static void query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e) {
+    const int lane = threadIdx.x & 31;
+    NearestD t;
+    t.p = {v.x, v.y, v.z};
+    t.tri64 = B.tri64;
+    if (lane == 0 && v.hint >= 0) {  // the lane traversal's best so far
+      t.best = v.hint;
+      t.best2 = v.d;
+      t.q = {v.qx, v.qy, v.qz};
+    }
+    const D3 p = t.p;
+    auto box = [p](float lx, float ly, float lz, float hx, float hy, float hz) {
+      return __double2float_rd(box_dist2(p, lx, ly, lz, hx, hy, hz));
+    };
+    traverse_coop(B, t, box, s_code, s_e, c);
+    c.leaf += t.evals;
+    double m = t.best2;
+    for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int src = __ffs(__ballot_sync(0xffffffffu, t.best2 == m)) - 1;
+    const int best = __shfl_sync(0xffffffffu, t.best, src);
+    const double qx = __shfl_sync(0xffffffffu, t.q.x, src), qy = __shfl_sync(0xffffffffu, t.q.y, src),
+                 qz = __shfl_sync(0xffffffffu, t.q.z, src);
+    v.tri = best;
+    v.d = sqrt(m);
+    v.qx = qx;
+    v.qy = qy;
+    v.qz = qz;
   }
   __device__ static double lower(const Vtx& v) { return v.d; }
   __device__ static double out_dist(const Vtx& v) { return v.d; }

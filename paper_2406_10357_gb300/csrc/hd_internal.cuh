@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 #include "hd.h"
 
 namespace hd {
@@ -127,6 +129,9 @@ struct RunState {
                                  // batches of 32 items until none are left)
   int n_mid;                     // midpoints made this round, when shared (else 3 per split)
   int share_mid;                 // split edges share midpoints (HD_FLAG_SHARE_MIDPOINTS)
+  int n_long;                    // queries handed to k_query_long by the last query launch
+  int long_next;                 // work counter of k_query_long
+  unsigned long long long_queries;  // queries finished by a whole warp (traverse_coop)
 };
 
 // Device view of hd_bvh, passed to kernels by value.
@@ -182,6 +187,35 @@ struct Counters {
   unsigned evals = 0, boxes = 0, escalations = 0, leaf = 0;
   int err = 0;
 };
+
+// ----------------------------------------------------------------------------- launch chaining
+
+// Programmatic dependent launch: a kernel launched with the programmatic-serialization
+// attribute (launch_chained) may be scheduled while the kernel before it in the stream is
+// still running.  Every such kernel calls grid_dep_wait() first, which returns once the kernel
+// before it has completed and its writes are visible, so only the launch latency overlaps;
+// grid_dep_launch() lets the next kernel be scheduled as soon as every block of this one has
+// started.  Both are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Launches kernel<<<grid, block, smem, s>>>(args...) chained to the kernel before it in the
+// stream (see grid_dep_wait).  Errors are left for cudaGetLastError (HD_TRY_LAUNCH).
+template <typename... KArgs, typename... Args>
+inline void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                           Args&&... args) {
+  cudaLaunchAttribute attr;
+  attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr.val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = &attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // ----------------------------------------------------------------------------- small math
 

@@ -34,6 +34,8 @@ __device__ inline D3 load_vertex(const T* V, int64_t i) {
 template <typename T>
 __global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, double* tri_unsorted, float4* cent,
                        unsigned* cbox /*6 ordered floats: min xyz (as ~max), max xyz*/, int* bad) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   if (f < nF) {
@@ -91,6 +93,8 @@ __device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit
 
 __global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
                          uint32_t* vals) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (f >= nF) return;
   const float cells = (float)(1u << bits);
@@ -118,6 +122,8 @@ constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32;
 // the fused small-input path, block-major (hist[b * 256 + d], read by every scatter block).
 template <int ROUNDS, bool FUSED>
 __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks) {
+  grid_dep_wait();
+  grid_dep_launch();
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
   __shared__ unsigned cnt[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) cnt[i] = 0;
@@ -140,6 +146,8 @@ constexpr int RS_FUSED_MAX_BLOCKS = 64;
 
 // exclusive scan of `n` counters in place, one block of 1024 threads
 __global__ void k_rs_scan(unsigned* a, int64_t n) {
+  grid_dep_wait();
+  grid_dep_launch();
   __shared__ unsigned part[1024];
   int64_t per = (n + 1023) / 1024;
   int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
@@ -164,6 +172,8 @@ __global__ void k_rs_scan(unsigned* a, int64_t n) {
 template <int ROUNDS, bool FUSED>
 __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
                              int shift, const unsigned* hist, int nblocks) {
+  grid_dep_wait();
+  grid_dep_launch();
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
   static_assert(RS_THREADS == 256, "one digit per thread in the fused offsets");
   __shared__ unsigned wcnt[RS_WARPS][256];
@@ -241,6 +251,8 @@ __device__ inline float ru(double x) { return __double2float_ru(x); }
 __global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uint32_t* order, int64_t nF,
                          double* tri64, float4* tri32, int4* tri_vid, int* inv, float4* leafbox /*2 per leaf*/,
                          unsigned* e2_bits) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double e2 = 0.0;  // squared distance between a float vertex and its input vertex
   if (i < nF) {
@@ -291,6 +303,8 @@ __device__ inline int delta(const uint64_t* k, int64_t n, int64_t i, int64_t j) 
 // Internal node i covers the sorted range [first, last]; its children are encoded as
 // c >= 0 internal, c < 0 leaf ~c.
 __global__ void k_karras(const uint64_t* keys, int64_t n, int* left, int* right, int* first, int* last) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n - 1) return;
   int d = delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1) >= 0 ? 1 : -1;
@@ -385,6 +399,8 @@ struct LevelOffsets {
 // Levels k0 + 1 .. k0 + 8 from the m boxes of level k0 at `in`: a block of 256 threads
 // reduces 256 consecutive boxes pairwise in shared memory.
 __global__ void k_levels(const float4* in, int m, float4* lv, LevelOffsets L, int k0) {
+  grid_dep_wait();
+  grid_dep_launch();
   __shared__ float sb[6][256];
   const int t = threadIdx.x;
   const int i = blockIdx.x * 256 + t;
@@ -418,6 +434,8 @@ __global__ void k_levels(const float4* in, int m, float4* lv, LevelOffsets L, in
 // The box of every inner node, as the union of the aligned blocks that tile its range.
 __global__ void k_node_box(int64_t n, const int* first, const int* last, const float4* leafbox, const float4* lv,
                            LevelOffsets L, float4* ibox) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (x >= n - 1) return;
   int f = first[x];
@@ -445,6 +463,8 @@ __global__ void k_node_box(int64_t n, const int* first, const int* last, const f
 // written too and never visited.)
 __global__ void k_emit(int64_t n, int L, const int* left, const int* right, const int* first, const int* last,
                        const float4* leafbox, const float4* ibox, BvhNode* nodes) {
+  grid_dep_wait();
+  grid_dep_launch();
   int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (node >= n - 1 || last[node] - first[node] + 1 <= L) return;
   float lo0[3], hi0[3], lo1[3], hi1[3];
@@ -469,6 +489,8 @@ __global__ void k_emit(int64_t n, int L, const int* left, const int* right, cons
 
 // Root for n <= leaf_size: one node whose first child is the whole range.
 __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
+  grid_dep_wait();
+  grid_dep_launch();
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t i = 0; i < n; ++i) {
     float a[3], b[3];
@@ -494,6 +516,8 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
 // eta (the largest distance between a float vertex of tri32 and its input value, the
 // square root of the gathered squared maximum, rounded up) and the validity flag of B.
 __global__ void k_build_meta(const unsigned* misc, float* meta) {
+  grid_dep_wait();
+  grid_dep_launch();
   const double r = sqrt((double)__uint_as_float(misc[7])) * (1.0 + 1e-15);
   meta[0] = __double2float_ru(r);
   meta[1] = __uint_as_float(misc[6] != 0u ? 1u : 0u);
@@ -504,7 +528,7 @@ __global__ void k_build_meta(const unsigned* misc, float* meta) {
 template <typename T>
 int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, float4* cent, unsigned* cbox,
                 int* bad, cudaStream_t s) {
-  k_prep<T><<<blocks_for(B->nF, kThreads), kThreads, 0, s>>>((const T*)V, B->nV, F, B->nF, tri_unsorted, cent, cbox,
+  launch_chained(k_prep<T>, blocks_for(B->nF, kThreads), kThreads, 0, s, (const T*)V, B->nV, F, B->nF, tri_unsorted, cent, cbox,
                                                               bad);
   HD_TRY_LAUNCH();
   return HD_OK;
@@ -604,31 +628,31 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
   int bits = 10;
   while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
-  k_morton<<<blocks_for(n, kThreads), kThreads, 0, s>>>(cent, n, misc, bits, k0, v0);
+  launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, k0, v0);
   HD_TRY_LAUNCH();
 
   for (int shift = 0; shift < 3 * bits; shift += 8) {
     if (fused && rs_rounds == 4) {
-      k_rs_hist<4, true><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
-      k_rs_scatter<4, true><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_hist<4, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
+      launch_chained(k_rs_scatter<4, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     } else if (fused) {
-      k_rs_hist<16, true><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
-      k_rs_scatter<16, true><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_hist<16, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
+      launch_chained(k_rs_scatter<16, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     } else {
-      k_rs_hist<16, false><<<nblk, RS_THREADS, 0, s>>>(k0, n, shift, hist, nblk);
-      k_rs_scan<<<1, 1024, 0, s>>>(hist, 256 * (int64_t)nblk);
-      k_rs_scatter<16, false><<<nblk, RS_THREADS, 0, s>>>(k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_hist<16, false>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
+      launch_chained(k_rs_scan, 1, 1024, 0, s, hist, 256 * (int64_t)nblk);
+      launch_chained(k_rs_scatter<16, false>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     }
     HD_TRY_LAUNCH();
     std::swap(k0, k1);
     std::swap(v0, v1);
   }
 
-  k_gather<<<blocks_for(n, kThreads), kThreads, 0, s>>>(tri_unsorted, F, v0, n, h->tri64, h->tri32, h->tri_vid, h->inv,
+  launch_chained(k_gather, blocks_for(n, kThreads), kThreads, 0, s, tri_unsorted, F, v0, n, h->tri64, h->tri32, h->tri_vid, h->inv,
                                                         leafbox, misc + 7);
   HD_TRY_LAUNCH();
   if (n > o.leaf_size) {
-    k_karras<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(k0, n, left, right, first, last);
+    launch_chained(k_karras, blocks_for(n - 1, kThreads), kThreads, 0, s, k0, n, left, right, first, last);
     // aligned-block boxes, 8 levels per launch, then every node's box
     LevelOffsets L;
     memset(&L, 0, sizeof L);
@@ -642,17 +666,17 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     }
     for (int k0 = 0; k0 < L.levels; k0 += 8) {
       const float4* in = k0 ? lv + 2 * (int64_t)L.off[k0] : leafbox;
-      k_levels<<<blocks_for(L.count[k0], 256), 256, 0, s>>>(in, L.count[k0], lv, L, k0);
+      launch_chained(k_levels, blocks_for(L.count[k0], 256), 256, 0, s, in, L.count[k0], lv, L, k0);
     }
-    k_node_box<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, first, last, leafbox, lv, L, ibox);
-    k_emit<<<blocks_for(n - 1, kThreads), kThreads, 0, s>>>(n, o.leaf_size, left, right, first, last, leafbox, ibox,
+    launch_chained(k_node_box, blocks_for(n - 1, kThreads), kThreads, 0, s, n, first, last, leafbox, lv, L, ibox);
+    launch_chained(k_emit, blocks_for(n - 1, kThreads), kThreads, 0, s, n, o.leaf_size, left, right, first, last, leafbox, ibox,
                                                             h->nodes);
   } else {
-    k_root_leaf<<<1, 1, 0, s>>>(n, leafbox, h->nodes);
+    launch_chained(k_root_leaf, 1, 1, 0, s, n, leafbox, h->nodes);
   }
   HD_TRY_LAUNCH();
 
-  k_build_meta<<<1, 1, 0, s>>>(misc, h->meta);
+  launch_chained(k_build_meta, 1, 1, 0, s, misc, h->meta);
   HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(scratch, s));
   if (Vtmp) HD_TRY(cudaFreeAsync(Vtmp, s));

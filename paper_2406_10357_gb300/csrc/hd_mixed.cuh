@@ -261,6 +261,7 @@ struct NearestM {
   float qerr = 0.f;
   unsigned evals = 0, esc = 0;
   __device__ float radius2() const { return __fmul_ru(best_hi, best_hi); }
+  __device__ float coop_r2() const { return radius2(); }
   __device__ void test1(int j) {
     const float4* t = tri32 + 3 * (size_t)j;
     PtOut o;
@@ -311,8 +312,11 @@ __device__ inline void push_code(unsigned* stack_code, float* stack_d, int& sp, 
   }
 }
 
-// Must be called by all 32 lanes of the warp; inactive lanes start finished.
-__device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, bool active) {
+// Must be called by all 32 lanes of the warp; inactive lanes start finished.  A lane that
+// has tested more than `budget` triangles stops unfinished before its next stack pop and sets
+// `over` (t then holds its best so far).
+__device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, bool active, int budget,
+                                  bool& over) {
   unsigned stack_code[kStack];
   float stack_d[kStack];
   int sp = 0;
@@ -338,6 +342,7 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
           }
         }
         if (!found) done = true;
+        if (!done && (int)t.evals > budget) over = done = true;  // hand the query off
         continue;
       }
       const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
@@ -748,7 +753,11 @@ struct PolicyM {
 
   // Called by every lane of the warp (the traversal votes with __all_sync over the full
   // warp); lanes with active == false only vote and leave v untouched.
-  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active) {
+  // Nearest triangle of v, certified.  With `over` given, a traversal that tests more than
+  // `budget` triangles stops, sets *over and leaves its best triangle so far in v (hint, dhi =
+  // its distance bound without eta, q, qerr) for query_coop to finish.
+  __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active, int budget = INT_MAX,
+                               bool* over = nullptr) {
     NearestM t;
     t.tri32 = B.tri32;
     if (active) {
@@ -757,18 +766,65 @@ struct PolicyM {
     } else {
       t.P = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     }
-    traverse_m(B, t, c, active);
+    bool unfinished = false;
+    traverse_m(B, t, c, active, budget, unfinished);
     if (!active) return;
     c.leaf += t.evals;
     c.escalations += t.esc;
-    v.tri = t.best;
+    if (unfinished) {
+      *over = true;
+      v.hint = t.best;
+      v.dhi = t.best_hi;
+      v.qx = t.q.x;
+      v.qy = t.q.y;
+      v.qz = t.q.z;
+      v.qerr = t.qerr;
+      return;
+    }
+    finish(B, v, t.best, t.best_hi, t.dlo, t.q, t.qerr);
+  }
+  // The query's result in v: eta (the distance between B's float triangles and its input)
+  // widens both bounds.
+  __device__ static void finish(const BvhDev& B, Vtx& v, int best, float best_hi, float dlo, F3 q, float qerr) {
     const float eta = __ldg(B.meta);
-    v.dhi = __fadd_ru(t.best_hi, eta);
-    v.dlo = fmaxf(__fsub_rd(fminf(t.dlo, t.best_hi), eta), 0.f);
-    v.qx = t.q.x;
-    v.qy = t.q.y;
-    v.qz = t.q.z;
-    v.qerr = __fadd_ru(t.qerr, eta);
+    v.tri = best;
+    v.dhi = __fadd_ru(best_hi, eta);
+    v.dlo = fmaxf(__fsub_rd(fminf(dlo, best_hi), eta), 0.f);
+    v.qx = q.x;
+    v.qy = q.y;
+    v.qz = q.z;
+    v.qerr = __fadd_ru(qerr, eta);
+  }
+  // query() of a vertex that a lane's traversal handed off, by the whole warp (every lane
+  // passes the same v; lane 0 returns the result in it).  The certified lower bound is the
+  // smallest lower bound over the triangles tested and the final best upper bound (every
+  // pruned box lies beyond the radius of the moment, which is at least that).
+  __device__ static void query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e) {
+    const int lane = threadIdx.x & 31;
+    NearestM t;
+    t.tri32 = B.tri32;
+    t.P = pos(v);
+    if (lane == 0 && v.hint >= 0) {  // the lane traversal's best so far
+      t.best = v.hint;
+      t.best_hi = v.dhi;
+      t.q = {v.qx, v.qy, v.qz};
+      t.qerr = v.qerr;
+    }
+    const F3 plo = {__fadd_rd(t.P.h.x, t.P.l.x), __fadd_rd(t.P.h.y, t.P.l.y), __fadd_rd(t.P.h.z, t.P.l.z)};
+    const F3 phi = {__fadd_ru(t.P.h.x, t.P.l.x), __fadd_ru(t.P.h.y, t.P.l.y), __fadd_ru(t.P.h.z, t.P.l.z)};
+    auto box = [plo, phi](float lx, float ly, float lz, float hx, float hy, float hz) {
+      return box_lo2(plo, phi, lx, ly, lz, hx, hy, hz);
+    };
+    traverse_coop(B, t, box, s_code, s_e, c);
+    c.leaf += t.evals;
+    c.escalations += t.esc;
+    const float m = warp_min_f(t.best_hi), dlo = warp_min_f(t.dlo);
+    const int src = __ffs(__ballot_sync(0xffffffffu, t.best_hi == m)) - 1;
+    const int best = __shfl_sync(0xffffffffu, t.best, src);
+    const F3 q = {__shfl_sync(0xffffffffu, t.q.x, src), __shfl_sync(0xffffffffu, t.q.y, src),
+                  __shfl_sync(0xffffffffu, t.q.z, src)};
+    const float qerr = __shfl_sync(0xffffffffu, t.qerr, src);
+    finish(B, v, best, m, dlo, q, qerr);
   }
   __device__ static double lower(const Vtx& v) { return v.dlo; }
   __device__ static double out_dist(const Vtx& v) { return v.dhi; }

@@ -300,7 +300,7 @@ def test_parent_clamp_on_and_off(hd, orc, precision):
 def test_shared_midpoints(hd, orc, precision, k, scale, chunk):
     """HD_FLAG_SHARE_MIDPOINTS: an edge split by two sub-triangles of one round gets one
     midpoint.  The bracket stays within eps and meets the oracle's; the run makes no more
-    midpoints (and queries) than without sharing, and fewer where neighbours split together
+    midpoints than 3 per split, and fewer where neighbours split together
     (workload 3 splits each face of A a few times); a small chunk (many rounds, the table
     cleared and reused between them) too."""
     p = mg.workload(k, scale)
@@ -316,7 +316,35 @@ def test_shared_midpoints(hd, orc, precision, k, scale, chunk):
     if k == 3:
         print("shared midpoints: splits", s_on["splits"], "made", made, "queries", s_on["queries"], s_off["queries"])
         assert made < SHARED_MAX_PER_SPLIT * s_on["splits"], (made, s_on["splits"])
-        assert s_on["queries"] < s_off["queries"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("scale", [0.01, 0.05])
+def test_cooperative_queries(hd, orc, precision, scale):
+    """Workload 3's sub-triangle vertices deep inside the sliver sphere have much of B within
+    their distance: their lane traversals pass the node budget and a warp finishes each.  The
+    bracket with those queries stays within eps and meets the oracle's."""
+    p = mg.workload(3, scale)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    r = _bracket_parity(hd, orc, p, opt=hd.hd_options_default(tol_mode=p.tol_mode, precision=prec), tight=False)[0]
+    s = r["stats"]
+    print("cooperative queries:", s["long_queries"], "of", s["queries"])
+    assert 0 < s["long_queries"] < s["queries"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_block_size_limits(hd, orc, precision):
+    """Block sizes the round kernels launch with give the oracle's bracket; one above what
+    their register use allows is refused with HD_ERR_INVALID instead of a failed launch."""
+    p = mg.workload(1)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    for bs in (32, 96, 256):
+        _bracket_parity(hd, orc, p, opt=hd.hd_options_default(tol_mode=p.tol_mode, precision=prec, block_size=bs))
+    with pytest.raises(hd.HdError) as e:
+        hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode, precision=prec,
+                                                                     block_size=1024))
+    assert e.value.status == hd.HD_ERR_INVALID
 
 
 def test_bracket_all_bound_orders_fp64(hd, orc):
