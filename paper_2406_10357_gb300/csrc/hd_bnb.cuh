@@ -192,9 +192,10 @@ struct LongList {
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.  Warps take batches of
 // 32 consecutive vertices, one per lane, each lane traversing on its own (the while-while
 // traversal).  With a list, a lane whose traversal tests more than kLongBudget triangles
-// stops and hands its query to k_query_long, which runs next and counts it.
+// stops and hands its query to k_query_long, which runs next and counts it.  Registers are
+// capped at 128 (a few spilled to L1), for 8 resident blocks of 64 threads per SM.
 template <class P>
-__global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
+__global__ void __maxnreg__(128) k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
                         RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
                         LongList ll) {
   grid_dep_wait();
@@ -260,7 +261,7 @@ __global__ void k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* cou
 // shared memory), taken one at a time from a counter since their costs vary widely; with
 // their contribution to l and to the query counts.
 template <class P>
-__global__ void __launch_bounds__(32 * kCoopWarps) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
+__global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
                                                                 RunState* st, double slack_in, const DynParams* dyn,
                                                                 bool round_midpoints) {
   __shared__ unsigned s_code[kCoopWarps][kCoopStack];

@@ -18,14 +18,16 @@
 
 namespace hd {
 
+// Build-time tunables (measured on GB300: the sliver, large-soup and benchmark workloads).
 #ifndef HD_LONG_BUDGET
 #define HD_LONG_BUDGET 10
 #endif
 #ifndef HD_COOP_STACK
-#define HD_COOP_STACK 1024
+#define HD_COOP_STACK 768
 #endif
 constexpr int kCoopStack = HD_COOP_STACK;  // stack entries per warp (8 bytes each, shared memory)
 constexpr int kCoopWarps = 4;              // warps per block of k_query_long
+constexpr int kCoopMinBlocks = 6;          // resident blocks per SM asked of the compiler (<= 80 registers)
 // Triangles a lane's traversal tests before it hands its query to a warp.  The hand-off
 // restarts the traversal from the root with the best triangle found so far as the radius,
 // so a small budget wastes little; most queries finish well within it (a point near B tests

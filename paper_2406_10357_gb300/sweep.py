@@ -6,10 +6,13 @@ tol    -- runtime against the tolerance, from 1e-1 to 1e-8 relative (the paper's
           versus epsilon study, Section 5), on workloads 2 and 5.
 batch  -- workload 4: the batched call untuned and autotuned (MIXED), against sequential
           per-pair calls in FP64 at the same tolerance.
+run    -- one workload at its own tolerance: a warm-up call, then timed calls (the command the
+          kernel profiles of a workload are taken with).
 
     python -m paper_2406_10357_gb300.sweep orders [--pairs 64] [--precision mixed]
     python -m paper_2406_10357_gb300.sweep tol [--workloads 2 5] [--scale 1.0]
     python -m paper_2406_10357_gb300.sweep batch [--pairs 1024] [--tune-pairs 32]
+    python -m paper_2406_10357_gb300.sweep run --workloads 3 [--scale 0.05] [--reps 1]
 
 Each line printed is one JSON record; the inputs are the seeded synthetic workloads of
 ``meshgen``.
@@ -124,23 +127,42 @@ def sweep_batch(n_pairs: int, tune_pairs: int, reps: int = 2):
                    pairs_per_s_with_build=n_pairs / (tb + tr), ok=ok)
 
 
+def run_workloads(workloads, scale: float, precision: int, reps: int, frontier_bytes: int):
+    import torch
+
+    import meshgen as mg
+    import paper_2406_10357_gb300 as hd
+
+    for k in workloads:
+        p = mg.workload(k, scale)
+        VA, FA = torch.from_numpy(p.VA).cuda(), torch.from_numpy(p.FA).cuda()
+        bvh = hd.hd_build_B(torch.from_numpy(p.VB).cuda(), torch.from_numpy(p.FB).cuda())
+        o = hd.hd_options_default(tol_mode=p.tol_mode, precision=precision, max_frontier_bytes=frontier_bytes)
+        t, r = _timed(lambda: hd.hd_hausdorff(bvh, VA, FA, p.tol, o), reps)
+        yield dict(sweep="run", workload=k, scale=scale, faces_A=len(p.FA), faces_B=len(p.FB), tol=p.tol,
+                   seconds=t, lower=r["lower"], upper=r["upper"], status=r["status_str"], stats=r["stats"])
+
+
 def main(argv=None):
     import paper_2406_10357_gb300 as hd
 
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("what", choices=["orders", "tol", "batch"])
+    ap.add_argument("what", choices=["orders", "tol", "batch", "run"])
     ap.add_argument("--tune-pairs", type=int, default=32)
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--workloads", type=int, nargs="+", default=[2, 5])
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--precision", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--frontier-bytes", type=int, default=0, help="run: max_frontier_bytes (0: the default)")
     a = ap.parse_args(argv)
     prec = hd.HD_MIXED if a.precision == "mixed" else hd.HD_FP64
     if a.what == "orders":
         rows = sweep_orders(a.pairs, prec, a.reps)
     elif a.what == "tol":
         rows = sweep_tol(a.workloads, a.scale, prec, a.reps)
+    elif a.what == "run":
+        rows = run_workloads(a.workloads, a.scale, prec, a.reps, a.frontier_bytes)
     else:
         rows = sweep_batch(a.pairs, a.tune_pairs, a.reps)
     for row in rows:
