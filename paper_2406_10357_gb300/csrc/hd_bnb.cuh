@@ -1351,14 +1351,32 @@ __global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tr
   if (dlo) dlo[i] = P::out_dlo(x);
 }
 
+// Nearest queries of n point records (k_points_in) on stream s.  With a list of n ints (and
+// n below 2^30), the lane traversal hands long queries to k_query_long as in the rounds;
+// without one, every lane finishes its own query.  `st` must be zeroed.
+template <class P>
+void query_points(const BvhDev& B, typename P::Vtx* rec, int64_t n, RunState* st, int* list, cudaStream_t s) {
+  if (list && n <= INT32_MAX / 2) {
+    const LongList ll = {list, (int)n};
+    launch_chained(k_query<P>, std::min(blocks_for(n, 128), query_grid<P>(128)), 128, 0, s, B, rec, 0, nullptr, 1,
+                   (int)n, st, 0.0, nullptr, false, MidTable{nullptr, nullptr, nullptr, 0}, ll);
+    launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, rec, ll, st, 0.0, nullptr, false);
+  } else {
+    launch_chained(k_query_points<P>, std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s, B, rec, n, st);
+  }
+}
+
 // hd_nearest: nearest triangle of B for n external points (P as float or double rows).
 template <class P>
 int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                    int32_t* idx, double* foot, double* dlo) {
   typename P::Vtx* tmp = nullptr;
   RunState* st = nullptr;
+  int* list = nullptr;
+  const bool two_phase = n <= INT32_MAX / 2;  // k_query counts in int
   HD_TRY(cudaMallocAsync((void**)&tmp, sizeof(typename P::Vtx) * n, s));
   HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
+  if (two_phase) HD_TRY(cudaMallocAsync((void**)&list, sizeof(int) * n, s));
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
   if (ptype == HD_F64)
     launch_chained(k_points_in<P, double>, blocks_for(n, 256), 256, 0, s, (const double*)Pts, n, tmp);
@@ -1366,12 +1384,13 @@ int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaS
     launch_chained(k_points_in<P, float>, blocks_for(n, 256), 256, 0, s, (const float*)Pts, n, tmp);
   {
     TraceScope tr(HD_K_QUERY, s);
-    k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), tmp, n, st);
+    query_points<P>(bvh_dev(B), tmp, n, st, list, s);
   }
   launch_chained(k_points_out<P>, blocks_for(n, 256), 256, 0, s, tmp, n, B->tri_vid, dist, idx, foot, dlo);
   HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(tmp, s));
   HD_TRY(cudaFreeAsync(st, s));
+  if (list) HD_TRY(cudaFreeAsync(list, s));
   return HD_OK;
 }
 

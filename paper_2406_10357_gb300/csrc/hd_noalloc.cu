@@ -25,7 +25,8 @@ namespace {
 constexpr int64_t kNoAllocMaxPoints = HD_NOALLOC_MAX_POINTS;
 static_assert(sizeof(VtxM) == 64 && sizeof(VtxD) == 64, "one 64-byte record per point");
 static_assert(sizeof(RunState) <= 256, "counters fit the reserved tail");
-constexpr size_t kNoAllocBytes = kNoAllocMaxPoints * 64 + 256;
+// per point: a 64-byte record and a slot of the long-query list; then the counters
+constexpr size_t kNoAllocBytes = kNoAllocMaxPoints * (64 + 4) + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 
@@ -57,12 +58,13 @@ int run(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, 
   if (rc != HD_OK) return rc;
   typename P::Vtx* rec = (typename P::Vtx*)base;
   RunState* st = (RunState*)((unsigned char*)base + kNoAllocMaxPoints * 64);
+  int* list = (int*)((unsigned char*)base + kNoAllocMaxPoints * 64 + 256);
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));  // counters start at zero every call
   if (ptype == HD_F64)
     k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, rec);
   else
     k_points_in<P, float><<<blocks_for(n, 256), 256, 0, s>>>((const float*)Pts, n, rec);
-  k_query_points<P><<<std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s>>>(bvh_dev(B), rec, n, st);
+  query_points<P>(bvh_dev(B), rec, n, st, list, s);
   k_points_out<P><<<blocks_for(n, 256), 256, 0, s>>>(rec, n, B->tri_vid, dist, idx, foot, dlo);
   HD_TRY_LAUNCH();
   return HD_OK;

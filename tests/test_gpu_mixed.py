@@ -75,6 +75,18 @@ def test_nearest_mixed_is_certified(hd, orc, k, scale):
     _check_certified(hd, orc, p.VB, p.FB, P, tight_rel=2e-5)
 
 
+@pytest.mark.parametrize("scale", [0.02, 0.2])
+def test_nearest_mixed_deep_interior_points(hd, orc, scale):
+    """Points deep inside workload 3's superquadric have much of B within their distance:
+    their lane traversals pass the budget and whole warps finish them (k_query_long).  The
+    intervals stay certified and tight."""
+    p = mg.workload(3, scale)
+    rng = np.random.default_rng(31)
+    u = rng.normal(size=(1500, 3))
+    P = (u / np.linalg.norm(u, axis=1, keepdims=True) * rng.uniform(0, 0.7, size=(1500, 1))).astype(np.float32)
+    _check_certified(hd, orc, p.VB, p.FB, P)
+
+
 def test_nearest_mixed_full_size_workload2_sampled(hd, orc):
     p = mg.workload(2)
     rng = np.random.default_rng(21)

@@ -71,6 +71,19 @@ def test_nearest_fp64_matches_bruteforce(hd, orc, k, scale, npts):
     assert err.max() <= REL, err.max()
 
 
+@pytest.mark.parametrize("scale", [0.02, 0.2])
+def test_nearest_fp64_deep_interior_points(hd, orc, scale):
+    """Points deep inside workload 3's superquadric: their queries are finished by whole warps
+    (k_query_long); distances match brute force to 1e-6 relative, like the lane traversal's."""
+    p = mg.workload(3, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    rng = np.random.default_rng(32)
+    u = rng.normal(size=(1500, 3))
+    P = u / np.linalg.norm(u, axis=1, keepdims=True) * rng.uniform(0, 0.7, size=(1500, 1))
+    err, *_ = _pts_parity(hd, orc, bvh, p.VB, p.FB, P, hd.HD_FP64)
+    assert err.max() <= REL, err.max()
+
+
 @pytest.mark.parametrize("leaf", [1, 4, 16])
 def test_nearest_every_leaf_size_and_tiny_B(hd, orc, leaf):
     rng = np.random.default_rng(leaf)
