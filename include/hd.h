@@ -83,7 +83,14 @@ typedef struct {
 /* hd_options.flags.  By default the UpperBound of a child sub-triangle is clamped to its
  * parent's: h(child, B) <= h(parent, B) <= U(parent) since the child lies inside the parent.
  * The paper's cascade (Section 4) has no such clamp; HD_FLAG_NO_PARENT_CLAMP turns it off. */
-enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2, HD_FLAG_SHARE_MIDPOINTS = 4 };
+enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2, HD_FLAG_SHARE_MIDPOINTS = 4, HD_FLAG_WELD_B = 8 };
+/* HD_FLAG_WELD_B (read by hd_build_B, for the mesh it builds a BVH of; for
+ * hd_hausdorff_sym give it when building A's BVH too): vertices at exactly the same
+ * position get one id before the adjacency
+ * test of u3 (Section 3.2, Kang's case 1: two triangles of B sharing an edge), so a soup
+ * (every triangle with its own three vertices) is treated like the indexed mesh it came
+ * from.  Positions are compared exactly (-0 equals +0); the coordinates and the distances
+ * are unchanged. */
 /* HD_FLAG_SHARE_MIDPOINTS: an edge split by two sub-triangles in the same round gets one
  * midpoint vertex (and one nearest query) instead of two, through a per-round hash table of
  * split edges.  Results are the same up to the order of floating-point maxima; it pays where

@@ -22,6 +22,7 @@ HD_FP64, HD_MIXED = 0, 1
 HD_FLAG_NO_PARENT_CLAMP = 1
 HD_FLAG_ASYNC_BUILD = 2
 HD_FLAG_SHARE_MIDPOINTS = 4
+HD_FLAG_WELD_B = 8
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 

@@ -96,7 +96,7 @@ int resolve_options(const hd_options* in, Opts* o) {
   o->max_frontier_bytes = x.max_frontier_bytes;
   memcpy(o->order, x.bound_order, 4);
   o->flags = x.flags;
-  if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS))) return HD_ERR_INVALID;
+  if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS | HD_FLAG_WELD_B))) return HD_ERR_INVALID;
   if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
   if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
   if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;

@@ -243,14 +243,51 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
   }
 }
 
+// ---------------------------------------------------------------- weld (option): one id per position
+
+__device__ inline unsigned long long mix64(unsigned long long z) {  // the SplitMix64 finaliser
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// canon[i] = the index of one vertex with exactly the position of vertex i (the same for all
+// of them): vertices are inserted into an open-addressing table keyed by their coordinates;
+// the first to claim an entry represents its position.  -0 and +0 are the same position.
+// table: 2^k ints, zeroed, at least twice the vertices (so a probe always ends).
+template <typename T>
+__global__ void k_weld(const T* V, int64_t nV, int* table, unsigned long long mask, int* canon) {
+  grid_dep_wait();
+  grid_dep_launch();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= nV) return;
+  const double x = (double)V[3 * i] + 0.0, y = (double)V[3 * i + 1] + 0.0, z = (double)V[3 * i + 2] + 0.0;
+  unsigned long long h = mix64((unsigned long long)__double_as_longlong(x) ^
+                               mix64((unsigned long long)__double_as_longlong(y) ^
+                                     mix64((unsigned long long)__double_as_longlong(z))));
+  h &= mask;
+  int id = (int)i;
+  for (unsigned long long probe = 0; probe <= mask; ++probe) {
+    const int prev = atomicCAS(&table[h], 0, (int)i + 1);
+    if (prev == 0) break;  // this vertex represents its position
+    const int64_t j = prev - 1;
+    if ((double)V[3 * j] == x && (double)V[3 * j + 1] == y && (double)V[3 * j + 2] == z) {
+      id = (int)j;
+      break;
+    }
+    h = (h + 1) & mask;
+  }
+  canon[i] = id;
+}
+
 // ---------------------------------------------------------------- 4: sorted triangles, leaf boxes
 
 __device__ inline float rd(double x) { return __double2float_rd(x); }
 __device__ inline float ru(double x) { return __double2float_ru(x); }
 
 __global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uint32_t* order, int64_t nF,
-                         double* tri64, float4* tri32, int4* tri_vid, int* inv, float4* leafbox /*2 per leaf*/,
-                         unsigned* e2_bits) {
+                         const int* canon, int64_t nV, double* tri64, float4* tri32, int4* tri_vid, int* inv,
+                         float4* leafbox /*2 per leaf*/, unsigned* e2_bits) {
   grid_dep_wait();
   grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -279,7 +316,14 @@ __global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uin
     tri32[3 * i] = out[0];
     tri32[3 * i + 1] = out[1];
     tri32[3 * i + 2] = out[2];
-    tri_vid[i] = make_int4(F[3 * f], F[3 * f + 1], F[3 * f + 2], (int)f);
+    // vertex ids for the adjacency of u3 (welded ids with canon; an index out of range makes
+    // B invalid and is kept as it is)
+    int id[3];
+    for (int v = 0; v < 3; ++v) {
+      const int k = F[3 * f + v];
+      id[v] = canon && k >= 0 && k < nV ? canon[k] : k;
+    }
+    tri_vid[i] = make_int4(id[0], id[1], id[2], (int)f);
     inv[f] = (int)i;
     leafbox[2 * i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     leafbox[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
@@ -601,6 +645,11 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   size_t o_tri = carve(sizeof(double) * 9 * n), o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
          o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
          o_ibox = carve(32 * n), o_lv = carve(32 * (n + 64)), o_int = carve(4 * 4 * n + 64), o_misc = carve(64);
+  // weld: canonical vertex ids, and a table of at least twice the vertices
+  const bool weld = (o.flags & HD_FLAG_WELD_B) != 0;
+  uint64_t weld_entries = 1024;
+  while (weld && weld_entries < 2 * (uint64_t)B->nV) weld_entries <<= 1;
+  const size_t o_canon = weld ? carve(4 * (size_t)B->nV) : 0, o_wtab = weld ? carve(4 * weld_entries) : 0;
   char* scratch = nullptr;
   HD_TRY(cudaMallocAsync((void**)&scratch, off, s));
   double* tri_unsorted = (double*)(scratch + o_tri);
@@ -648,8 +697,20 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     std::swap(v0, v1);
   }
 
-  launch_chained(k_gather, blocks_for(n, kThreads), kThreads, 0, s, tri_unsorted, F, v0, n, h->tri64, h->tri32, h->tri_vid, h->inv,
-                                                        leafbox, misc + 7);
+  int* canon = nullptr;
+  if (weld) {
+    canon = (int*)(scratch + o_canon);
+    int* wtab = (int*)(scratch + o_wtab);
+    HD_TRY(cudaMemsetAsync(wtab, 0, 4 * weld_entries, s));
+    if (B->vtype == HD_F64)
+      launch_chained(k_weld<double>, blocks_for(B->nV, kThreads), kThreads, 0, s, (const double*)V, B->nV, wtab,
+                     (unsigned long long)(weld_entries - 1), canon);
+    else
+      launch_chained(k_weld<float>, blocks_for(B->nV, kThreads), kThreads, 0, s, (const float*)V, B->nV, wtab,
+                     (unsigned long long)(weld_entries - 1), canon);
+  }
+  launch_chained(k_gather, blocks_for(n, kThreads), kThreads, 0, s, tri_unsorted, F, v0, n, (const int*)canon,
+                 (int64_t)B->nV, h->tri64, h->tri32, h->tri_vid, h->inv, leafbox, misc + 7);
   HD_TRY_LAUNCH();
   if (n > o.leaf_size) {
     launch_chained(k_karras, blocks_for(n - 1, kThreads), kThreads, 0, s, k0, n, left, right, first, last);

@@ -134,6 +134,67 @@ def test_upper_bounds_match_oracle(hd, orc):
             assert code[i] == names[co], (i, code[i], co)
 
 
+def _soup(V, F):
+    """Every triangle with its own three vertices (positions copied exactly)."""
+    V = np.asarray(V)
+    return np.ascontiguousarray(V[np.asarray(F)].reshape(-1, 3)), np.arange(3 * len(F), dtype=np.int32).reshape(-1, 3)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_weld_soup_bounds_equal_indexed_mesh(hd, orc, dtype):
+    """HD_FLAG_WELD_B: a soup of B's triangles, welded, gives exactly the UpperBounds of the
+    indexed mesh (u3's shared-edge case finds the same neighbours), which match the oracle's."""
+    p = mg.workload(1)
+    VB = np.asarray(p.VB, dtype)
+    VS, FS = _soup(VB, p.FB)
+    idx = hd.hd_build_B(VB, p.FB)
+    welded = hd.hd_build_B(VS, FS, hd.hd_options_default(flags=hd.HD_FLAG_WELD_B))
+    rng = np.random.default_rng(15)
+    V = np.asarray(p.VA, float)
+    n = 800
+    f = rng.integers(0, len(p.FA), n)
+    W = rng.dirichlet([1, 1, 1], size=(n, 3))
+    c = rng.dirichlet([1, 1, 1], size=n)[:, None, :]
+    W = c + rng.choice([1.0, 0.3, 0.05], size=n)[:, None, None] * (W - c)
+    T = np.einsum("nkj,njd->nkd", W, V[p.FA[f]])
+    VBd = np.asarray(VB, float)
+    d, I, q = orc.nearest(T.reshape(-1, 3), VBd, p.FB)
+    d, I, q = d.reshape(n, 3), I.reshape(n, 3), q.reshape(n, 3, 3)
+    l0 = float(np.quantile(d, 0.8))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    args = (t(T.reshape(n, 9)), t(d), t(I.astype(np.int32)), t(q.reshape(n, 9)), l0)
+    o3 = hd.hd_options_default(bound_order=(3,))  # u3 alone, so that every item reaches it
+    U1, c1 = (x.cpu().numpy() for x in hd.hd_upper_bounds(idx, *args, opt=o3))
+    U2, c2 = (x.cpu().numpy() for x in hd.hd_upper_bounds(welded, *args, opt=o3))
+    assert np.array_equal(U1, U2) and np.array_equal(c1, c2)
+    # without the weld the soup has no shared edges: some u3 values change
+    U3, _ = (x.cpu().numpy() for x in hd.hd_upper_bounds(hd.hd_build_B(VS, FS), *args, opt=o3))
+    assert np.any(U3 != U1)
+    for i in rng.choice(n, size=150, replace=False):
+        Uo, _ = orc.upper_bound(T[i], d[i], I[i], q[i], VBd, p.FB, l0, order=(3,))
+        assert abs(U2[i] - Uo) <= 1e-9 * max(1.0, Uo), (i, U2[i], Uo)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_weld_soup_run_equals_indexed_run(hd, orc, precision):
+    """The whole run on a welded soup of B is the run on the indexed mesh: same BVH (same
+    triangles, same Morton order), same neighbours for u3, so the same bracket and counts.
+    Without the weld the soup's bracket is still valid."""
+    p = mg.workload(1)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    o = hd.hd_options_default(tol_mode=p.tol_mode, precision=prec)
+    VS, FS = _soup(p.VB, p.FB)
+    r1 = hd.hd_hausdorff(hd.hd_build_B(p.VB, p.FB), p.VA, p.FA, p.tol, o)
+    r2 = hd.hd_hausdorff(hd.hd_build_B(VS, FS, hd.hd_options_default(flags=hd.HD_FLAG_WELD_B)), p.VA, p.FA, p.tol, o)
+    assert (r1["lower"], r1["upper"], r1["status"]) == (r2["lower"], r2["upper"], r2["status"])
+    for k in ("rounds", "splits", "queries", "pointtri_evals", "retired"):
+        assert r1["stats"][k] == r2["stats"][k], k
+    r3 = hd.hd_hausdorff(hd.hd_build_B(VS, FS), p.VA, p.FA, p.tol, o)
+    ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    assert r3["status"] == hd.HD_OK and r3["upper"] - r3["lower"] <= p.tol * (1 + 1e-12)
+    assert max(r3["lower"], ro["lower"]) <= min(r3["upper"], ro["upper"]) + 1e-12
+
+
 def _load_golden():
     with open(GOLDEN) as f:
         return json.load(f)["cases"]
