@@ -46,9 +46,9 @@ FLOPS_PER_BOX_TEST = 17
 FLOPS_PER_ITEM_BOUND = 100
 BYTES_PER_NODE = 128
 # device->host bytes per step (the build is queued without a read-back): a run-state
-# snapshot (248 B) and the device-side parameters (32 B) per queued frontier round, plus the
+# snapshot (256 B) and the device-side parameters (32 B) per queued frontier round, plus the
 # final state after a round queued past the last (runs of 3 or more rounds)
-RUNSTATE_BYTES = 248
+RUNSTATE_BYTES = 256
 
 
 def parse():
@@ -198,16 +198,12 @@ def profiled_traffic(kind: str, precision: str):
 
 
 def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> int:
-    """Kernels one hd_build_B + hd_hausdorff call launches (the library's launch sequence):
-    build -- centroids, Morton codes, per sort pass a digit count and a scatter (plus a scan
-    when B needs more than 64 sort tiles), the gather, then the radix tree, the aligned-block
-    boxes (one launch per 8 levels), the node boxes and the node emission (one root kernel
-    instead when B fits in one leaf), and B's eta and validity; A's referenced vertices,
-    validation with pool set-up, and the tolerance (3), round 0 (query, cooperative query of
-    the long traversals, bound faces), 5 per frontier round (control, select, query,
-    cooperative query, bound children), and in MIXED the u4 pass after every bound kernel;
-    runs of 3 or more rounds also queue one round after the last, whose kernels find the loop
-    stopped and return at once."""
+    """Kernels one hd_build_B + hd_hausdorff call launches.  hd_hausdorff counts its own
+    (stats["kernel_launches"]); the build's sequence is fixed by n_B: centroids, Morton
+    codes, per sort pass a digit count and a scatter (plus a scan when B needs more than 64
+    sort tiles), the gather, then the radix tree, the aligned-block boxes (one launch per 8
+    levels), the node boxes and the node emission (one root kernel instead when B fits in
+    one leaf), and B's eta and validity."""
     bits = 10
     while bits < 16 and (1 << (3 * (bits - 4))) < nB:
         bits += 1
@@ -216,10 +212,7 @@ def kernel_launches(nB: int, stats: dict, mixed: bool, leaf_size: int = 1) -> in
     fused = -(-nB // tile) <= 64
     levels = max(1, (nB - 1).bit_length())  # aligned-block levels, 8 per launch
     build = 2 + passes * (2 if fused else 3) + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1) + 1
-    rounds = stats["rounds"]
-    full = rounds + 1 if rounds >= 3 else max(rounds, 1)
-    run = 3 + 3 + (1 if mixed else 0) + (6 if mixed else 5) * full
-    return build + run
+    return build + int(stats["kernel_launches"])
 
 
 def measured_peaks():

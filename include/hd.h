@@ -83,7 +83,17 @@ typedef struct {
 /* hd_options.flags.  By default the UpperBound of a child sub-triangle is clamped to its
  * parent's: h(child, B) <= h(parent, B) <= U(parent) since the child lies inside the parent.
  * The paper's cascade (Section 4) has no such clamp; HD_FLAG_NO_PARENT_CLAMP turns it off. */
-enum { HD_FLAG_NO_PARENT_CLAMP = 1, HD_FLAG_ASYNC_BUILD = 2, HD_FLAG_SHARE_MIDPOINTS = 4, HD_FLAG_WELD_B = 8 };
+enum {
+  HD_FLAG_NO_PARENT_CLAMP = 1,
+  HD_FLAG_ASYNC_BUILD = 2,
+  HD_FLAG_SHARE_MIDPOINTS = 4,
+  HD_FLAG_WELD_B = 8,
+  HD_FLAG_NO_SMALL_ROUNDS = 16
+};
+/* HD_FLAG_NO_SMALL_ROUNDS: every frontier round runs as a sequence of grid-wide kernels.  By
+ * default, rounds over a frontier of at most 64 items (the last rounds of most runs) run
+ * inside one single-block kernel that loops over them without the host; the results are the
+ * same either way. */
 /* HD_FLAG_WELD_B (read by hd_build_B, for the mesh it builds a BVH of; for
  * hd_hausdorff_sym give it when building A's BVH too): vertices at exactly the same
  * position get one id before the adjacency
@@ -120,6 +130,7 @@ typedef struct {
   double dA;                 /* bbox diagonal of A's referenced vertices                    */
   int64_t long_queries;      /* queries whose traversal a whole warp finished (part of
                                 queries: those with many BVH boxes within their distance)  */
+  int64_t kernel_launches;   /* GPU kernels the call launched                               */
 } hd_stats;
 
 typedef struct {

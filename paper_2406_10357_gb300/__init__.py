@@ -23,6 +23,7 @@ HD_FLAG_NO_PARENT_CLAMP = 1
 HD_FLAG_ASYNC_BUILD = 2
 HD_FLAG_SHARE_MIDPOINTS = 4
 HD_FLAG_WELD_B = 8
+HD_FLAG_NO_SMALL_ROUNDS = 16
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 
@@ -42,7 +43,8 @@ class HdStats(C.Structure):
     _fields_ = [("rounds", C.c_int64), ("splits", C.c_int64), ("queries", C.c_int64), ("pointtri_evals", C.c_int64),
                 ("leaf_tests", C.c_int64), ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
-                ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64)]
+                ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64),
+                ("kernel_launches", C.c_int64)]
 
 
 class HdResult(C.Structure):
@@ -214,7 +216,7 @@ def _result(r: HdResult) -> dict:
                            box_tests=s.box_tests, discards={BOUND_NAMES[k]: s.discards[k] for k in range(6)},
                            retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
                            pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA,
-                           long_queries=s.long_queries))
+                           long_queries=s.long_queries, kernel_launches=s.kernel_launches))
 
 
 def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:

@@ -96,7 +96,8 @@ int resolve_options(const hd_options* in, Opts* o) {
   o->max_frontier_bytes = x.max_frontier_bytes;
   memcpy(o->order, x.bound_order, 4);
   o->flags = x.flags;
-  if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS | HD_FLAG_WELD_B))) return HD_ERR_INVALID;
+  if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS | HD_FLAG_WELD_B |
+                                      HD_FLAG_NO_SMALL_ROUNDS))) return HD_ERR_INVALID;
   if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
   if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
   if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;
@@ -333,6 +334,7 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
   S.peak_frontier = std::max(X.peak_frontier, Y.peak_frontier);
   S.pool_vertices = X.pool_vertices + Y.pool_vertices;
   S.long_queries = X.long_queries + Y.long_queries;
+  S.kernel_launches = X.kernel_launches + Y.kernel_launches;
   S.eps_abs = X.eps_abs;
   S.dA = X.dA;
   return HD_OK;

@@ -195,11 +195,9 @@ struct LongList {
 // stops and hands its query to k_query_long, which runs next and counts it.  Registers are
 // capped at 128 (a few spilled to L1), for 8 resident blocks of 64 threads per SM.
 template <class P>
-__global__ void __maxnreg__(128) k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
+__device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
                         RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
                         LongList ll) {
-  grid_dep_wait();
-  grid_dep_launch();
   int count = cap;
   if (round_midpoints) {
     // the midpoints made by this frontier round, from the pool size at its start
@@ -257,17 +255,21 @@ __global__ void __maxnreg__(128) k_query(BvhDev B, typename P::Vtx* pool, int be
   flush_counters(st, c);
 }
 
+template <class P>
+__global__ void __maxnreg__(128) k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
+                        RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
+                        LongList ll) {
+  grid_dep_wait();
+  grid_dep_launch();
+  query_body<P>(B, pool, beg, count_ptr, mult, cap, st, slack_in, dyn, round_midpoints, tab, ll);
+}
+
 // The queries k_query handed off, one warp each (traverse_coop, with this warp's stack in
 // shared memory), taken one at a time from a counter since their costs vary widely; with
 // their contribution to l and to the query counts.
 template <class P>
-__global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
-                                                                RunState* st, double slack_in, const DynParams* dyn,
-                                                                bool round_midpoints) {
-  __shared__ unsigned s_code[kCoopWarps][kCoopStack];
-  __shared__ float s_e[kCoopWarps][kCoopStack];
-  grid_dep_wait();
-  grid_dep_launch();
+__device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList ll, RunState* st, double slack_in,
+                                       const DynParams* dyn, bool round_midpoints, unsigned* s_code, float* s_e) {
   if (round_midpoints && st->stop) return;  // as k_query (uniform over the grid)
   const int n = min(st->n_long, ll.cap);
   if (n == 0) return;  // uniform over the grid
@@ -283,7 +285,7 @@ __global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(
     if (i >= n) break;
     const int k = ll.idx[i];
     typename P::Vtx v = pool[k];
-    P::query_coop(B, v, c, s_code[w], s_e[w]);
+    P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack);
     if (lane == 0) {
       pool[k] = v;
       lmax = fmax(lmax, P::lower(v) - slack);
@@ -299,6 +301,17 @@ __global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(
     }
   }
   flush_counters(st, c);
+}
+
+template <class P>
+__global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
+                                                                RunState* st, double slack_in, const DynParams* dyn,
+                                                                bool round_midpoints) {
+  __shared__ unsigned s_code[kCoopWarps * kCoopStack];
+  __shared__ float s_e[kCoopWarps * kCoopStack];
+  grid_dep_wait();
+  grid_dep_launch();
+  query_long_body<P>(B, pool, ll, st, slack_in, dyn, round_midpoints, s_code, s_e);
 }
 
 // Per-thread outcome counts and maxima of classified items, flushed once per warp.
@@ -443,10 +456,8 @@ __global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32
 // The u4 pass (MIXED): items whose cascade reached a trailing u4 get it here, in FP64, with
 // every lane of a warp on its own item; then discard / retire / keep as usual.
 template <class P>
-__global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
+__device__ inline void bound_u4_body(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
                            RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
-  grid_dep_wait();
-  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const RunParams rp = with_dyn(rp_in);
   int n = min(*(volatile int*)&st->n_u4, cap);
@@ -466,6 +477,14 @@ __global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename
     classify<P>(st, it, th, code, next, next_cap, nullptr, ty);
   }
   flush_tally(st, ty);
+}
+
+template <class P>
+__global__ void k_bound_u4(BvhDev B, const typename P::Vtx* pool, const typename P::Item* u4list, int cap,
+                           RunState* st, RunParams rp_in, typename P::Item* next, int next_cap) {
+  grid_dep_wait();
+  grid_dep_launch();
+  bound_u4_body<P>(B, pool, u4list, cap, st, rp_in, next, next_cap);
 }
 
 __device__ inline unsigned edge_hash(unsigned long long k, unsigned mask) {
@@ -543,11 +562,9 @@ __device__ inline int mid_slot(bool active, int s, int e, int ia, int ib, const 
 // Select the items to split: discard (U < l), retire (U <= l + eps), split up to K of the
 // rest (three midpoints each into the pool at mbase), carry the others over.
 template <class P>
-__global__ void k_select(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
+__device__ inline void select_body(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
                          int4* split_mid, MidTable tab, typename P::Vtx* pool, typename P::Item* next, int next_cap,
                          typename P::Item* promo, int promo_cap) {
-  grid_dep_wait();
-  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const int n_front = st->n_front, K = st->K, mbase = st->n_pool;
   const RunParams rp = with_dyn(rp_in);
@@ -609,13 +626,20 @@ __global__ void k_select(const typename P::Item* front, RunState* st, RunParams 
   flush_tally(st, ty);
 }
 
+template <class P>
+__global__ void k_select(const typename P::Item* front, RunState* st, RunParams rp_in, int4* split_par,
+                         int4* split_mid, MidTable tab, typename P::Vtx* pool, typename P::Item* next, int next_cap,
+                         typename P::Item* promo, int promo_cap) {
+  grid_dep_wait();
+  grid_dep_launch();
+  select_body<P>(front, st, rp_in, split_par, split_mid, tab, pool, next, next_cap, promo, promo_cap);
+}
+
 // The four children of every split (Section 4, midpoint subdivision):
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
 template <class P>
-__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
+__device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
                                  const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
-  grid_dep_wait();
-  grid_dep_launch();
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
   const RunParams rp = with_dyn(rp_in);
   const int mbase = st->n_pool, share = st->share_mid;
@@ -648,6 +672,14 @@ __global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const in
   }
   flush_counters(st, c);
   flush_tally(st, ty);
+}
+
+template <class P>
+__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
+                                 const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
+  grid_dep_wait();
+  grid_dep_launch();
+  bound_children_body<P>(B, pool, split_par, split_mid, st, rp_in, next, next_cap, u4list);
 }
 
 // Per-loop constants of the round control.
@@ -711,9 +743,11 @@ __host__ __device__ inline int close_round(RunState& st, long long rounds_left) 
 // (pool entries [0, n_pool0), after the bounds of its first items -- the faces of A, or the
 // promoted items -- were launched).  Once stopped, later rounds find `stop` set and do
 // nothing, so the host may queue a round before it has read the previous one.
-static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_pool0) {
-  grid_dep_wait();
-  grid_dep_launch();
+// With max_front set, a round over more items than that, or after a round that handed more
+// than max_long queries to the cooperative pass, is not opened (the loop goes on with
+// in_round cleared, for the normal path to open it).
+__device__ inline void round_ctl_body(RunState* st, RoundCtl c, int init, int n_pool0, int max_front = INT_MAX,
+                                      int max_long = INT_MAX) {
   if (init) {
     st->stop = 0;
     st->status = HD_OK;
@@ -738,6 +772,7 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
     st->stop = 1;
     return;
   }
+  if (st->n_front > max_front || st->n_long > max_long) return;
   st->K = (int)K;
   st->n_next = 0;
   st->n_split = 0;
@@ -750,6 +785,77 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
   st->n_long = 0;
   st->long_next = 0;
   st->in_round = 1;
+}
+
+static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_pool0) {
+  grid_dep_wait();
+  grid_dep_launch();
+  round_ctl_body(st, c, init, n_pool0);
+}
+
+// ----------------------------------------------------------------------------- small rounds
+
+// Rounds over a small frontier (the last rounds of most runs) in one block: each phase of a
+// round is a kernel of the normal path, and for a frontier of a few dozen items each is one
+// pass of a few warps, so the launches and the host's reading of the round dominate.  Here
+// one block runs the same steps (control, select, query, cooperative query, bound, u4) with
+// block barriers between them, round after round, until the loop stops, the frontier grows
+// past kTailFront, or a round hands more than kTailWarps queries to the cooperative pass (a
+// round with many long traversals needs the whole GPU); the normal path then takes over, so
+// any frontier is correct.
+constexpr int kTailThreads = 256;
+constexpr int kTailWarps = kTailThreads / 32;
+constexpr int kTailFront = 64;
+constexpr size_t kTailSmem = (sizeof(unsigned) + sizeof(float)) * kTailWarps * kCoopStack;
+
+template <class P>
+struct TailBufs {
+  typename P::Item* front[2];
+  int4* split_par;
+  int4* split_mid;
+  MidTable tab;
+  typename P::Vtx* pool;
+  typename P::Item* promo;
+  int promo_cap;
+  int front_cap;
+  typename P::Item* u4list;
+  LongList longq;
+};
+
+template <class P>
+__global__ void __launch_bounds__(kTailThreads) k_tail_rounds(BvhDev B, TailBufs<P> a, RunState* st, RunParams rp,
+                                                              RoundCtl c, int init, int n_pool0, int cur) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];  // kTailSmem bytes: the warps' cooperative stacks
+  unsigned* s_code = reinterpret_cast<unsigned*>(tail_smem);
+  float* s_e = reinterpret_cast<float*>(tail_smem + sizeof(unsigned) * kTailWarps * kCoopStack);
+  __shared__ int s_go;
+  grid_dep_wait();
+  grid_dep_launch();
+  int rounds = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      // the control step of k_round_ctl, refusing to open a round over kTailFront items
+      round_ctl_body(st, c, init, n_pool0, kTailFront, kTailWarps);
+      s_go = !st->stop && st->in_round;
+    }
+    init = 0;
+    __syncthreads();
+    if (!s_go) break;
+    select_body<P>(a.front[cur], st, rp, a.split_par, a.split_mid, a.tab, a.pool, a.front[cur ^ 1], a.front_cap,
+                   a.promo, a.promo_cap);
+    __syncthreads();
+    query_body<P>(B, a.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, a.tab, a.longq);
+    __syncthreads();
+    query_long_body<P>(B, a.pool, a.longq, st, rp.slack, rp.dyn, true, s_code, s_e);
+    __syncthreads();
+    bound_children_body<P>(B, a.pool, a.split_par, a.split_mid, st, rp, a.front[cur ^ 1], a.front_cap, a.u4list);
+    __syncthreads();
+    if (a.u4list) bound_u4_body<P>(B, a.pool, a.u4list, a.front_cap, st, rp, a.front[cur ^ 1], a.front_cap);
+    __syncthreads();
+    cur ^= 1;
+    ++rounds;
+  }
+  if (threadIdx.x == 0) st->tail_rounds = rounds;
 }
 
 // Nearest queries for external points (hd_nearest): P as double rows.
@@ -984,6 +1090,25 @@ inline int host_res(HostRes*& out) {
   return HD_OK;
 }
 
+#ifndef HD_AHEAD_FROM
+#define HD_AHEAD_FROM 2  // rounds read before the host keeps one round queued ahead
+#endif
+
+// k_tail_rounds takes more than the default 48 KB of dynamic shared memory: allowed once per
+// device.
+template <class P>
+cudaError_t tail_smem_attr() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_tail_rounds<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem);
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_relaxed);
+  return e;
+}
+
 // Frontier rounds of policy P over the items that the bound kernel before it left in
 // R.front[R.cur] (their count in st->n_next), until the frontier is empty, the capacity or
 // round limit is reached, or an error is flagged.  Each round starts with k_round_ctl, which
@@ -1020,6 +1145,13 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   int64_t front_bound = first_front_bound;  // the first round is queued without a wait
   int cur = R.cur;
   bool init = true;
+  // the run state and parameters after the work queued so far, into ring slot `slot`
+  auto snapshot = [&](int slot) -> int {
+    HD_TRY(cudaMemcpyAsync(&hr.hb->ring[slot], st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+    HD_TRY(cudaEventRecord(hr.ev[slot], s));
+    return HD_OK;
+  };
   auto issue = [&](int slot, int64_t nf) -> int {
     // grids for a frontier of at most nf items (grid-stride kernels: any size is correct)
     const int64_t k = std::max<int64_t>(1, std::min<int64_t>(nf, R.chunk));
@@ -1049,22 +1181,45 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     }
     HD_TRY_LAUNCH();
     cur ^= 1;
-    HD_TRY(cudaMemcpyAsync(&hr.hb->ring[slot], st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
-    HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
-    HD_TRY(cudaEventRecord(hr.ev[slot], s));
-    return HD_OK;
+    return snapshot(slot);
   };
-  long long issued = 0, seen = 0;
+  // the small-round kernel, for a frontier of at most kTailFront items; it may run any number
+  // of rounds, so nothing is queued after it until its snapshot has been read
+  const TailBufs<P> tb = {{R.front[0], R.front[1]}, R.split_par, R.split_mid, R.tab, R.pool, R.promo, (int)R.promo_cap,
+                          (int)R.front_cap, R.u4list, R.longq};
+  auto issue_tail = [&](int slot) -> int {
+    HD_TRY(tail_smem_attr<P>());
+    {
+      TraceScope tr(HD_K_SELECT, s);
+      launch_chained(k_tail_rounds<P>, 1, kTailThreads, kTailSmem, s, B, tb, st, rp, c, init ? 1 : 0, n_pool0, cur);
+      init = false;
+    }
+    HD_TRY_LAUNCH();
+    return snapshot(slot);
+  };
+  long long issued = 0, seen = 0, tail_at = -1;  // tail_at: the snapshot of the small-round kernel in flight
+  int last_long = 0;  // long queries of the last round read
   for (;;) {
-    const long long ahead = seen >= 2 ? 2 : 1;  // rounds in flight, the one being read included
-    while (issued < seen + ahead) {
-      int rc = issue((int)(issued & 1), front_bound);
+    const long long ahead = seen >= HD_AHEAD_FROM ? 2 : 1;  // rounds in flight, the one being read included
+    while (issued < seen + ahead && tail_at < 0) {
+      int rc;
+      if (front_bound <= kTailFront && last_long <= kTailWarps && !(o.flags & HD_FLAG_NO_SMALL_ROUNDS)) {
+        rc = issue_tail((int)(issued & 1));
+        tail_at = issued;
+      } else {
+        rc = issue((int)(issued & 1), front_bound);
+      }
       if (rc != HD_OK) return rc;
       ++issued;
       front_bound = std::min<int64_t>(4 * front_bound, R.front_cap);  // for a round queued ahead
     }
     HD_TRY(cudaEventSynchronize(hr.ev[seen & 1]));
     const RunState& h = hr.hb->ring[seen & 1];
+    if (seen == tail_at) {  // the small-round kernel's rounds each swapped the frontier buffers
+      if (h.tail_rounds & 1) cur ^= 1;
+      tail_at = -1;
+    }
+    last_long = h.n_long;
     ++seen;
     // the next round's frontier is h.n_next; one more round ahead may have up to 4x as many
     front_bound = issued == seen ? (int64_t)h.n_next : std::min<int64_t>(4 * (int64_t)h.n_next, R.front_cap);
@@ -1198,6 +1353,7 @@ int run_bnb(const RunIO& io) {
   // a block the round kernels cannot launch with (MIXED also runs the FP64 ones)
   if (o.block_size > round_block_limit<P>() || (!P::kFp64 && o.block_size > round_block_limit<PolicyD>()))
     return HD_ERR_INVALID;
+  const long long launches0 = g_launches;
 
   HostRes* hr = nullptr;
   {
@@ -1304,6 +1460,7 @@ int run_bnb(const RunIO& io) {
   S.splits = T.splits;
   S.queries = (int64_t)hst->queries;
   S.long_queries = (int64_t)hst->long_queries;
+  S.kernel_launches = g_launches - launches0;
   S.pointtri_evals = (int64_t)hst->evals;
   S.leaf_tests = (int64_t)hst->leaf_tests;
   S.box_tests = (int64_t)hst->box_tests;

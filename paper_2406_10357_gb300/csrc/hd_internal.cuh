@@ -132,6 +132,8 @@ struct RunState {
   int n_long;                    // queries handed to k_query_long by the last query launch
   int long_next;                 // work counter of k_query_long
   unsigned long long long_queries;  // queries finished by a whole warp (traverse_coop)
+  int tail_rounds;               // rounds the last k_tail_rounds launch ran
+  int pad_;
 };
 
 // Device view of hd_bvh, passed to kernels by value.
@@ -199,11 +201,15 @@ struct Counters {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
+// Kernels this host thread has launched through launch_chained (the library's own count).
+inline thread_local long long g_launches = 0;
+
 // Launches kernel<<<grid, block, smem, s>>>(args...) chained to the kernel before it in the
 // stream (see grid_dep_wait).  Errors are left for cudaGetLastError (HD_TRY_LAUNCH).
 template <typename... KArgs, typename... Args>
 inline void launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
                            Args&&... args) {
+  ++g_launches;
   cudaLaunchAttribute attr;
   attr.id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr.val.programmaticStreamSerializationAllowed = 1;

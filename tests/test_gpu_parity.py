@@ -421,6 +421,36 @@ def test_block_size_limits(hd, orc, precision):
     assert e.value.status == hd.HD_ERR_INVALID
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("k,scale,chunk", [(1, 1.0, 0), (1, 1.0, 16), (2, 0.02, 0), (3, 0.01, 0), (4, None, 0)])
+def test_small_round_kernel_same_result(hd, orc, precision, k, scale, chunk):
+    """Rounds over small frontiers run in one single-block kernel (k_tail_rounds) unless
+    HD_FLAG_NO_SMALL_ROUNDS: both paths give the same bracket and counts, and the bracket meets
+    the oracle's.  A chunk of 16 splits per round makes the frontier cross the small-round
+    limit back and forth."""
+    p = mg.batch_workload(n_pairs=1)[0] if k == 4 else mg.workload(k, scale)
+    prec = hd.HD_FP64 if precision == "fp64" else hd.HD_MIXED
+    mk = lambda f: hd.hd_options_default(tol_mode=p.tol_mode, precision=prec, frontier_chunk=chunk, flags=f)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    a = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, mk(0))
+    b = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, mk(hd.HD_FLAG_NO_SMALL_ROUNDS))
+    if chunk == 0:  # every item above l + eps splits each round: the same sets on both paths
+        assert (a["lower"], a["upper"], a["status"]) == (b["lower"], b["upper"], b["status"])
+        for key in ("rounds", "splits", "queries", "retired", "peak_frontier"):
+            assert a["stats"][key] == b["stats"][key], key
+    else:  # which 16 items split first depends on the order in the frontier
+        eps = a["stats"]["eps_abs"]
+        for r in (a, b):
+            assert r["status"] == hd.HD_OK and r["upper"] - r["lower"] <= eps * (1 + 1e-12)
+        assert max(a["lower"], b["lower"]) <= min(a["upper"], b["upper"]) + 1e-12
+    assert a["stats"]["kernel_launches"] <= b["stats"]["kernel_launches"]
+    if k == 1:  # its last rounds are small: one launch for them instead of six per round
+        assert a["stats"]["kernel_launches"] < b["stats"]["kernel_launches"]
+    if k != 4:
+        ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+        assert max(a["lower"], ro["lower"]) <= min(a["upper"], ro["upper"]) + 1e-12
+
+
 def test_bracket_all_bound_orders_fp64(hd, orc):
     import itertools
 
