@@ -356,7 +356,7 @@ def run_ours(args):
     leaf = sum(s["leaf_tests"] for s in stats)
     boxes = sum(s["box_tests"] for s in stats)
     evals = sum(s["pointtri_evals"] for s in stats)
-    dom = max(("query", "bound", "select", "build", "prep"), key=lambda k: trace[k]["ms"])
+    dom = max(("query", "bound", "select", "build", "prep", "small_rounds"), key=lambda k: trace[k]["ms"])
     q = trace["query"]
     peaks, src = measured_peaks()
     clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))

@@ -245,8 +245,9 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
  * the number of launches and their total device time in milliseconds.  Each pair costs a
  * few microseconds of host time.  Kinds: the whole BVH build of one hd_build_B call
  * (counted as one launch), the nearest-triangle traversal, UpperBound of faces and
- * children, select/split/compaction, and validation/pool set-up. */
-enum { HD_K_BUILD = 0, HD_K_QUERY = 1, HD_K_BOUND = 2, HD_K_SELECT = 3, HD_K_PREP = 4, HD_K_KINDS = 5 };
+ * children, select/split/compaction, validation/pool set-up, and the single-block kernel
+ * that runs whole rounds over small frontiers. */
+enum { HD_K_BUILD = 0, HD_K_QUERY = 1, HD_K_BOUND = 2, HD_K_SELECT = 3, HD_K_PREP = 4, HD_K_SMALL = 5, HD_K_KINDS = 6 };
 typedef struct {
   int64_t launches[8];
   double ms[8];

@@ -55,8 +55,8 @@ class HdTrace(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
 
 
-HD_K_BUILD, HD_K_QUERY, HD_K_BOUND, HD_K_SELECT, HD_K_PREP = range(5)
-KERNEL_KINDS = ("build", "query", "bound", "select", "prep")
+HD_K_BUILD, HD_K_QUERY, HD_K_BOUND, HD_K_SELECT, HD_K_PREP, HD_K_SMALL = range(6)
+KERNEL_KINDS = ("build", "query", "bound", "select", "prep", "small_rounds")
 
 
 _lib = None

@@ -1190,7 +1190,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   auto issue_tail = [&](int slot) -> int {
     HD_TRY(tail_smem_attr<P>());
     {
-      TraceScope tr(HD_K_SELECT, s);
+      TraceScope tr(HD_K_SMALL, s);
       launch_chained(k_tail_rounds<P>, 1, kTailThreads, kTailSmem, s, B, tb, st, rp, c, init ? 1 : 0, n_pool0, cur);
       init = false;
     }
