@@ -131,6 +131,8 @@ typedef struct {
   int64_t long_queries;      /* queries whose traversal a whole warp finished (part of
                                 queries: those with many BVH boxes within their distance)  */
   int64_t kernel_launches;   /* GPU kernels the call launched                               */
+  int64_t d2h_bytes;         /* bytes the call read back from the device (run-state
+                                snapshots of its rounds)                                    */
 } hd_stats;
 
 typedef struct {

@@ -44,7 +44,7 @@ class HdStats(C.Structure):
                 ("leaf_tests", C.c_int64), ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
                 ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64),
-                ("kernel_launches", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("d2h_bytes", C.c_int64)]
 
 
 class HdResult(C.Structure):
@@ -216,7 +216,8 @@ def _result(r: HdResult) -> dict:
                            box_tests=s.box_tests, discards={BOUND_NAMES[k]: s.discards[k] for k in range(6)},
                            retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
                            pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA,
-                           long_queries=s.long_queries, kernel_launches=s.kernel_launches))
+                           long_queries=s.long_queries, kernel_launches=s.kernel_launches,
+                           d2h_bytes=s.d2h_bytes))
 
 
 def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:

@@ -335,6 +335,7 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
   S.pool_vertices = X.pool_vertices + Y.pool_vertices;
   S.long_queries = X.long_queries + Y.long_queries;
   S.kernel_launches = X.kernel_launches + Y.kernel_launches;
+  S.d2h_bytes = X.d2h_bytes + Y.d2h_bytes;
   S.eps_abs = X.eps_abs;
   S.dA = X.dA;
   return HD_OK;

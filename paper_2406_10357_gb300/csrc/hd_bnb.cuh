@@ -1149,6 +1149,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   auto snapshot = [&](int slot) -> int {
     HD_TRY(cudaMemcpyAsync(&hr.hb->ring[slot], st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+    g_d2h_bytes += sizeof(RunState) + sizeof(DynParams);
     HD_TRY(cudaEventRecord(hr.ev[slot], s));
     return HD_OK;
   };
@@ -1241,6 +1242,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   } else {
     HD_TRY(cudaMemcpyAsync(&hr.hb->st, st, sizeof(RunState), cudaMemcpyDeviceToHost, s));
     HD_TRY(cudaMemcpyAsync(&hr.hb->dyn, rp.dyn, sizeof(DynParams), cudaMemcpyDeviceToHost, s));
+    g_d2h_bytes += sizeof(RunState) + sizeof(DynParams);
     HD_TRY(cudaStreamSynchronize(s));
   }
   const RunState& f = hr.hb->st;
@@ -1353,7 +1355,7 @@ int run_bnb(const RunIO& io) {
   // a block the round kernels cannot launch with (MIXED also runs the FP64 ones)
   if (o.block_size > round_block_limit<P>() || (!P::kFp64 && o.block_size > round_block_limit<PolicyD>()))
     return HD_ERR_INVALID;
-  const long long launches0 = g_launches;
+  const long long launches0 = g_launches, d2h0 = g_d2h_bytes;
 
   HostRes* hr = nullptr;
   {
@@ -1461,6 +1463,7 @@ int run_bnb(const RunIO& io) {
   S.queries = (int64_t)hst->queries;
   S.long_queries = (int64_t)hst->long_queries;
   S.kernel_launches = g_launches - launches0;
+  S.d2h_bytes = g_d2h_bytes - d2h0;
   S.pointtri_evals = (int64_t)hst->evals;
   S.leaf_tests = (int64_t)hst->leaf_tests;
   S.box_tests = (int64_t)hst->box_tests;

@@ -201,8 +201,10 @@ struct Counters {
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
-// Kernels this host thread has launched through launch_chained (the library's own count).
+// Kernels this host thread has launched through launch_chained, and bytes it has read back
+// from the device in runs (the library's own counts).
 inline thread_local long long g_launches = 0;
+inline thread_local long long g_d2h_bytes = 0;
 
 // Launches kernel<<<grid, block, smem, s>>>(args...) chained to the kernel before it in the
 // stream (see grid_dep_wait).  Errors are left for cudaGetLastError (HD_TRY_LAUNCH).

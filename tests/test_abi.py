@@ -48,8 +48,8 @@ def test_struct_layouts_match_header(hd):
     # sizes of the ABI structs as laid out by a C compiler for this header
     assert C.sizeof(hd.HdMesh) == 40
     assert C.sizeof(hd.HdOptions) == 64
-    assert C.sizeof(hd.HdStats) == 8 * 20
-    assert C.sizeof(hd.HdResult) == 24 + 8 * 20
+    assert C.sizeof(hd.HdStats) == 8 * 21
+    assert C.sizeof(hd.HdResult) == 24 + 8 * 21
     assert C.sizeof(hd.HdTrace) == 128
 
 
