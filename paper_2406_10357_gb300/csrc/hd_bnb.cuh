@@ -29,6 +29,15 @@
 #include "hd_fp64.cuh"
 #include "hd_internal.cuh"
 
+// Register caps of the lane traversal and of the UpperBound kernels (a few values spill to
+// L1; more resident warps pay for it in these latency-bound kernels).
+#ifndef HD_QUERY_REGS
+#define HD_QUERY_REGS __maxnreg__(128)
+#endif
+#ifndef HD_BOUND_REGS
+#define HD_BOUND_REGS __maxnreg__(96)
+#endif
+
 namespace hd {
 
 __device__ inline unsigned long long warp_sum(unsigned long long v) {
@@ -256,7 +265,7 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
 }
 
 template <class P>
-__global__ void __maxnreg__(128) k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
+__global__ void HD_QUERY_REGS k_query(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
                         RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
                         LongList ll) {
   grid_dep_wait();
@@ -422,7 +431,7 @@ __device__ inline Level<P> block_level(const RunState* st, double eps) {
 
 // Round 0: UpperBound for every face of A.
 template <class P>
-__global__ void k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
+__global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
                               RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list,
                               int64_t n_pool_valid) {
   grid_dep_wait();
@@ -675,7 +684,7 @@ __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool
 }
 
 template <class P>
-__global__ void k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
+__global__ void HD_BOUND_REGS k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
                                  const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
   grid_dep_wait();
   grid_dep_launch();
