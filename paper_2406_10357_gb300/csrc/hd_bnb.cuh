@@ -29,16 +29,23 @@
 #include "hd_fp64.cuh"
 #include "hd_internal.cuh"
 
-// Register caps of the lane traversal and of the UpperBound kernels (a few values spill to
-// L1; more resident warps pay for it in these latency-bound kernels).
+// Register caps of the lane traversal and of the UpperBound kernels (the policy's
+// kBoundRegs): more resident warps pay for a few values spilled to L1 in these latency-bound
+// kernels.
 #ifndef HD_QUERY_REGS
 #define HD_QUERY_REGS __maxnreg__(128)
 #endif
 #ifndef HD_BOUND_REGS
-#define HD_BOUND_REGS __maxnreg__(96)
+#define HD_BOUND_REGS __maxnreg__((bound_regs<P, kPaper>()))
 #endif
 
 namespace hd {
+
+template <class P, bool kPaper>
+constexpr int bound_regs() {
+  if constexpr (kPaper) return P::kPaperRegs;
+  else return P::kBoundRegs;
+}
 
 __device__ inline unsigned long long warp_sum(unsigned long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -429,8 +436,19 @@ __device__ inline Level<P> block_level(const RunState* st, double eps) {
   return Level<P>{s_l, s_lf, Thresholds<P>(typename Thresholds<P>::Raw{}, s_lo, s_hi)};
 }
 
+// UpperBound of one sub-triangle: the cascade in the paper's order with u4 deferred
+// (kPaper, straight-line code, MIXED only), or in any order rp gives.
+template <class P, bool kPaper>
+__device__ inline typename P::UT bound_item(const BvhDev& B, const typename P::Vtx* pool, const typename P::Item& it,
+                                            const Level<P>& lv, const RunParams& rp, int& code, Counters& c) {
+  if constexpr (kPaper)
+    return P::upper_bound_paper(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
+  else
+    return P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
+}
+
 // Round 0: UpperBound for every face of A.
-template <class P>
+template <class P, bool kPaper = false>
 __global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
                               RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list,
                               int64_t n_pool_valid) {
@@ -455,7 +473,7 @@ __global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* poo
           it.v[2] < n_pool_valid))
       continue;
     int code;
-    it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
+    it.U = bound_item<P, kPaper>(B, pool, it, lv, rp, code, c);
     classify<P>(st, it, th, code, next, next_cap, u4list, ty);
   }
   flush_counters(st, c);
@@ -646,7 +664,7 @@ __global__ void k_select(const typename P::Item* front, RunState* st, RunParams 
 
 // The four children of every split (Section 4, midpoint subdivision):
 // (v1, m12, m31), (m12, v2, m23), (m31, m23, v3), (m12, m23, m31).
-template <class P>
+template <class P, bool kPaper = false>
 __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
                                  const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
   if (st->stop) return;  // the loop ended before this round (uniform over the grid)
@@ -672,7 +690,7 @@ __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool
       else if (k == 2) { it.v[0] = m31; it.v[1] = m23; it.v[2] = par.z; }
       else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
       int code;
-      it.U = P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
+      it.U = bound_item<P, kPaper>(B, pool, it, lv, rp, code, c);
       // the child lies inside its parent: h(child, B) <= U(parent)
       const typename P::UT Up = (typename P::UT)__int_as_float(par.w);
       if (rp.parent_clamp && Up < it.U) it.U = Up;
@@ -683,12 +701,31 @@ __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool
   flush_tally(st, ty);
 }
 
-template <class P>
+template <class P, bool kPaper = false>
 __global__ void HD_BOUND_REGS k_bound_children(BvhDev B, const typename P::Vtx* pool, const int4* split_par,
                                  const int4* split_mid, RunState* st, RunParams rp_in, typename P::Item* next, int next_cap, typename P::Item* u4list) {
   grid_dep_wait();
   grid_dep_launch();
-  bound_children_body<P>(B, pool, split_par, split_mid, st, rp_in, next, next_cap, u4list);
+  bound_children_body<P, kPaper>(B, pool, split_par, split_mid, st, rp_in, next, next_cap, u4list);
+}
+
+// Whether the options ask for the paper's cascade (u1, u2, u3, u4) with u4 left to the u4
+// pass: then the UpperBound kernels run their straight-line instantiation (kPaper), which
+// keeps fewer values live than the loop over rp.order and so needs no spills at its
+// register cap.
+inline bool paper_cascade(const RunParams& rp) {
+  return rp.defer_u4 && rp.n_bounds == 4 && rp.order[0] == 1 && rp.order[1] == 2 && rp.order[2] == 3 &&
+         rp.order[3] == 4;
+}
+template <class P>
+auto bound_faces_kernel(bool paper) {
+  if constexpr (P::kFp64) return k_bound_faces<P, false>;
+  else return paper ? k_bound_faces<P, true> : k_bound_faces<P, false>;
+}
+template <class P>
+auto bound_children_kernel(bool paper) {
+  if constexpr (P::kFp64) return k_bound_children<P, false>;
+  else return paper ? k_bound_children<P, true> : k_bound_children<P, false>;
 }
 
 // Per-loop constants of the round control.
@@ -957,8 +994,11 @@ int round_block_limit() {
     m = 1024;
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, k_query<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
-    if (cudaFuncGetAttributes(&fa, k_bound_faces<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
-    if (cudaFuncGetAttributes(&fa, k_bound_children<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+    for (bool paper : {false, true}) {
+      if (cudaFuncGetAttributes(&fa, bound_faces_kernel<P>(paper)) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
+      if (cudaFuncGetAttributes(&fa, bound_children_kernel<P>(paper)) == cudaSuccess)
+        m = std::min(m, fa.maxThreadsPerBlock);
+    }
     if (cudaFuncGetAttributes(&fa, k_bound_u4<P>) == cudaSuccess) m = std::min(m, fa.maxThreadsPerBlock);
     m &= ~31;
     cached.store(m, std::memory_order_relaxed);
@@ -1148,8 +1188,10 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   c.splits_left = (long long)std::max(0.0, std::min(cap_splits - (double)T.splits, 9.0e18));
   c.rounds_left = std::max<long long>(0, o.max_rounds - T.rounds);
   c.bad = bad;
-  static std::atomic<unsigned> grid_b_cache[33];
-  const unsigned grid_q = query_grid<P>(bs), grid_b = persistent_grid_bs(k_bound_children<P>, bs, grid_b_cache);
+  static std::atomic<unsigned> grid_b_cache[2][33];
+  const bool paper = paper_cascade(rp);
+  const auto k_children = bound_children_kernel<P>(paper);
+  const unsigned grid_q = query_grid<P>(bs), grid_b = persistent_grid_bs(k_children, bs, grid_b_cache[paper ? 1 : 0]);
   const unsigned grid_long = long_grid<P>();
   int64_t front_bound = first_front_bound;  // the first round is queued without a wait
   int cur = R.cur;
@@ -1183,8 +1225,8 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      launch_chained(k_bound_children<P>, g_b, bs, 0, s, B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1], (int)R.front_cap,
-                                             R.u4list);
+      launch_chained(k_children, g_b, bs, 0, s, B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1],
+                     (int)R.front_cap, R.u4list);
       if (R.u4list)
         launch_chained(k_bound_u4<P>, g_u4, bs, 0, s, B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
                                           (int)R.front_cap);
@@ -1425,7 +1467,8 @@ int run_bnb(const RunIO& io) {
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_BOUND, s);
-    launch_chained(k_bound_faces<P>, std::min(blocks_for(io.nFA, bs), persistent_grid(k_bound_faces<P>, bs, sms)), bs, 0, s, 
+    const auto k_faces = bound_faces_kernel<P>(paper_cascade(rp));
+    launch_chained(k_faces, std::min(blocks_for(io.nFA, bs), persistent_grid(k_faces, bs, sms)), bs, 0, s, 
         B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
                                                            (int)R.front_cap, R.u4list, io.nVA);
     if (R.u4list)

@@ -328,11 +328,16 @@ __device__ inline double upper_bound_d(const BvhDev& B, const VI t[3], double l,
 
 // ----------------------------------------------------------------------------- the policy
 
+#ifndef HD_FP64_BOUND_REGS
+#define HD_FP64_BOUND_REGS 128
+#endif
+
 struct PolicyD {
   using Vtx = VtxD;
   using Item = ItemD;
   using UT = double;
   static constexpr bool kFp64 = true;
+  static constexpr int kBoundRegs = HD_FP64_BOUND_REGS;  // register cap of the UpperBound kernels
 
   // Nearest triangle of v.  With `over` given, a traversal that tests more than `budget`
   // triangles stops, sets *over and leaves its best triangle so far in v (hint, d = its

@@ -706,13 +706,58 @@ __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], float lf, 
   return __fadd_ru(U, rp.slack_f);
 }
 
+// The cascade in the paper's order (u1, u2, u3, then u4, which the u4 pass evaluates) as
+// straight-line code: the same values and result codes as upper_bound_m's loop over
+// rp.order, but the edges are dead once u2 is known and the footpoints are not needed at all,
+// so that fewer values are live across u3, the heaviest bound.
+__device__ inline float upper_bound_m_paper(const BvhDev& B, const VM t[3], float lf, const RunParams& rp, int& code,
+                                            Counters& c) {
+  float U;
+  if (t[0].I == t[1].I && t[1].I == t[2].I) {
+    code = 0;
+    U = fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi));
+  } else {
+    const EdgesM E(t);
+    const float u1 = ubm_u1(t, E);
+    if (u1 < lf) {
+      code = 1;
+      U = u1;
+    } else {
+      const float u2 = ubm_u2(t, E);
+      if (u2 < lf) {
+        code = 2;
+        U = u2;
+      } else {
+        const float u3 = ubm_u3(B, t, lf, c.evals);
+        if (u3 < lf) {
+          code = 3;
+          U = u3;
+        } else {
+          code = kDeferU4;
+          U = fminf(fminf(u1, u2), u3);
+        }
+      }
+    }
+  }
+  return __fadd_ru(U, rp.slack_f);
+}
+
 // ----------------------------------------------------------------------------- the policy
+
+#ifndef HD_MIXED_BOUND_REGS
+#define HD_MIXED_BOUND_REGS 96
+#endif
+#ifndef HD_MIXED_PAPER_REGS
+#define HD_MIXED_PAPER_REGS 96
+#endif
 
 struct PolicyM {
   using Vtx = VtxM;
   using Item = ItemM;
   using UT = float;
   static constexpr bool kFp64 = false;
+  static constexpr int kBoundRegs = HD_MIXED_BOUND_REGS;  // register cap of the UpperBound kernels
+  static constexpr int kPaperRegs = HD_MIXED_PAPER_REGS;  // ... of their paper-order instantiation
 
   // 2^-40 of the largest coordinate: covers the float-pair representation of subdivided
   // vertices (2^-48 relative per level, at most 60 levels) and the double rounding of u4
@@ -843,6 +888,15 @@ struct PolicyM {
     m.tri = -2;
     m.hint = a.tri;
     m.pad0 = m.pad1 = 0.f;
+  }
+  // upper_bound for the paper's cascade order with u4 deferred (only valid for those
+  // options; the kernels pick it on the host): u4 comes later, so the footpoints are not read
+  __device__ static UT upper_bound_paper(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double,
+                                         float lf, const RunParams& rp, int& code, Counters& cnt) {
+    const VM t[3] = {{pos(a), a.dhi, a.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(b), b.dhi, b.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(c), c.dhi, c.tri, {0.f, 0.f, 0.f}, 0.f}};
+    return upper_bound_m_paper(B, t, lf, rp, code, cnt);
   }
   __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double,
                                    float lf, const RunParams& rp, int& code, Counters& cnt) {
