@@ -238,7 +238,10 @@ int hd_nearest_noalloc(const hd_bvh* B, const void* P, int32_t ptype, int64_t n,
  * T (device, n x 9 doubles: v1, v2, v3), Td (n x 3), TI (n x 3 int32), Tq (n x 9),
  * all device memory.  Writes U (n doubles) and code (n int32: 0 exact case,
  * 1..4 the bound that discarded T (U < l), 5 kept: U = min of the computed bounds).
- * FP64 arithmetic.  Asynchronous on `stream`. */
+ * opt->precision HD_FP64 (the default): FP64 arithmetic.  HD_MIXED: the certified FP32
+ * arithmetic of the rounds (each vertex as a float pair, its distance rounded up, its closest
+ * point as a float offset with the offset's rounding as error radius; u4 evaluated in place),
+ * so U bounds h(T, B) from above whenever Td and Tq are exact.  Asynchronous on `stream`. */
 int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const int32_t* TI, const double* Tq,
                     int64_t n, double l, const hd_options* opt, void* stream, double* U, int32_t* code);
 

@@ -320,7 +320,8 @@ def hd_nearest_noalloc(bvh: Bvh, P, precision: int = HD_FP64, out=None, stream=N
 
 
 def hd_upper_bounds(bvh: Bvh, T, Td, TI, Tq, l: float, opt: HdOptions | None = None, stream=None):
-    """UpperBound(T, l) in FP64 for n triangles (CUDA tensors): returns (U, code)."""
+    """UpperBound(T, l) for n triangles (CUDA tensors): returns (U, code).  FP64 by default;
+    with ``opt.precision = HD_MIXED`` the certified FP32 arithmetic of the rounds."""
     import torch
 
     T, Td, Tq = (x.to(torch.float64).contiguous() for x in (T, Td, Tq))

@@ -142,6 +142,8 @@ int nearest_points_fp64(const hd_bvh* B, const void* Pts, int ptype, int64_t n, 
 }
 int nearest_points_mixed(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                          int32_t* idx, double* foot, double* dlo);
+int upper_bounds_mixed(const hd_bvh* B, const double* T, const double* Td, const int32_t* TI, const double* Tq,
+                       int64_t n, double l, const RunParams& rp, cudaStream_t s, double* U, int32_t* code);
 
 __global__ void k_upper_bounds(BvhDev B, const int* inv, const double* T, const double* Td, const int32_t* TI,
                                const double* Tq, int64_t n, double l, RunParams rp, double* U, int32_t* code) {
@@ -438,6 +440,7 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
   memcpy(rp.order, o.order, 4);
   rp.n_bounds = o.n_bounds;
   cudaStream_t s = (cudaStream_t)stream;
+  if (o.precision == HD_MIXED) return upper_bounds_mixed(B, T, Td, TI, Tq, n, l, rp, s, U, code);
   k_upper_bounds<<<blocks_for(n, 128), 128, 0, s>>>(bvh_dev(B), B->inv, T, Td, TI, Tq, n, l, rp, U, code);
   HD_TRY_LAUNCH();
   return HD_OK;

@@ -613,61 +613,133 @@ __device__ inline float ubm_u3(const BvhDev& B, const VM t[3], float l, unsigned
   return fminf(ut, best);
 }
 
-// u4, Eq. (bound_u4), in FP64 on the float-pair vertices and footpoints, plus the footpoint
-// error radii and a relative margin for the double rounding.
-__device__ inline float ubm_u4(const VM t[3], double slack) {
-  VI d[3];
-  float qe = 0.f;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    D3 v = {(double)t[i].p.h.x + (double)t[i].p.l.x, (double)t[i].p.h.y + (double)t[i].p.l.y,
-            (double)t[i].p.h.z + (double)t[i].p.l.z};
-    d[i].v = v;
-    d[i].q = v + D3{(double)t[i].q.x, (double)t[i].q.y, (double)t[i].q.z};
-    d[i].d = 0.0;
-    d[i].I = t[i].I;
-    qe = fmaxf(qe, t[i].qerr);
-  }
-  double u = ub_u4(d);
-  return __fadd_ru(__double2float_ru(u + 2.0 * slack + 1e-12 * u), qe);
-}
+// ---- u4 in certified FP32.  Differences of vertices and footpoints are formed as float pairs
+// (h + l) with error-free sums: each such difference is within T = 64u (L + uM) of the exact
+// one per component, where L bounds the vertices' low parts and M every coordinate involved
+// (u = 2^-24; each pair operation adds at most 2u times the low parts it combines, which grow
+// to a few L + uM along the chain).  Only the final dot products and norms round, and each is
+// raised by a bound on its error.
 
-// Plain FP32 value of Eq. (bound_u4), without rounding control, in coordinates relative to
-// the first vertex.  It only decides whether the certified FP64 evaluation can pay off (see
-// PolicyM::bound_u4): a wrong estimate costs tightness, never validity.
-__device__ inline float u4_h2_estimate(const F3 X[3], F3 a, F3 b) {
-  float h2 = 0.f;
+// a + b as s + e exactly (Knuth's two-sum; intrinsics, so that nothing is contracted or
+// reassociated).
+__device__ inline void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ inline FFP pair_sub(const FFP& a, const FFP& b) {
+  FFP r;
+  two_sum(a.h.x, -b.h.x, r.h.x, r.l.x);
+  two_sum(a.h.y, -b.h.y, r.h.y, r.l.y);
+  two_sum(a.h.z, -b.h.z, r.h.z, r.l.z);
+  r.l = {__fadd_rn(r.l.x, __fsub_rn(a.l.x, b.l.x)), __fadd_rn(r.l.y, __fsub_rn(a.l.y, b.l.y)),
+         __fadd_rn(r.l.z, __fsub_rn(a.l.z, b.l.z))};
+  return r;
+}
+__device__ inline FFP pair_add(const FFP& a, const FFP& b) {
+  FFP r;
+  two_sum(a.h.x, b.h.x, r.h.x, r.l.x);
+  two_sum(a.h.y, b.h.y, r.h.y, r.l.y);
+  two_sum(a.h.z, b.h.z, r.h.z, r.l.z);
+  r.l = {__fadd_rn(r.l.x, __fadd_rn(a.l.x, b.l.x)), __fadd_rn(r.l.y, __fadd_rn(a.l.y, b.l.y)),
+         __fadd_rn(r.l.z, __fadd_rn(a.l.z, b.l.z))};
+  return r;
+}
+__device__ inline F3 pair_f(const FFP& a) {  // h + l rounded: within u |h + l| per component
+  return {__fadd_rn(a.h.x, a.l.x), __fadd_rn(a.h.y, a.l.y), __fadd_rn(a.h.z, a.l.z)};
+}
+__device__ inline float sum1(F3 a) { return __fadd_ru(__fadd_ru(fabsf(a.x), fabsf(a.y)), fabsf(a.z)); }
+
+// Upper bound of the length of the exact vector whose float-pair form rounds to d: each
+// component of d is within u |d_c| + 3T of it (two differences of pairs and one more pair
+// operation), so the exact length is at most |d| (1 + u) + 6T; tiny >= 12T covers it.
+__device__ inline float len_cert(F3 d, float tiny) { return __fadd_ru(__fmul_ru(norm_ru(d), 1.f + 4.f * kU), tiny); }
+
+// H(a, b) of Eq. (bound_u4), the largest distance from a point of T to the nearer of a and b,
+// certified.  It is attained at a vertex of T or where an edge crosses the bisector plane of a
+// and b.  X are T's vertices and a, b the footpoints, as float pairs relative to T's first
+// vertex.  For an edge x0 x1 with c_j = n . (x_j - mid) (n = b - a, mid = (a + b) / 2),
+// computed as dot products of rounded vectors with |error| <= E_j = 8u |n|_1 |w_j|_1 +
+// 4T (|n|_1 + |w_j|_1), the edge is skipped only when both c_j lie beyond E_j on the same
+// side (it certainly does not cross).  Otherwise its term is the distance from a to the
+// farther endpoint (|x - a| is convex along the edge, so this bounds the crossing's distance
+// wherever it is) or, when |c0 - c1| > 4 (E0 + E1), the smaller of that and the distance at
+// the computed crossing x0 + tau (x1 - x0) plus tau's error, (2 E0 + E1) / |c0 - c1| + 3u,
+// times the edge length.  Every term bounds its exact counterpart from above, and extra terms
+// only raise the maximum, so the result bounds H(a, b).
+__device__ inline float u4_h_cert(const FFP X[3], const FFP& a, const FFP& b, float T) {
+  const float tiny = __fmul_ru(16.f, T);
+  F3 dA[3];
+  float h = 0.f;
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    F3 ea = X[i] - a, eb = X[i] - b;
-    h2 = fmaxf(h2, fminf(dotf(ea, ea), dotf(eb, eb)));
+    dA[i] = pair_f(pair_sub(X[i], a));
+    const F3 db = pair_f(pair_sub(X[i], b));
+    h = fmaxf(h, fminf(len_cert(dA[i], tiny), len_cert(db, tiny)));
   }
-  F3 n = b - a;
-  F3 mid = {0.5f * (a.x + b.x), 0.5f * (a.y + b.y), 0.5f * (a.z + b.z)};
+  const F3 n = pair_f(pair_sub(b, a));
+  FFP mid = pair_add(a, b);
+  mid.h = {0.5f * mid.h.x, 0.5f * mid.h.y, 0.5f * mid.h.z};
+  mid.l = {0.5f * mid.l.x, 0.5f * mid.l.y, 0.5f * mid.l.z};
+  const float n1 = sum1(n), m2 = __fmul_ru(4.f, T);
+  float c[3], E[3];
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    F3 x0 = X[i], x1 = X[(i + 1) % 3];
-    float c0 = dotf(n, x0 - mid), c1 = dotf(n, x1 - mid);
-    if (((c0 <= 0.f && c1 >= 0.f) || (c0 >= 0.f && c1 <= 0.f)) && c0 != c1) {
-      float tau = __fdividef(c0, c0 - c1);
-      F3 x = {fmaf(tau, x1.x - x0.x, x0.x), fmaf(tau, x1.y - x0.y, x0.y), fmaf(tau, x1.z - x0.z, x0.z)};
-      F3 ea = x - a, eb = x - b;
-      h2 = fmaxf(h2, fminf(dotf(ea, ea), dotf(eb, eb)));
+    const F3 w = pair_f(pair_sub(X[i], mid));
+    const float w1 = sum1(w);
+    c[i] = dotf(n, w);
+    E[i] = __fadd_ru(__fmul_ru(__fmul_ru(8.f * kU, n1), w1), __fmul_ru(m2, __fadd_ru(n1, w1)));
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int k = (i + 1) % 3;
+    const float c0 = c[i], c1 = c[k], E0 = E[i], E1 = E[k];
+    if ((c0 > E0 && c1 > E1) || (c0 < -E0 && c1 < -E1)) continue;
+    float term = fmaxf(len_cert(dA[i], tiny), len_cert(dA[k], tiny));
+    const float D = fabsf(__fsub_rn(c0, c1));
+    if (D > __fmul_ru(4.f, __fadd_ru(E0, E1))) {
+      const float tau = __saturatef(__fdiv_rn(c0, __fsub_rn(c0, c1)));
+      const F3 e = pair_f(pair_sub(X[k], X[i]));
+      // x - a = (x0 - a) + tau e, each component within u (|x0 - a| + |e| + |x - a|) + 6T
+      const F3 r = {fmaf(tau, e.x, dA[i].x), fmaf(tau, e.y, dA[i].y), fmaf(tau, e.z, dA[i].z)};
+      const float slop = __fadd_ru(__fmul_ru(2.f * kU, __fadd_ru(__fadd_ru(amax3(dA[i]), amax3(e)), amax3(r))), tiny);
+      const float errt = __fadd_ru(__fdiv_ru(__fadd_ru(__fmul_ru(2.f, E0), E1), D), 3.f * kU);
+      const float at = __fadd_ru(__fadd_ru(norm_ru(r), slop), __fmul_ru(errt, len_cert(e, tiny)));
+      term = fminf(term, at);
     }
+    h = fmaxf(h, term);
   }
-  return h2;
+  return h;
 }
 
-__device__ inline float u4_estimate(const VM t[3]) {
-  const F3 X[3] = {{0.f, 0.f, 0.f}, edge(t[0], t[1]), edge(t[0], t[2])};
-  const F3 Q[3] = {t[0].q, X[1] + t[1].q, X[2] + t[2].q};
-  F3 e0 = X[0] - X[1], e1 = X[1] - X[2], e2 = X[2] - X[0];
-  float l0 = dotf(e0, e0), l1 = dotf(e1, e1), l2 = dotf(e2, e2);
-  // shortest edge v1v2 with footpoints q1 (the opposite vertex's), q2, q3 as in ub_u4
-  F3 q2 = Q[0], q3 = Q[1], q1 = Q[2];
+// u4, Eq. (bound_u4), certified in FP32: the footpoints q1 of the vertex opposite T's shortest
+// edge and q2, q3 of its ends, u4 = min(H(q1, q2), H(q1, q3)), plus the footpoints' error
+// radii (the points of B they stand for are within qerr) and twice the vertices'
+// representation error.
+__device__ inline float ubm_u4(const VM t[3], float slack_f) {
+  const FFP zero = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  const FFP X[3] = {zero, pair_sub(t[1].p, t[0].p), pair_sub(t[2].p, t[0].p)};
+  FFP Q[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Q[i] = pair_add(X[i], FFP{t[i].q, {0.f, 0.f, 0.f}});
+  float M = 0.f, L = 0.f;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    M = fmaxf(M, fmaxf(amax3(X[i].h), amax3(Q[i].h)));
+    L = fmaxf(L, amax3(t[i].p.l));
+  }
+  M = __fmul_ru(M, 2.f);  // also bounds midpoints and differences of two of these
+  const float T = __fmul_ru(64.f * kU, __fadd_ru(L, __fmul_ru(kU, M)));
+  const F3 x1 = pair_f(X[1]), x2 = pair_f(X[2]), e12 = x2 - x1;
+  const float l0 = dotf(x1, x1), l1 = dotf(e12, e12), l2 = dotf(x2, x2);
+  // shortest edge v1v2 with footpoints q1 (the opposite vertex's), q2, q3 (any choice is
+  // valid; this one is the paper's)
+  FFP q2 = Q[0], q3 = Q[1], q1 = Q[2];
   if (l1 < l0 && l1 <= l2) { q2 = Q[1]; q3 = Q[2]; q1 = Q[0]; }
   else if (l2 < l0 && l2 < l1) { q2 = Q[2]; q3 = Q[0]; q1 = Q[1]; }
-  return sqrtf(fminf(u4_h2_estimate(X, q1, q2), u4_h2_estimate(X, q1, q3)));
+  const float h = fminf(u4_h_cert(X, q1, q2, T), u4_h_cert(X, q1, q3, T));
+  const float qe = fmaxf(t[0].qerr, fmaxf(t[1].qerr, t[2].qerr));
+  return __fadd_ru(__fadd_ru(h, qe), __fmul_ru(2.f, slack_f));
 }
 
 // lf is l rounded down to float: comparisons against it in float are safe, u < lf => u < l
@@ -693,7 +765,7 @@ __device__ inline float upper_bound_m(const BvhDev& B, const VM t[3], float lf, 
         case 1: u = ubm_u1(t, E); break;
         case 2: u = ubm_u2(t, E); break;
         case 3: u = ubm_u3(B, t, lf, c.evals); break;
-        default: u = ubm_u4(t, rp.slack); break;
+        default: u = ubm_u4(t, rp.slack_f); break;
       }
       U = fminf(U, u);
       if (u < lf) {
@@ -763,16 +835,13 @@ struct PolicyM {
   // vertices (2^-48 relative per level, at most 60 levels) and the double rounding of u4
   static double slack(double amax) { return ldexp(amax, -40); }
   __device__ static float ut_down(double x) { return __double2float_rd(x); }
-  // the u4 pass: Eq. (bound_u4) for one item, plus the slack, for an item whose bound so far
-  // is U (not below l).  The certified value is evaluated in FP64 (slow on GB300) only when
-  // the FP32 estimate says it may lower U or discard the item; otherwise +inf (no change).
-  __device__ static float bound_u4(const Vtx& a, const Vtx& b, const Vtx& c, const RunParams& rp, float U) {
-    VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
-               {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
-               {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
-    const float est = u4_estimate(t);
-    if (!(est * (1.f - 1e-3f) < U)) return INFINITY;
-    return __fadd_ru(ubm_u4(t, rp.slack), rp.slack_f);
+  // the u4 pass: Eq. (bound_u4) for one item (certified FP32), plus the slack.  The item's
+  // bound so far (the last argument) is not needed.
+  __device__ static float bound_u4(const Vtx& a, const Vtx& b, const Vtx& c, const RunParams& rp, float) {
+    const VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
+                     {pos(b), b.dhi, b.tri, {b.qx, b.qy, b.qz}, b.qerr},
+                     {pos(c), c.dhi, c.tri, {c.qx, c.qy, c.qz}, c.qerr}};
+    return __fadd_ru(ubm_u4(t, rp.slack_f), rp.slack_f);
   }
 
   __device__ static FFP pos(const Vtx& v) { return {{v.hx, v.hy, v.hz}, {v.lx, v.ly, v.lz}}; }

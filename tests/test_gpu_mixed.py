@@ -160,6 +160,23 @@ def test_bracket_mixed_vs_oracle(hd, orc, k, scale):
     assert max(r["lower"], r64["lower"]) <= min(r["upper"], r64["upper"]) + ORACLE_REL * r64["upper"]
 
 
+@pytest.mark.parametrize("order", [(4,), (1, 4), (4, 3), (1, 2, 3, 4)])
+@pytest.mark.parametrize("k,scale", [(1, 1.0), (2, 0.02)])
+def test_bracket_mixed_bound_orders(hd, orc, order, k, scale):
+    """MIXED runs whose cascades lean on u4 (alone, first, or last as in the paper): the
+    bracket intersects the oracle's, so every discard u4 made was valid."""
+    p = mg.workload(k, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    o = hd.hd_options_default(tol_mode=p.tol_mode, precision=hd.HD_MIXED, bound_order=order, max_face_factor=2000)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, o)
+    ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, p.tol_mode)
+    assert r["status"] in (hd.HD_OK, hd.HD_ERR_CAPACITY), (order, r)
+    assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + ORACLE_REL * ro["upper"], order
+    if r["status"] == hd.HD_OK:
+        eps = p.tol * (_dA(p.VA, p.FA) if p.tol_mode else 1.0)
+        assert r["upper"] - r["lower"] <= eps
+
+
 def test_full_size_workload2_mixed_properties(hd, orc):
     p = mg.workload(2)
     bvh = hd.hd_build_B(p.VB, p.FB)
@@ -179,3 +196,65 @@ def test_identical_meshes_mixed(hd):
     bvh = hd.hd_build_B(V, F)
     r = hd.hd_hausdorff(bvh, V, F, 1e-3, hd.hd_options_default(precision=hd.HD_MIXED))
     assert r["status"] == hd.HD_OK and 0 <= r["lower"] <= 1e-6 and r["upper"] <= 1e-3 + 1e-6
+
+
+def _bary_grid(k):
+    """Barycentric weights of a regular grid with k steps per edge (vertices included)."""
+    return np.array([(i / k, j / k, (k - i - j) / k) for i in range(k + 1) for j in range(k + 1 - i)])
+
+
+@pytest.mark.parametrize("order", [(1, 2, 3, 4), (1,), (2,), (3,), (4,)])
+def test_upper_bounds_mixed_certified(hd, orc, order):
+    """UpperBound(T, l) in the certified FP32 arithmetic (hd_upper_bounds with HD_MIXED), each
+    bound alone and the paper's cascade, for random sub-triangles of A's faces with the
+    oracle's nearest data.  Validity: every value is at least max d(p, B) over a dense sample of
+    T, since d(p, B) <= h(T, B) <= any of the paper's bounds.  Tightness: for a single bound the
+    value is within a few float roundings of the local magnitude of the oracle's FP64 value of
+    the same bound (u3's split points are computed in plain FP32 and may differ slightly, which
+    moves it either way)."""
+    # the re-triangulated torus pair (reduced): B's triangles do not follow A's, so the three
+    # vertices of a sub-triangle usually have different nearest triangles (not the exact case)
+    p = mg.workload(2, 0.02)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    rng = np.random.default_rng(11)
+    V = np.asarray(p.VA, float)
+    n = 400
+    f = rng.integers(0, len(p.FA), n)
+    W = rng.dirichlet([1, 1, 1], size=(n, 3))
+    s = rng.choice([3.0, 2.0, 1.0, 0.3], size=n)[:, None, None]  # above 1: past the face (any T is valid)
+    c = rng.dirichlet([1, 1, 1], size=n)[:, None, :]
+    T = np.einsum("nkj,njd->nkd", c + s * (W - c), V[p.FA[f]])
+    d, I, q = orc.nearest(T.reshape(-1, 3), p.VB, p.FB)
+    d, I, q = d.reshape(n, 3), I.reshape(n, 3), q.reshape(n, 3, 3)
+    assert np.sum((I[:, 0] != I[:, 1]) | (I[:, 1] != I[:, 2])) >= n // 4
+    l0 = float(np.quantile(d, 0.8))
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    opt = hd.hd_options_default(precision=hd.HD_MIXED, bound_order=order)
+    U, code = hd.hd_upper_bounds(bvh, t(T.reshape(n, 9)), t(d), t(I.astype(np.int32)), t(q.reshape(n, 9)), l0, opt)
+    U, code = U.cpu().numpy(), code.cpu().numpy()
+    assert np.all(np.isfinite(U)) and np.all((code >= 0) & (code <= 5))
+    G = _bary_grid(12)
+    S = np.einsum("gk,nkd->ngd", G, T)
+    ds, _, _ = orc.nearest(S.reshape(-1, 3), p.VB, p.FB)
+    smax = ds.reshape(n, len(G)).max(1)
+    assert np.all(U >= smax - 1e-12 * np.maximum(1.0, smax)), np.min(U - smax)
+    if len(order) == 1:
+        k = order[0]
+        M = np.abs(T - T[:, :1]).max((1, 2)) + np.abs(q - T).max((1, 2)) + d.max(1)
+        sel = np.nonzero(code != 0)[0]
+        assert len(sel) >= n // 4
+        ref = np.array([orc.bounds_all(T[i], d[i], I[i], q[i], p.VB, p.FB)[k] for i in sel])
+        rel = (U[sel] - ref) / M[sel]
+        if k != 3:
+            # certified: never below the exact value of the same bound
+            assert np.all(U[sel] >= ref - 1e-12 * np.maximum(1.0, ref)), (k, np.min(U[sel] - ref))
+            # tight: almost always within a few hundred float roundings (an edge nearly parallel
+            # to u4's bisector plane may fall back to the edge's farther endpoint)
+            assert np.quantile(rel, 0.99) <= 2000 * 2.0**-24, (k, np.quantile(rel, 0.99))
+        else:
+            # u3 of kept items (a discarded item stops at min_i h(T, S_i) once that is below l,
+            # where the oracle goes on to min(u3~, ...)); its case-1 split points are computed in
+            # plain FP32, so near the fallback to midpoints the two may take different points
+            kept = code[sel] == 5
+            assert kept.sum() >= 20
+            assert np.quantile(np.abs(rel[kept]), 0.95) <= 1e-3, np.quantile(np.abs(rel[kept]), 0.95)
