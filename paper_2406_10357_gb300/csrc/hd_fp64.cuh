@@ -165,13 +165,10 @@ __device__ inline double ub_u2(const VI t[3]) {
 __device__ inline bool shared_edge(const BvhDev& B, int f, int g, int& fs0, int& fs1, int& fo, int& go) {
   int4 a = __ldg(B.tri_vid + f), b = __ldg(B.tri_vid + g);
   int av[3] = {a.x, a.y, a.z}, bv[3] = {b.x, b.y, b.z};
-  bool ash[3], bsh[3];
+  bool ash[3];
   int nsh = 0;
 #pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    ash[i] = (av[i] == bv[0] || av[i] == bv[1] || av[i] == bv[2]);
-    bsh[i] = (bv[i] == av[0] || bv[i] == av[1] || bv[i] == av[2]);
-  }
+  for (int i = 0; i < 3; ++i) ash[i] = (av[i] == bv[0] || av[i] == bv[1] || av[i] == bv[2]);
   // distinct shared vertex indices of f
   int sl[3], ns = 0;
 #pragma unroll
