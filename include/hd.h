@@ -219,9 +219,10 @@ int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t
 #define HD_NOALLOC_MAX_POINTS 65536
 
 /* The same queries as hd_nearest (same arguments, same results), for callers that cannot
- * let a library allocate device memory during the call: code being recorded into a CUDA
- * graph, programs whose device memory is all handed to their own allocator, loops that must
- * not block in the driver.  The paper has no counterpart; this is an interface variant.
+ * let a library allocate device memory during the call: programs whose device memory is all
+ * handed to their own allocator, services held to a fixed device-memory budget, loops that
+ * must not wait in the driver for an allocation.  The paper has no counterpart; this is an
+ * interface variant.
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
  * array of 4 MiB + 256 B in the library's device image, which every GPU that loads the
  * library keeps until the process exits.  n may be at most HD_NOALLOC_MAX_POINTS (65,536);

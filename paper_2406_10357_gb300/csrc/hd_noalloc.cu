@@ -1,12 +1,12 @@
 // Nearest-triangle queries that allocate nothing.
 //
 // hd_nearest takes its per-point work records and counters from cudaMallocAsync.  Some
-// callers cannot let a library allocate device memory while they run: code that is being
-// recorded into a CUDA graph (an allocation would become part of the graph or break the
-// capture), programs that hand all device memory to their own allocator up front, and
-// latency-critical loops that must not block in the driver.  This variant keeps its scratch
-// in a fixed array that lives in the library's device image instead, so a call only issues a
-// memset and kernel launches on the caller's stream.
+// callers cannot let a library allocate device memory while they run: programs that hand all
+// device memory to their own allocator up front (a library allocation would fail, or take
+// memory their allocator counts on), services that must keep within a fixed device-memory
+// budget, and latency-critical loops that must not wait in the driver for an allocation.  This
+// variant keeps its scratch in a fixed array that lives in the library's device image instead,
+// so a call only issues a memset and kernel launches on the caller's stream.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the library holds it
 // (kNoAllocBytes) until the process exits.  All calls share it and it keeps the last call's

@@ -1,5 +1,5 @@
 """hd_nearest_noalloc: the nearest-triangle queries for callers that cannot let the library
-allocate device memory (graph capture, caller-owned allocators, latency-critical loops).
+allocate device memory (caller-owned allocators, fixed memory budgets, latency-critical loops).
 
 It must give the same results as hd_nearest through the C ABI, on consecutive calls that
 reuse its fixed scratch array, and reject sizes beyond HD_NOALLOC_MAX_POINTS.  This file is
