@@ -249,6 +249,37 @@ def test_u4_closed_form_bridge(orc):
     assert u4 == pytest.approx(math.sqrt(2.01), rel=1e-14)
 
 
+def test_u4_is_the_sampled_two_point_radius(orc):
+    """u4 (Eq. bound_u4) written from its definition, for arbitrary footpoints: with q2, q3 the
+    footpoints of the shortest edge's ends (edges v1v2, v2v3, v3v1, ties to the first) and q1
+    that of the opposite vertex, u4 = min(H(q1, q2), H(q1, q3)), where H(a, b) is the largest
+    min(|p - a|, |p - b|) over p in T.  That is a maximum of a 1-Lipschitz function over T, so
+    a barycentric grid with k steps brackets it: sampled <= H <= sampled + longest edge / k
+    (the grid's covering radius).  This pins the oracle's vertex-and-bisector evaluation and its
+    footpoint labels without using either."""
+    rng = np.random.default_rng(41)
+    VB = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    FB = np.array([[0, 1, 2]], np.int32)
+    k = 150
+    W = bary_grid(k)
+    for t in range(120):
+        T = random_triangle(rng, "generic" if t % 4 else "sliver")
+        q = T + rng.normal(size=(3, 3)) * rng.choice([0.05, 0.5, 2.0])
+        d = np.linalg.norm(q - T, axis=1)
+        I = np.zeros(3, np.int32)
+        u4 = orc.bounds_all(T, d, I, q, VB, FB)[4]
+        e = [np.linalg.norm(T[0] - T[1]), np.linalg.norm(T[1] - T[2]), np.linalg.norm(T[2] - T[0])]
+        s = int(np.argmin(e))
+        q1, q2, q3 = q[(s + 2) % 3], q[s], q[(s + 1) % 3]
+        P = W @ T
+
+        def H(a, b):
+            return np.max(np.minimum(np.linalg.norm(P - a, axis=1), np.linalg.norm(P - b, axis=1)))
+
+        us = min(H(q1, q2), H(q1, q3))
+        assert us - 1e-12 <= u4 <= us + max(e) / k + 1e-12, (t, u4, us, max(e) / k)
+
+
 def test_bounds_closed_form_unequal_heights(orc):
     """T = (0,0,1), (1,0,2), (0,1,3) over a large triangle of z=0, so d = (1, 2, 3) and all
     three project to one triangle.  By hand: exact = 3; u1 = 1 + sqrt(5) (vertex v1, longest
