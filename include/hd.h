@@ -118,11 +118,13 @@ typedef struct {
   int64_t queries;           /* nearest-triangle queries (vertices of A and midpoints)     */
   int64_t pointtri_evals;    /* point-triangle distance evaluations (leaf tests + u3)      */
   int64_t leaf_tests;        /* ... of which in the BVH traversal (leaf triangles tested)  */
-  int64_t box_tests;         /* BVH child-box distance evaluations (2 per node visited)    */
+  int64_t box_tests;         /* BVH child-box distance evaluations (one per non-empty child
+                                of each node visited, so up to 4 per node)                 */
   int64_t discards[6];       /* sub-triangles discarded, by the deciding bound: exact, u1,
                                 u2, u3, u4; [5] = discarded later because l grew past U    */
   int64_t retired;           /* sub-triangles kept but never split again: l <= U <= l + eps */
-  int64_t fp64_escalations;  /* MIXED: point-triangle tests redone in FP64 (slivers)        */
+  int64_t fp64_escalations;  /* MIXED: point-triangle tests redone in FP64 (slivers whose
+                                FP32 certificate was loose)                                 */
   int64_t peak_frontier;     /* largest live frontier                                       */
   int64_t pool_vertices;     /* vertices of A + midpoints made (an edge split by two
                                 sub-triangles in one round gets one midpoint)             */
@@ -133,6 +135,13 @@ typedef struct {
   int64_t kernel_launches;   /* GPU kernels the call launched                               */
   int64_t d2h_bytes;         /* bytes the call read back from the device (run-state
                                 snapshots of its rounds)                                    */
+  int64_t promoted;          /* MIXED: sub-triangles whose gap U - l fell within the FP32 error
+                                width of their vertex distances, so they were finished in the
+                                FP64 certification phase (Section 5.3's rounding limit)    */
+  int64_t node_visits;       /* BVH nodes (128 bytes each) fetched by the traversals        */
+  int64_t long_node_visits;  /* ... of which by the warp-cooperative traversal of long queries */
+  int64_t long_leaf_tests;   /* leaf tests of the warp-cooperative traversal (part of
+                                leaf_tests)                                                  */
 } hd_stats;
 
 typedef struct {
@@ -224,11 +233,13 @@ int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t
  * must not wait in the driver for an allocation.  The paper has no counterpart; this is an
  * interface variant.
  * It calls no cudaMalloc, cudaFree or other allocating routine: its scratch is a fixed
- * array of 4 MiB + 256 B in the library's device image, which every GPU that loads the
+ * array of 4 MiB + 512 B in the library's device image, which every GPU that loads the
  * library keeps until the process exits.  n may be at most HD_NOALLOC_MAX_POINTS (65,536);
  * larger n returns HD_ERR_INVALID without launching anything.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress) with that device current, so
- * make the first call on a device before any stream capture.  All calls share the array:
+ * make the first call on a device before any stream capture.  The address is kept until the
+ * process exits: do not call this entry point on a device after a cudaDeviceReset of it (the
+ * reset destroys the array the address points to).  All calls share the array:
  * calls that overlap on the GPU (different streams or threads without ordering) race and
  * must be serialised by the caller.  Asynchronous on `stream`. */
 int hd_nearest_noalloc(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,
@@ -250,10 +261,12 @@ int hd_upper_bounds(const hd_bvh* B, const double* T, const double* Td, const in
  * pair on the launching stream around each of its kernels and accumulates, per kind,
  * the number of launches and their total device time in milliseconds.  Each pair costs a
  * few microseconds of host time.  Kinds: the whole BVH build of one hd_build_B call
- * (counted as one launch), the nearest-triangle traversal, UpperBound of faces and
- * children, select/split/compaction, validation/pool set-up, and the single-block kernel
- * that runs whole rounds over small frontiers. */
-enum { HD_K_BUILD = 0, HD_K_QUERY = 1, HD_K_BOUND = 2, HD_K_SELECT = 3, HD_K_PREP = 4, HD_K_SMALL = 5, HD_K_KINDS = 6 };
+ * (counted as one launch), the nearest-triangle lane traversal (k_query), UpperBound of
+ * faces and children, select/split/compaction, validation/pool set-up, the single-block
+ * kernel that runs whole rounds over small frontiers, and the warp-cooperative traversal of
+ * long queries (k_query_long). */
+enum { HD_K_BUILD = 0, HD_K_QUERY = 1, HD_K_BOUND = 2, HD_K_SELECT = 3, HD_K_PREP = 4, HD_K_SMALL = 5, HD_K_LONG = 6,
+       HD_K_KINDS = 7 };
 typedef struct {
   int64_t launches[8];
   double ms[8];

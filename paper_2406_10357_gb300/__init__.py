@@ -44,7 +44,8 @@ class HdStats(C.Structure):
                 ("leaf_tests", C.c_int64), ("box_tests", C.c_int64), ("discards", C.c_int64 * 6), ("retired", C.c_int64),
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
                 ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64),
-                ("kernel_launches", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("kernel_launches", C.c_int64), ("d2h_bytes", C.c_int64), ("promoted", C.c_int64),
+                ("node_visits", C.c_int64), ("long_node_visits", C.c_int64), ("long_leaf_tests", C.c_int64)]
 
 
 class HdResult(C.Structure):
@@ -55,8 +56,8 @@ class HdTrace(C.Structure):
     _fields_ = [("launches", C.c_int64 * 8), ("ms", C.c_double * 8)]
 
 
-HD_K_BUILD, HD_K_QUERY, HD_K_BOUND, HD_K_SELECT, HD_K_PREP, HD_K_SMALL = range(6)
-KERNEL_KINDS = ("build", "query", "bound", "select", "prep", "small_rounds")
+HD_K_BUILD, HD_K_QUERY, HD_K_BOUND, HD_K_SELECT, HD_K_PREP, HD_K_SMALL, HD_K_LONG = range(7)
+KERNEL_KINDS = ("build", "query", "bound", "select", "prep", "small_rounds", "query_long")
 
 
 _lib = None
@@ -217,7 +218,8 @@ def _result(r: HdResult) -> dict:
                            retired=s.retired, fp64_escalations=s.fp64_escalations, peak_frontier=s.peak_frontier,
                            pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA,
                            long_queries=s.long_queries, kernel_launches=s.kernel_launches,
-                           d2h_bytes=s.d2h_bytes))
+                           d2h_bytes=s.d2h_bytes, promoted=s.promoted, node_visits=s.node_visits,
+                           long_node_visits=s.long_node_visits, long_leaf_tests=s.long_leaf_tests))
 
 
 def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:
@@ -274,16 +276,26 @@ def hd_hausdorff_batched(bvhs, As, tol: float, opt: HdOptions | None = None, str
     return [_result(outs[i]) for i in range(n)]
 
 
+def _points(P):
+    """P as a contiguous (n, 3) float32 or float64 CUDA tensor (other real dtypes become float64)."""
+    import torch
+
+    if not (_is_torch(P) and P.is_cuda):
+        raise ValueError("P must be a CUDA tensor")
+    if P.ndim != 2 or P.shape[1] != 3:
+        raise ValueError(f"P must have shape (n, 3), not {tuple(P.shape)}")
+    if P.dtype not in (torch.float32, torch.float64):
+        P = P.double()
+    return P.contiguous()
+
+
 def hd_nearest(bvh: Bvh, P, precision: int = HD_FP64, stream=None):
     """Nearest triangle of B for each row of P (a CUDA tensor, float32 or float64).
     Returns CUDA tensors (dist, idx, foot, dist_lo); in HD_MIXED dist is a certified upper
     bound and dist_lo a certified lower bound of d(p, B)."""
     import torch
 
-    assert P.is_cuda
-    P = P.contiguous()
-    if P.dtype not in (torch.float32, torch.float64):
-        P = P.double()
+    P = _points(P)
     n = P.shape[0]
     dev = P.device
     dist = torch.empty(n, dtype=torch.float64, device=dev)
@@ -296,22 +308,39 @@ def hd_nearest(bvh: Bvh, P, precision: int = HD_FP64, stream=None):
     return dist, idx, foot, dlo
 
 
-HD_NOALLOC_MAX_POINTS = 65536
+HD_NOALLOC_MAX_POINTS = 65536  # as include/hd.h defines it (a CPU test compares the two)
+
+
+def _check_out(out, n, device):
+    """The caller's output tensors (dist, idx, foot, dist_lo) must match what the kernels write:
+    float64 / int32 / float64 / float64, n / n / 3 n / n elements, contiguous, on P's device."""
+    import torch
+
+    if len(out) != 4:
+        raise ValueError("out must be (dist, idx, foot, dist_lo)")
+    want = ((torch.float64, n), (torch.int32, n), (torch.float64, 3 * n), (torch.float64, n))
+    for name, t, (dt, k) in zip(("dist", "idx", "foot", "dist_lo"), out, want):
+        if not _is_torch(t) or t.dtype != dt or t.numel() != k or not t.is_contiguous() or t.device != device:
+            raise ValueError(f"out {name}: need a contiguous {dt} tensor of {k} elements on {device}")
 
 
 def hd_nearest_noalloc(bvh: Bvh, P, precision: int = HD_FP64, out=None, stream=None):
     """hd_nearest without any device allocation inside the library (at most
     HD_NOALLOC_MAX_POINTS points).  The output tensors may be passed in ``out`` =
-    (dist, idx, foot, dist_lo) so that the call allocates nothing at all."""
+    (dist, idx, foot, dist_lo) so that the call allocates nothing at all; they are checked
+    (type, size, device, layout) before anything is launched."""
     import torch
 
-    assert P.is_cuda
-    P = P.contiguous()
+    P = _points(P)
     n = P.shape[0]
+    if n > HD_NOALLOC_MAX_POINTS:
+        raise ValueError(f"hd_nearest_noalloc takes at most {HD_NOALLOC_MAX_POINTS} points, not {n}")
+    dev = P.device
     if out is None:
-        dev = P.device
         out = (torch.empty(n, dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
                torch.empty((n, 3), dtype=torch.float64, device=dev), torch.empty(n, dtype=torch.float64, device=dev))
+    else:
+        _check_out(out, n, dev)
     dist, idx, foot, dlo = out
     _check(lib().hd_nearest_noalloc(bvh.handle, P.data_ptr(), HD_F64 if P.dtype == torch.float64 else HD_F32, n,
                                     precision, _stream(True, stream), dist.data_ptr(), idx.data_ptr(),

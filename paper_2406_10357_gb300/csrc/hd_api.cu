@@ -338,6 +338,10 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
   S.long_queries = X.long_queries + Y.long_queries;
   S.kernel_launches = X.kernel_launches + Y.kernel_launches;
   S.d2h_bytes = X.d2h_bytes + Y.d2h_bytes;
+  S.promoted = X.promoted + Y.promoted;
+  S.node_visits = X.node_visits + Y.node_visits;
+  S.long_node_visits = X.long_node_visits + Y.long_node_visits;
+  S.long_leaf_tests = X.long_leaf_tests + Y.long_leaf_tests;
   S.eps_abs = X.eps_abs;
   S.dA = X.dA;
   return HD_OK;

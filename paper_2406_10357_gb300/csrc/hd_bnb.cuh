@@ -66,14 +66,19 @@ __device__ inline int warp_batch(int* counter) {
 }
 
 // Flush per-thread counters with one atomic per warp.  Every lane of the warp must call it.
-__device__ inline void flush_counters(RunState* st, const Counters& c) {
+// The cooperative traversal (long_pass) also counts its node fetches and leaf tests apart.
+__device__ inline void flush_counters(RunState* st, const Counters& c, bool long_pass = false) {
   unsigned long long e = warp_sum((unsigned long long)c.evals), b = warp_sum((unsigned long long)c.boxes),
-                     lf = warp_sum((unsigned long long)c.leaf), x = warp_sum((unsigned long long)c.escalations);
+                     lf = warp_sum((unsigned long long)c.leaf), x = warp_sum((unsigned long long)c.escalations),
+                     nd = warp_sum((unsigned long long)c.nodes);
   if ((threadIdx.x & 31) == 0) {
     if (e + lf) atomicAdd(&st->evals, e + lf);
     if (lf) atomicAdd(&st->leaf_tests, lf);
     if (b) atomicAdd(&st->box_tests, b);
     if (x) atomicAdd(&st->escalations, x);
+    if (nd) atomicAdd(&st->node_visits, nd);
+    if (long_pass && nd) atomicAdd(&st->long_node_visits, nd);
+    if (long_pass && lf) atomicAdd(&st->long_leaf_tests, lf);
   }
   if (c.err) atomicExch(&st->err, 1);
 }
@@ -316,7 +321,7 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
       atomicAdd(&st->long_queries, (unsigned long long)nq);
     }
   }
-  flush_counters(st, c);
+  flush_counters(st, c, true);
 }
 
 template <class P>
@@ -1221,6 +1226,9 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     {
       TraceScope tr(HD_K_QUERY, s);
       launch_chained(k_query<P>, g_q, bs, 0, s, B, R.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, R.tab, R.longq);
+    }
+    {
+      TraceScope tr(HD_K_LONG, s);
       launch_chained(k_query_long<P>, grid_long, 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, true);
     }
     {
@@ -1375,11 +1383,14 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   HD_TRY_LAUNCH();
   {
     TraceScope tr(HD_K_QUERY, s);
-    launch_chained(k_query<PolicyD>, blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s, 
+    launch_chained(k_query<PolicyD>, blocks_for(3 * n_pro, o.block_size), o.block_size, 0, s,
         B, D.pool, 0, nullptr, 1, (int)(3 * n_pro), st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0},
         D.longq);
-    launch_chained(k_query_long<PolicyD>, long_grid<PolicyD>(), 32 * kCoopWarps, 0, s, B, D.pool, D.longq, st, rp.slack, rp.dyn,
-                                                                         false);
+  }
+  {
+    TraceScope tr(HD_K_LONG, s);
+    launch_chained(k_query_long<PolicyD>, long_grid<PolicyD>(), 32 * kCoopWarps, 0, s, B, D.pool, D.longq, st, rp.slack,
+                   rp.dyn, false);
   }
   {
     TraceScope tr(HD_K_BOUND, s);
@@ -1459,9 +1470,12 @@ int run_bnb(const RunIO& io) {
   // round 0: vertices of A, their nearest triangles, l, and the bounds of every face
   {
     TraceScope tr(HD_K_QUERY, s);
-    launch_chained(k_query<P>, std::min(blocks_for(io.nVA, bs), query_grid<P>(bs)), bs, 0, s, 
+    launch_chained(k_query<P>, std::min(blocks_for(io.nVA, bs), query_grid<P>(bs)), bs, 0, s,
         B, R.pool, 0, nullptr, 1, (int)io.nVA, st, rp.slack, rp.dyn, false, MidTable{nullptr, nullptr, nullptr, 0},
         R.longq);
+  }
+  {
+    TraceScope tr(HD_K_LONG, s);
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
@@ -1521,7 +1535,11 @@ int run_bnb(const RunIO& io) {
   S.box_tests = (int64_t)hst->box_tests;
   for (int k = 0; k < 6; ++k) S.discards[k] = (int64_t)hst->discards[k];
   S.retired = (int64_t)hst->retired;
-  S.fp64_escalations = (int64_t)hst->escalations + n_pro;
+  S.fp64_escalations = (int64_t)hst->escalations;
+  S.promoted = n_pro;
+  S.node_visits = (int64_t)hst->node_visits;
+  S.long_node_visits = (int64_t)hst->long_node_visits;
+  S.long_leaf_tests = (int64_t)hst->long_leaf_tests;
   S.peak_frontier = T.peak;
   S.pool_vertices = io.nVA + T.mids;
 
@@ -1574,7 +1592,10 @@ void query_points(const BvhDev& B, typename P::Vtx* rec, int64_t n, RunState* st
                    (int)n, st, 0.0, nullptr, false, MidTable{nullptr, nullptr, nullptr, 0}, ll);
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, rec, ll, st, 0.0, nullptr, false);
   } else {
-    launch_chained(k_query_points<P>, std::min(blocks_for(n, 128), 152u * 16u), 128, 0, s, B, rec, n, st);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    launch_chained(k_query_points<P>, std::min(blocks_for(n, 128), (unsigned)sms * 16u), 128, 0, s, B, rec, n, st);
   }
 }
 

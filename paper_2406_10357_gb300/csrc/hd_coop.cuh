@@ -71,6 +71,7 @@ __device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, u
     float e = INFINITY;
     if (node >= 0) {
       const float* nf = reinterpret_cast<const float*>(B.nodes + node);
+      c.nodes += ch == 0;  // one fetch of the node by its four lanes
       code = __ldg(reinterpret_cast<const unsigned*>(nf) + 24 + ch);
       if (code != kNoChild) {
         ++c.boxes;

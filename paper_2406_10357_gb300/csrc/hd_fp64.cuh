@@ -27,6 +27,7 @@ __device__ inline bool traverse(const BvhDev& B, D3 p, Test& test, Counters& c, 
     const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
     const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
     const uint4 cd = __ldg(reinterpret_cast<const uint4*>(np + 6));
+    ++c.nodes;
     double e[4] = {box_dist2(p, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x), box_dist2(p, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y),
                    box_dist2(p, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z), box_dist2(p, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w)};
     unsigned k[4] = {cd.x, cd.y, cd.z, cd.w};

@@ -134,6 +134,8 @@ struct RunState {
   unsigned long long long_queries;  // queries finished by a whole warp (traverse_coop)
   int tail_rounds;               // rounds the last k_tail_rounds launch ran
   int pad_;
+  unsigned long long node_visits;  // BVH nodes fetched by the traversals (128 bytes each)
+  unsigned long long long_node_visits, long_leaf_tests;  // ... of which by k_query_long, and its leaf tests
 };
 
 // Device view of hd_bvh, passed to kernels by value.
@@ -186,7 +188,7 @@ constexpr int kDeferU4 = 6;
 // Per-thread work counters, summed over the warp and flushed with 64-bit atomics; 32 bits
 // per thread are ample (a thread handles a few thousand items at most).
 struct Counters {
-  unsigned evals = 0, boxes = 0, escalations = 0, leaf = 0;
+  unsigned evals = 0, boxes = 0, escalations = 0, leaf = 0, nodes = 0;
   int err = 0;
 };
 

@@ -26,8 +26,9 @@
 //    is a lower bound of d(p, B).
 //  * Bounds of Section 3.2 take certified vertex distances (upper bounds), edge lengths
 //    rounded up, the circumradius only with the area rounded down, and the split points of
-//    u3 with their representation error added.  u4 runs in FP64 with a relative margin,
-//    where an FP32 estimate says it can pay off.
+//    u3 with their representation error added.  u4 is certified in FP32 too: the vertex and
+//    footpoint differences are float pairs formed with error-free sums, and each remaining
+//    rounded dot product or norm is raised by a bound on its error (ubm_u4).
 #pragma once
 
 #include "hd_fp64.cuh"
@@ -349,6 +350,7 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
       const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
       const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
       const uint4 cd = __ldg(reinterpret_cast<const uint4*>(np + 6));
+      ++c.nodes;
       const float r2 = t.radius2();
       // children within the current radius (the others at +inf), nearest first
       float e0 = box_lo2(plo, phi, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x);

@@ -24,15 +24,19 @@ namespace {
 
 constexpr int64_t kNoAllocMaxPoints = HD_NOALLOC_MAX_POINTS;
 static_assert(sizeof(VtxM) == 64 && sizeof(VtxD) == 64, "one 64-byte record per point");
-static_assert(sizeof(RunState) <= 256, "counters fit the reserved tail");
+constexpr size_t kNoAllocTail = 512;  // the counters (RunState), after the per-point records
+static_assert(sizeof(RunState) <= kNoAllocTail, "counters fit the reserved tail");
 // per point: a 64-byte record and a slot of the long-query list; then the counters
-constexpr size_t kNoAllocBytes = kNoAllocMaxPoints * (64 + 4) + 256;
+constexpr size_t kNoAllocBytes = kNoAllocMaxPoints * (64 + 4) + kNoAllocTail;
 
 static __device__ __align__(256) unsigned char g_scratch[kNoAllocBytes];
 
 // Device address of g_scratch, per device.  In host code the name g_scratch is only a
 // host-side stand-in for the symbol, not a device address, so it is looked up once per device
-// with that device current.
+// with that device current.  The address is kept for the life of the process: it belongs to
+// the device's primary context, so a cudaDeviceReset (which destroys that context and the
+// module's copy of the array) makes it stale, and the entry point must not be used on a device
+// after such a reset.
 std::mutex g_mu;
 void* g_addr[64] = {};
 
@@ -58,7 +62,7 @@ int run(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, 
   if (rc != HD_OK) return rc;
   typename P::Vtx* rec = (typename P::Vtx*)base;
   RunState* st = (RunState*)((unsigned char*)base + kNoAllocMaxPoints * 64);
-  int* list = (int*)((unsigned char*)base + kNoAllocMaxPoints * 64 + 256);
+  int* list = (int*)((unsigned char*)base + kNoAllocMaxPoints * 64 + kNoAllocTail);
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));  // counters start at zero every call
   if (ptype == HD_F64)
     k_points_in<P, double><<<blocks_for(n, 256), 256, 0, s>>>((const double*)Pts, n, rec);

@@ -48,8 +48,8 @@ def test_struct_layouts_match_header(hd):
     # sizes of the ABI structs as laid out by a C compiler for this header
     assert C.sizeof(hd.HdMesh) == 40
     assert C.sizeof(hd.HdOptions) == 64
-    assert C.sizeof(hd.HdStats) == 8 * 21
-    assert C.sizeof(hd.HdResult) == 24 + 8 * 21
+    assert C.sizeof(hd.HdStats) == 8 * 25
+    assert C.sizeof(hd.HdResult) == 24 + 8 * 25
     assert C.sizeof(hd.HdTrace) == 128
 
 
@@ -83,3 +83,53 @@ def test_invalid_arguments_rejected_before_any_launch(hd):
     if not _has_gpu():
         good = hd.hd_options_default(flags=hd.HD_FLAG_NO_PARENT_CLAMP)
         assert L.hd_build_B(C.byref(mv), C.byref(good), None, C.byref(out)) == hd.HD_ERR_CUDA
+
+
+def test_noalloc_limit_matches_header(hd):
+    text = open(os.path.join(ROOT, "include", "hd.h")).read()
+    m = re.search(r"#define\s+HD_NOALLOC_MAX_POINTS\s+(\d+)", text)
+    assert m and int(m.group(1)) == hd.HD_NOALLOC_MAX_POINTS
+    assert "hd_nearest_noalloc" in declared_symbols()
+
+
+def test_noalloc_invalid_arguments_rejected_before_any_launch(hd):
+    """Every check below returns before the handle is read or any CUDA call is made (the
+    non-null handle is a dummy host buffer that is never dereferenced)."""
+    L = hd.lib()
+    dummy = (C.c_char * 64)()
+    B = C.cast(dummy, C.c_void_p)
+    buf = (C.c_double * 8)()
+    p = C.cast(buf, C.c_void_p)
+    args = lambda b, ptype, n, prec: (b, p, ptype, n, prec, None, p, p, p, p)
+    assert L.hd_nearest_noalloc(*args(None, hd.HD_F64, 1, hd.HD_FP64)) == hd.HD_ERR_INVALID
+    assert L.hd_nearest_noalloc(*args(B, hd.HD_F64, -1, hd.HD_FP64)) == hd.HD_ERR_INVALID
+    assert L.hd_nearest_noalloc(*args(B, hd.HD_F64, hd.HD_NOALLOC_MAX_POINTS + 1, hd.HD_FP64)) == hd.HD_ERR_INVALID
+    assert L.hd_nearest_noalloc(*args(B, 7, 1, hd.HD_FP64)) == hd.HD_ERR_INVALID
+    assert L.hd_nearest_noalloc(*args(B, hd.HD_F32, 1, 9)) == hd.HD_ERR_INVALID
+    assert L.hd_nearest_noalloc(B, None, hd.HD_F64, 1, hd.HD_FP64, None, p, p, p, p) == hd.HD_ERR_INVALID
+
+
+def test_noalloc_binding_checks_before_any_launch(hd):
+    """The Python binding refuses points that are not an (n, 3) CUDA tensor and output tensors
+    of the wrong type, size, layout or device, before it calls the library."""
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        hd.hd_nearest_noalloc(None, torch.zeros((4, 3), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        hd.hd_nearest(None, np.zeros((4, 3)))
+    dev = torch.device("cpu")
+    good = (torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.int32), torch.zeros((5, 3), dtype=torch.float64),
+            torch.zeros(5, dtype=torch.float64))
+    hd._check_out(good, 5, dev)
+    bad = [
+        (good[0][:4], *good[1:]),                                   # too small
+        (good[0].float(), *good[1:]),                               # wrong type
+        (good[0], good[1].long(), *good[2:]),                       # wrong index type
+        (good[0], good[1], torch.zeros((3, 5), dtype=torch.float64).t(), good[3]),  # not contiguous
+        good[:3],                                                   # missing dist_lo
+    ]
+    for out in bad:
+        with pytest.raises(ValueError):
+            hd._check_out(out, 5, dev)
+    with pytest.raises(ValueError):
+        hd._check_out(good, 5, torch.device("meta"))

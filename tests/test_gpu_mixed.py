@@ -155,6 +155,12 @@ def test_bracket_mixed_vs_oracle(hd, orc, k, scale):
     assert r["status"] == hd.HD_OK, r
     assert r["upper"] - r["lower"] <= eps
     assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + ORACLE_REL * ro["upper"]
+    if k != 3:
+        # the oracle at eps / 100 brackets h within a hundredth of eps: a MIXED bracket that
+        # missed h would miss this narrow one, even where it meets the wide one above
+        rt = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol / 100, p.tol_mode)
+        assert rt["status"] == orc.OK
+        assert r["lower"] <= rt["upper"] + ORACLE_REL * rt["upper"] and rt["lower"] <= r["upper"] + ORACLE_REL * rt["upper"]
     # MIXED and FP64 GPU brackets intersect too
     r64 = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, hd.hd_options_default(tol_mode=p.tol_mode))
     assert max(r["lower"], r64["lower"]) <= min(r["upper"], r64["upper"]) + ORACLE_REL * r64["upper"]
@@ -258,3 +264,118 @@ def test_upper_bounds_mixed_certified(hd, orc, order):
             kept = code[sel] == 5
             assert kept.sum() >= 20
             assert np.quantile(np.abs(rel[kept]), 0.95) <= 1e-3, np.quantile(np.abs(rel[kept]), 0.95)
+
+
+# ---------------------------------------------------------------- the FP64 certification phase
+
+
+def _tight_parity(orc, p, r, tol, mode, eps):
+    """r is within eps, meets the oracle's bracket at the same tolerance and at 1/100 of it."""
+    assert r["status"] == 0, r
+    assert r["upper"] - r["lower"] <= eps * (1 + 1e-12), (r["upper"] - r["lower"], eps)
+    for t in (tol, tol / 100):
+        ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, t, mode)
+        assert ro["status"] == orc.OK
+        assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + ORACLE_REL * ro["upper"], (t, r, ro)
+
+
+def test_closed_forms_promote_to_fp64_at_tight_tolerance(hd):
+    """At tol 1e-6 the closed-form pairs end with gaps U - l below the FP32 error width of
+    their vertex distances (about 2^-18 of U), which FP32 refinement cannot resolve: those
+    sub-triangles are finished in the FP64 phase (Section 5.3's rounding limit), and every
+    bracket still holds the hand-derived h."""
+    total = 0
+    for case in _load_golden():
+        VA, FA = np.array(case["VA"], float), np.array(case["FA"], np.int32)
+        VB, FB = np.array(case["VB"], float), np.array(case["FB"], np.int32)
+        r = hd.hd_hausdorff(hd.hd_build_B(VB, FB), VA, FA, case["tol"], hd.hd_options_default(precision=hd.HD_MIXED))
+        assert r["status"] == hd.HD_OK, (case["name"], r)
+        assert r["lower"] <= case["h"] <= r["upper"] and r["upper"] - r["lower"] <= case["tol"], case["name"]
+        total += r["stats"]["promoted"]
+        print(case["name"], "promoted", r["stats"]["promoted"])
+    assert total > 0
+
+
+@pytest.mark.parametrize("k,scale,tol", [(2, 0.02, 1e-8), (5, 0.005, 1e-8)])
+def test_promotion_on_reduced_workloads(hd, orc, k, scale, tol):
+    """Reduced workloads at tol 1e-8 dA: the last items' gaps are below FP32 resolution, so
+    the run promotes them and finishes them in FP64; the bracket meets the oracle's at the
+    same tolerance and at 1/100 of it."""
+    p = mg.workload(k, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, tol, hd.hd_options_default(tol_mode=p.tol_mode, precision=hd.HD_MIXED))
+    print(p.name, "promoted", r["stats"]["promoted"], "splits", r["stats"]["splits"])
+    assert r["stats"]["promoted"] > 0
+    _tight_parity(orc, p, r, tol, p.tol_mode, tol * _dA(p.VA, p.FA))
+
+
+@pytest.mark.parametrize("tol", [1e-4, 1e-5, 1e-6, 1e-7, 1e-8])
+@pytest.mark.parametrize("k,scale", [(2, 0.02), (5, 0.005)])
+def test_tolerance_ladder_mixed(hd, orc, k, scale, tol):
+    """Runtime-versus-eps ladder (Section 5) in MIXED: at every tolerance from 1e-4 to 1e-8
+    of dA the bracket is within eps and meets the oracle's at that tolerance and at 1/100 of
+    it (the tight end is where the FP64 phase takes over)."""
+    p = mg.workload(k, scale)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    r = hd.hd_hausdorff(bvh, p.VA, p.FA, tol, hd.hd_options_default(tol_mode=p.tol_mode, precision=hd.HD_MIXED))
+    _tight_parity(orc, p, r, tol, p.tol_mode, tol * _dA(p.VA, p.FA))
+
+
+def test_sliver_B_escalates_to_fp64(hd, orc):
+    """B made of slivers up to aspect 1e6 (plus zero-area and repeated-vertex triangles), A a
+    mesh of small triangles hugging their long edges: the FP32 point-triangle certificate is
+    loose there, so tests are redone in FP64 (fp64_escalations > 0), and the bracket still
+    meets the oracle's."""
+    rng = np.random.default_rng(606)
+    n = 300
+    a = rng.normal(size=(n, 3))
+    d = rng.normal(size=(n, 3))
+    side = np.cross(d, rng.normal(size=(n, 3)))
+    side /= np.linalg.norm(side, axis=1, keepdims=True)
+    L = np.linalg.norm(d, axis=1, keepdims=True)
+    aspect = 10.0 ** rng.uniform(3, 6, size=(n, 1))
+    T = np.stack([a, a + d, a + 0.37 * d + side * L / aspect], 1)
+    T[::17, 2] = T[::17, 0]
+    T[::23, 2] = 0.5 * (T[::23, 0] + T[::23, 1])
+    VB = T.reshape(-1, 3)
+    FB = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    # A: one small triangle near the middle of each sliver's long edge, slightly off it
+    c = a + 0.5 * d + rng.normal(size=(n, 3)) * 1e-3
+    u = rng.normal(size=(n, 3)) * 1e-3
+    w = rng.normal(size=(n, 3)) * 1e-3
+    VA = np.stack([c, c + u, c + w], 1).reshape(-1, 3)
+    FA = np.arange(3 * n, dtype=np.int32).reshape(n, 3)
+    tol = 1e-6
+    r = hd.hd_hausdorff(hd.hd_build_B(VB, FB), VA, FA, tol, hd.hd_options_default(precision=hd.HD_MIXED))
+    print("sliver B: escalations", r["stats"]["fp64_escalations"], "promoted", r["stats"]["promoted"])
+    assert r["stats"]["fp64_escalations"] > 0
+    ro = orc.hausdorff(VA, FA, VB, FB, tol, 0)
+    assert r["status"] == hd.HD_OK and r["upper"] - r["lower"] <= tol * (1 + 1e-12)
+    assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + ORACLE_REL * ro["upper"]
+
+
+@pytest.mark.parametrize("clamp", [True, False])
+def test_bracket_all_bound_orders_mixed(hd, orc, clamp):
+    """Every one of the 64 cascades (ordered subsets of u1..u4, Section 5's bound-order
+    benchmark) in MIXED on workload 1: each bracket meets the oracle's at eps and, when the
+    run finished, at eps / 100.  The paper's order runs the straight-line kernels, every
+    other order the general ones; with the parent clamp on and off."""
+    import itertools
+
+    p = mg.workload(1)
+    ref = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol, 0)
+    tight = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, p.tol / 100, 0)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    flags = 0 if clamp else hd.HD_FLAG_NO_PARENT_CLAMP
+    n = 0
+    for kk in range(1, 5):
+        for order in itertools.permutations((1, 2, 3, 4), kk):
+            o = hd.hd_options_default(precision=hd.HD_MIXED, bound_order=order, max_face_factor=2000, flags=flags)
+            r = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, o)
+            assert r["status"] in (hd.HD_OK, hd.HD_ERR_CAPACITY), (order, r)
+            for ro in (ref, tight):
+                assert max(r["lower"], ro["lower"]) <= min(r["upper"], ro["upper"]) + 1e-12, (order, r, ro)
+            if r["status"] == hd.HD_OK:
+                assert r["upper"] - r["lower"] <= p.tol * (1 + 1e-12), order
+            n += 1
+    assert n == 64

@@ -397,6 +397,28 @@ def test_sampling_bracket_agrees_workload1(orc):
     assert r["upper"] - r["lower"] <= p.tol
 
 
+@pytest.mark.parametrize("k", [4, 5, 10, 11, 40, 41])
+def test_sampling_bracket_thin_bridge_closed_form(orc, k):
+    """P5 pinned to a closed form: on the thin bridge (tests/golden/closed_forms.json, h = sqrt(2)
+    at x = 1, interior to A) the sampling bracket holds h for every k.  With one face its width
+    is the covering radius emax / k (emax = A's longest edge), so it shrinks like 1/k.  An even
+    k puts a sample on x = 1, so lo = h; an odd k's nearest samples are 1/k away in x, so
+    h - lo ~ 0.71 / k: a covering radius below that (a quarter of the true one, say) would
+    leave hi < h there."""
+    c = [c for c in _load_golden() if c["name"] == "thin_bridge_interior_maximiser"][0]
+    VA, FA = np.array(c["VA"], float), np.array(c["FA"], np.int32)
+    VB, FB = np.array(c["VB"], float), np.array(c["FB"], np.int32)
+    h = math.sqrt(2.0)
+    lo, hi = orc.sampling_bracket(VA, FA, VB, FB, k)
+    emax = max(np.linalg.norm(VA[1] - VA[0]), np.linalg.norm(VA[2] - VA[1]), np.linalg.norm(VA[0] - VA[2]))
+    assert lo <= h + 1e-12 and h <= hi + 1e-12, (k, lo, hi)
+    assert abs((hi - lo) - emax / k) <= 1e-12
+    if k % 2 == 0:
+        assert abs(lo - h) <= 1e-12
+    else:
+        assert 0.5 / k <= h - lo <= 1.0 / k, (k, h - lo)
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_sampling_bracket_random_soups(orc, seed):
     """P5 on random soups where the maximiser is usually interior."""
