@@ -542,13 +542,21 @@ def batched_pairs(args, torch, hd, dev, prec):
         if best is None or t < best:
             best, rs = t, rr
     ok = sum(r["status"] == hd.HD_OK for r in rs)
+    # the same pairs as single runs on host threads with a stream each (HD_FLAG_BATCH_STREAMS)
+    ost = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=prec, flags=hd.HD_FLAG_BATCH_STREAMS)
+    t_st, r_st = ev_time(lambda: hd.hd_hausdorff_batched(bvhs, As, tol, ost))
     o64 = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64)
     t64, r64 = ev_time(lambda: [hd.hd_hausdorff(b, VA, FA, tol, o64) for b, (VA, FA) in zip(bvhs, As)])
     ok64 = sum(r["status"] == hd.HD_OK for r in r64)
     nf = sum(len(q.FA) + len(q.FB) for q in pairs)
     return dict(workload=f"{n} pairs of the batched workload (triangles per side log-uniform in [1K, 200K], "
                          f"{nf:,} in total), tol 1e-4 x bbox diagonal of each A",
-                batched_mixed=dict(value=n / best, unit=UNIT, seconds=best, ok=ok),
+                batched_mixed=dict(value=n / best, unit=UNIT, seconds=best, ok=ok,
+                                   rounds=max(r["stats"]["rounds"] for r in rs),
+                                   kernel_launches=rs[0]["stats"]["kernel_launches"]),
+                streams_mixed=dict(value=n / t_st, unit=UNIT, seconds=t_st,
+                                   ok=sum(r["status"] == hd.HD_OK for r in r_st),
+                                   note="single runs on host threads, one stream each (HD_FLAG_BATCH_STREAMS)"),
                 batched_mixed_with_builds=dict(value=n / (best + t_build), unit=UNIT, build_seconds=t_build),
                 sequential_fp64=dict(value=n / t64, unit=UNIT, seconds=t64, ok=ok64),
                 speedup_vs_sequential_fp64=t64 / best)

@@ -88,8 +88,12 @@ enum {
   HD_FLAG_ASYNC_BUILD = 2,
   HD_FLAG_SHARE_MIDPOINTS = 4,
   HD_FLAG_WELD_B = 8,
-  HD_FLAG_NO_SMALL_ROUNDS = 16
+  HD_FLAG_NO_SMALL_ROUNDS = 16,
+  HD_FLAG_BATCH_STREAMS = 32
 };
+/* HD_FLAG_BATCH_STREAMS (read by hd_hausdorff_batched): run the pairs as independent single
+ * runs on host threads with one stream each, instead of the default batched run in which every
+ * kernel launch works on the items of all pairs. */
 /* HD_FLAG_NO_SMALL_ROUNDS: every frontier round runs as a sequence of grid-wide kernels.  By
  * default, rounds over a frontier of at most 64 items (the last rounds of most runs) run
  * inside one single-block kernel that loops over them without the host; the results are the
@@ -203,14 +207,20 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
                      const hd_options* opt, void* stream, hd_result* out, hd_result* ab, hd_result* ba);
 
 /* npairs independent problems h(As[i], Bs[i]) with one tolerance and one option set;
- * outs[i] receives each result.  Host threads (two per host core, 8 to 64), each with its
- * own non-blocking stream on the current device, take the pairs in turn, so that the
- * kernels of several small pairs run on the GPU at the same time; they start after the work
- * already queued on `stream`, and every pair is complete when the call returns.  All Bs[i]
- * must live on the current device.  Returns HD_ERR_INVALID when the arguments are invalid
- * (checked before anything is launched) or a pair's mesh is found invalid on the device,
- * HD_ERR_CUDA on a CUDA failure, else HD_OK; per-pair CAPACITY/TIMEOUT/NUMERIC are reported
- * in outs[i].status. */
+ * outs[i] receives each result (Sections 3.1 and 4 for every pair).  By default the pairs run
+ * together on `stream` in one batched branch and bound: every kernel launch of a round (the
+ * nearest queries, the bounds, the selection and split) takes its work from a device-side
+ * queue holding the items of all pairs, each pair keeps its own l, u, tolerance and status on
+ * the device and retires on its own gap, and the host reads one small snapshot per round for
+ * the whole batch.  Each pair's bracket has the meaning of its single run's; kernel_launches and
+ * d2h_bytes of every result are the batch's totals.  With HD_FLAG_BATCH_STREAMS (or
+ * HD_FLAG_SHARE_MIDPOINTS, which the batched run does not implement), host threads (two per
+ * host core, 8 to 64), each with its own non-blocking stream, take the pairs in turn as single
+ * runs; they start after the work already queued on `stream`.  Every pair is complete when the
+ * call returns.  All Bs[i] must live on the current device.  Returns HD_ERR_INVALID when the
+ * arguments are invalid (checked before anything is launched) or a pair's mesh is found
+ * invalid on the device, HD_ERR_CUDA on a CUDA failure, else HD_OK; per-pair
+ * CAPACITY/TIMEOUT/NUMERIC are reported in outs[i].status. */
 int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol,
                          const hd_options* opt, void* stream, hd_result* outs);
 

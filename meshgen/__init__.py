@@ -177,15 +177,20 @@ def superquadric(e1: float, e2: float, scale: float, n_lon: int, n_lat: int, jit
     return P, F
 
 
-def _superquadric_point_normal(e1, e2, scale, eta, om, h=1e-6):
-    def pos(et, o):
-        ce = np.cos(et)
-        return scale * np.stack([_spow(ce, e1) * _spow(np.cos(o), e2), _spow(ce, e1) * _spow(np.sin(o), e2),
-                                 _spow(np.sin(et), e1)], 1)
-    P = pos(eta, om)
-    du = pos(eta, om + h) - pos(eta, om - h)
-    dv = pos(eta + h, om) - pos(eta - h, om)
-    N = np.cross(du, dv)
+def _superquadric_point_normal(e1, e2, scale, eta, om):
+    """Points of the superquadric at parameters (eta, om) and their unit normals, the
+    normalised gradient of its implicit form F = (|x|^(2/e2) + |y|^(2/e2))^(e2/e1) + |z|^(2/e1)
+    (closed form: no finite differences, whose cancellation would magnify the last-bit
+    differences of libm between machines into visible ones)."""
+    ce = np.cos(eta)
+    P = scale * np.stack([_spow(ce, e1) * _spow(np.cos(om), e2), _spow(ce, e1) * _spow(np.sin(om), e2),
+                          _spow(np.sin(eta), e1)], 1)
+    U = P / scale
+    ax, ay, az = np.abs(U[:, 0]), np.abs(U[:, 1]), np.abs(U[:, 2])
+    S = ax ** (2 / e2) + ay ** (2 / e2)
+    f = (2 / e1) * S ** (e2 / e1 - 1)
+    N = np.stack([f * ax ** (2 / e2 - 1) * np.sign(U[:, 0]), f * ay ** (2 / e2 - 1) * np.sign(U[:, 1]),
+                  (2 / e1) * az ** (2 / e1 - 1) * np.sign(U[:, 2])], 1)
     N /= np.maximum(np.linalg.norm(N, axis=1, keepdims=True), 1e-300)
     return P, N
 

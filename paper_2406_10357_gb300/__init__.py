@@ -24,6 +24,7 @@ HD_FLAG_ASYNC_BUILD = 2
 HD_FLAG_SHARE_MIDPOINTS = 4
 HD_FLAG_WELD_B = 8
 HD_FLAG_NO_SMALL_ROUNDS = 16
+HD_FLAG_BATCH_STREAMS = 32
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 

@@ -8,6 +8,7 @@
 #include <thread>
 #include <vector>
 
+#include "hd_batch.cuh"
 #include "hd_bnb.cuh"
 #include "hd_fp64.cuh"
 
@@ -97,7 +98,7 @@ int resolve_options(const hd_options* in, Opts* o) {
   memcpy(o->order, x.bound_order, 4);
   o->flags = x.flags;
   if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS | HD_FLAG_WELD_B |
-                                      HD_FLAG_NO_SMALL_ROUNDS))) return HD_ERR_INVALID;
+                                      HD_FLAG_NO_SMALL_ROUNDS | HD_FLAG_BATCH_STREAMS))) return HD_ERR_INVALID;
   if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
   if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
   if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;
@@ -135,6 +136,8 @@ static void keep_pool_memory() {
 
 int run_fp64(const RunIO& io) { return run_bnb<PolicyD>(io); }
 int run_mixed(const RunIO& io);
+int run_batch_mixed(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol, const Opts& o,
+                    cudaStream_t s, hd_result* outs);
 
 int nearest_points_fp64(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                         int32_t* idx, double* foot, double* dlo) {
@@ -355,8 +358,24 @@ int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npa
   if (!(tol > 0.0) || resolve_options(opt, &o) != HD_OK) return HD_ERR_INVALID;
   int dev = -1;
   HD_TRY(cudaGetDevice(&dev));
-  for (int64_t i = 0; i < npairs; ++i)
+  int64_t nV = 0, nF = 0;
+  for (int64_t i = 0; i < npairs; ++i) {
     if (!Bs[i] || Bs[i]->device != dev || check_mesh(&As[i]) != HD_OK) return HD_ERR_INVALID;
+    nV += As[i].nV;
+    nF += As[i].nF;
+  }
+  keep_pool_memory();
+  // the batched run: one launch per phase for all pairs (pool indices of all pairs' vertices
+  // and the face enumeration must stay well inside int)
+  if (!(o.flags & (HD_FLAG_BATCH_STREAMS | HD_FLAG_SHARE_MIDPOINTS)) && npairs <= INT32_MAX / 4 && nV <= INT32_MAX / 8 &&
+      nF <= INT32_MAX / 8) {
+    for (int64_t i = 0; i < npairs; ++i) {
+      memset(&outs[i], 0, sizeof outs[i]);
+      outs[i].status = HD_ERR_INVALID;
+    }
+    return o.precision == HD_FP64 ? run_batch<PolicyD>(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs)
+                                  : run_batch_mixed(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs);
+  }
   // Pairs are independent: host threads, each with its own non-blocking stream, take pairs
   // in turn, so that the kernels of several small pairs share the GPU (two threads per host
   // core, 8 to 64: each thread spends much of a pair waiting for its stream).  The streams

@@ -1,10 +1,16 @@
 // Instantiation of the frontier rounds and point queries for the certified FP32 policy.
+#include "hd_batch.cuh"
 #include "hd_bnb.cuh"
 #include "hd_mixed.cuh"
 
 namespace hd {
 
 int run_mixed(const RunIO& io) { return run_bnb<PolicyM>(io); }
+
+int run_batch_mixed(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol, const Opts& o,
+                    cudaStream_t s, hd_result* outs) {
+  return run_batch<PolicyM>(Bs, As, npairs, tol, o, s, outs);
+}
 
 int nearest_points_mixed(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                          int32_t* idx, double* foot, double* dlo) {

@@ -76,6 +76,10 @@ def oracle_bracket(orc, key, p):
             _live[key] = dict(lower=r["lower"], upper=r["upper"], status=r["status"], max_face_factor=m)
         e = _live[key]
     m = e.get("max_face_factor", 1e7)
+    if e["status"] == orc.NUMERIC:
+        # the paper's FP64 rounding limit (Section 5.3): every item was discarded by a bound
+        # rounded a hair below l; only the oracle's lower bound is then known
+        return e["lower"], float("inf"), m
     assert e["status"] == orc.OK or (m < 1e7 and e["status"] == orc.CAPACITY), e
     return e["lower"], e["upper"], m
 
