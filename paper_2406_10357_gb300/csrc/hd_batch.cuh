@@ -130,8 +130,11 @@ __device__ inline void flush_counters_pair(RunState* sts, int pair, const Counte
   if (c.err) atomicExch(&st->err, 1);
 }
 
-// Lower bound and query count of one lane for its pair.  Every lane must call it.
+// Lower bound and query count of one lane for its pair.  Every lane must call it.  l stays
+// non-negative (a certified vertex distance less its slack can be below 0), which the atomic
+// maximum on its bits needs.
 __device__ inline void flush_lower_pair(RunState* sts, int pair, double lmax, int nq, bool long_pass) {
+  lmax = fmax(lmax, 0.0);
   const int u = warp_pair(pair);
   if (u >= 0) {
     const double m = warp_max(pair >= 0 ? lmax : 0.0);

@@ -203,11 +203,53 @@ __device__ inline int warp_slot(int* counter) {
 }
 
 // The queries a launch of k_query hands to k_query_long: pool indices, with room for as many
-// as the launch has queries.  A null list: every lane finishes its own query.
+// as the launch has queries.  A null list: every lane finishes its own query.  With `sorted`
+// and `buckets` (kSortBuckets counters, zero between launches), a list of at least
+// kSortMin queries is reordered along a Morton curve of the query points before the
+// cooperative pass (k_long_hist, k_long_scan, k_long_scatter), so that queries taken one
+// after another share the nodes and triangles near them in L1 and L2.
 struct LongList {
   int* idx;
   int cap;
+  int* sorted = nullptr;
+  unsigned* buckets = nullptr;
 };
+
+constexpr int kSortBits = 5;                           // Morton bits per axis of the reordering
+constexpr int kSortBuckets = 1 << (3 * kSortBits);     // 32768 cells of B's bounding box
+constexpr int kSortMin = 2048;                         // shorter lists keep their order
+#ifndef HD_LONG_CHUNK
+#define HD_LONG_CHUNK 4
+#endif
+constexpr int kLongChunk = HD_LONG_CHUNK;              // consecutive sorted queries per warp step
+
+__device__ inline unsigned spread5(unsigned x) {  // bits 0..4 of x to bits 0, 3, 6, 9, 12
+  x &= 31u;
+  x = (x | (x << 8)) & 0x0000f00fu;
+  x = (x | (x << 4)) & 0x000c30c3u;
+  x = (x | (x << 2)) & 0x00249249u;
+  return x;
+}
+
+// Morton cell of point p in B's bounding box (the union of the root's child boxes).
+__device__ inline unsigned long_bucket(const BvhDev& B, float px, float py, float pz) {
+  const float4* np = reinterpret_cast<const float4*>(B.nodes);
+  const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
+  const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
+  const float lo[3] = {fminf(fminf(lx.x, lx.y), fminf(lx.z, lx.w)), fminf(fminf(ly.x, ly.y), fminf(ly.z, ly.w)),
+                       fminf(fminf(lz.x, lz.y), fminf(lz.z, lz.w))};
+  const float hi[3] = {fmaxf(fmaxf(hx.x, hx.y), fmaxf(hx.z, hx.w)), fmaxf(fmaxf(hy.x, hy.y), fmaxf(hy.z, hy.w)),
+                       fmaxf(fmaxf(hz.x, hz.y), fmaxf(hz.z, hz.w))};
+  const float p[3] = {px, py, pz};
+  unsigned q[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ext = hi[k] - lo[k];
+    const float u = ext > 0.f ? (p[k] - lo[k]) * ((float)(1 << kSortBits) / ext) : 0.f;
+    q[k] = (unsigned)fminf(fmaxf(u, 0.f), (float)((1 << kSortBits) - 1));  // NaN -> 0
+  }
+  return (spread5(q[0]) << 2) | (spread5(q[1]) << 1) | spread5(q[2]);
+}
 
 // Nearest-triangle queries for pool vertices [beg, beg + count); count = min(*count_ptr *
 // mult, cap) when count_ptr is given (device-side counts), else `cap`.  Warps take batches of
@@ -282,6 +324,10 @@ __global__ void HD_QUERY_REGS k_query(BvhDev B, typename P::Vtx* pool, int beg, 
                         LongList ll) {
   grid_dep_wait();
   grid_dep_launch();
+  if (ll.buckets) {  // the cell counters of this launch's reordering (k_long_hist) start at zero
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kSortBuckets; i += gridDim.x * blockDim.x)
+      ll.buckets[i] = 0u;
+  }
   query_body<P>(B, pool, beg, count_ptr, mult, cap, st, slack_in, dyn, round_midpoints, tab, ll);
 }
 
@@ -296,21 +342,27 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
   if (n == 0) return;  // uniform over the grid
   const double slack = dyn ? dyn->slack : slack_in;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // a sorted list is taken kLongChunk neighbouring queries at a time
+  const bool sorted = ll.sorted && n >= kSortMin;
+  const int* list = sorted ? ll.sorted : ll.idx;
+  const int chunk = sorted ? kLongChunk : 1;
   Counters c;
   double lmax = 0.0;
   int nq = 0;
   for (;;) {
-    int i = 0;
-    if (lane == 0) i = atomicAdd(&st->long_next, 1);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= n) break;
-    const int k = ll.idx[i];
-    typename P::Vtx v = pool[k];
-    P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack);
-    if (lane == 0) {
-      pool[k] = v;
-      lmax = fmax(lmax, P::lower(v) - slack);
-      ++nq;
+    int i0 = 0;
+    if (lane == 0) i0 = atomicAdd(&st->long_next, chunk);
+    i0 = __shfl_sync(0xffffffffu, i0, 0);
+    if (i0 >= n) break;
+    for (int i = i0; i < min(i0 + chunk, n); ++i) {
+      const int k = list[i];
+      typename P::Vtx v = pool[k];
+      P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack);
+      if (lane == 0) {
+        pool[k] = v;
+        lmax = fmax(lmax, P::lower(v) - slack);
+        ++nq;
+      }
     }
   }
   lmax = warp_max(lmax);
@@ -333,6 +385,83 @@ __global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(
   grid_dep_wait();
   grid_dep_launch();
   query_long_body<P>(B, pool, ll, st, slack_in, dyn, round_midpoints, s_code, s_e);
+}
+
+// The reordering of a long-query list along the Morton curve of its points (a counting sort on
+// kSortBuckets cells): per-cell counts, their exclusive scan, then each index to its cell's next
+// slot (the order within a cell is arbitrary).  Lists shorter than kSortMin are left as they are
+// (every kernel returns at once; uniform over the grid).
+template <class P>
+__global__ void k_long_hist(BvhDev B, const typename P::Vtx* pool, LongList ll, const RunState* st,
+                            bool round_midpoints) {
+  grid_dep_wait();
+  grid_dep_launch();
+  if (round_midpoints && st->stop) return;
+  const int n = min(st->n_long, ll.cap);
+  if (n < kSortMin) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const D3 x = P::exact_pos(pool[ll.idx[i]]);
+    atomicAdd(&ll.buckets[long_bucket(B, (float)x.x, (float)x.y, (float)x.z)], 1u);
+  }
+}
+
+// One block of 1024 threads; each scans 32 consecutive counters.
+static __global__ void k_long_scan(LongList ll, const RunState* st, bool round_midpoints) {
+  grid_dep_wait();
+  grid_dep_launch();
+  if (round_midpoints && st->stop) return;
+  if (min(st->n_long, ll.cap) < kSortMin) return;
+  constexpr int per = kSortBuckets / 1024;
+  __shared__ unsigned part[1024];
+  unsigned v[per];
+  unsigned sum = 0;
+  const int b = threadIdx.x * per;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    v[k] = ll.buckets[b + k];
+    sum += v[k];
+  }
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the 1024 partial sums
+    const unsigned y = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    ll.buckets[b + k] = run;
+    run += v[k];
+  }
+}
+
+template <class P>
+__global__ void k_long_scatter(BvhDev B, const typename P::Vtx* pool, LongList ll, const RunState* st,
+                               bool round_midpoints) {
+  grid_dep_wait();
+  grid_dep_launch();
+  if (round_midpoints && st->stop) return;
+  const int n = min(st->n_long, ll.cap);
+  if (n < kSortMin) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int k = ll.idx[i];
+    const D3 x = P::exact_pos(pool[k]);
+    const unsigned pos = atomicAdd(&ll.buckets[long_bucket(B, (float)x.x, (float)x.y, (float)x.z)], 1u);
+    ll.sorted[pos] = k;  // pos < n: the cells' counts sum to n
+  }
+}
+
+// Launches the reordering of the long-query list of the k_query launch queued just before
+// (nothing happens on the device for short lists).
+template <class P>
+void sort_long(const BvhDev& B, const typename P::Vtx* pool, const LongList& ll, const RunState* st,
+               bool round_midpoints, int sms, cudaStream_t s) {
+  if (!ll.sorted) return;
+  launch_chained(k_long_hist<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints);
+  launch_chained(k_long_scan, 1, 1024, 0, s, ll, st, round_midpoints);
+  launch_chained(k_long_scatter<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints);
 }
 
 // Per-thread outcome counts and maxima of classified items, flushed once per warp.
@@ -882,6 +1011,8 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_rounds(BvhDev B, TailBufs
   __shared__ int s_go;
   grid_dep_wait();
   grid_dep_launch();
+  // a round here hands off at most a few queries: the list keeps its order
+  const LongList lq = {a.longq.idx, a.longq.cap, nullptr, nullptr};
   int rounds = 0;
   for (;;) {
     if (threadIdx.x == 0) {
@@ -895,9 +1026,9 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_rounds(BvhDev B, TailBufs
     select_body<P>(a.front[cur], st, rp, a.split_par, a.split_mid, a.tab, a.pool, a.front[cur ^ 1], a.front_cap,
                    a.promo, a.promo_cap);
     __syncthreads();
-    query_body<P>(B, a.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, a.tab, a.longq);
+    query_body<P>(B, a.pool, 0, nullptr, 3, 0, st, rp.slack, rp.dyn, true, a.tab, lq);
     __syncthreads();
-    query_long_body<P>(B, a.pool, a.longq, st, rp.slack, rp.dyn, true, s_code, s_e);
+    query_long_body<P>(B, a.pool, lq, st, rp.slack, rp.dyn, true, s_code, s_e);
     __syncthreads();
     bound_children_body<P>(B, a.pool, a.split_par, a.split_mid, st, rp, a.front[cur ^ 1], a.front_cap, a.u4list);
     __syncthreads();
@@ -1082,9 +1213,13 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
                b_key = round_up(sizeof(unsigned long long) * n_tab), b_val = round_up(sizeof(int) * n_tab),
                b_qh = share ? round_up(sizeof(int) * 3 * R.chunk) : 0,
                b_long = round_up(sizeof(int) * std::max<int64_t>(min_pool, 3 * R.chunk));
+  // the long-query reordering, where a launch can hand off enough queries for it to matter
+  const bool sort = std::max<int64_t>(min_pool, 3 * R.chunk) >= kSortMin;
+  const size_t b_sorted = sort ? b_long : 0, b_buckets = sort ? round_up(sizeof(unsigned) * kSortBuckets) : 0;
   char* base = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&base,
-                         b_pool + 2 * b_front + 2 * b_split + 2 * b_promo + b_key + b_val + b_qh + b_long, s));
+  HD_TRY(cudaMallocAsync((void**)&base, b_pool + 2 * b_front + 2 * b_split + 2 * b_promo + b_key + b_val + b_qh + b_long +
+                                            b_sorted + b_buckets,
+                         s));
   R.base = base;
   char* p = base;
   auto carve = [&p](size_t b) {
@@ -1098,6 +1233,10 @@ int alloc_rounds(Rounds<P>& R, const Opts& o, int64_t min_pool, int64_t min_fron
   R.split_par = (int4*)carve(b_split);
   R.split_mid = (int4*)carve(b_split);
   R.longq = {(int*)carve(b_long), (int)std::max<int64_t>(min_pool, 3 * R.chunk)};
+  if (sort) {
+    R.longq.sorted = (int*)carve(b_sorted);
+    R.longq.buckets = (unsigned*)carve(b_buckets);
+  }
   if (share) {
     R.tab.key = (unsigned long long*)carve(b_key);
     R.tab.val = (int*)carve(b_val);
@@ -1229,6 +1368,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     }
     {
       TraceScope tr(HD_K_LONG, s);
+      sort_long<P>(B, R.pool, R.longq, st, true, sms, s);
       launch_chained(k_query_long<P>, grid_long, 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, true);
     }
     {
@@ -1389,6 +1529,10 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
   }
   {
     TraceScope tr(HD_K_LONG, s);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    sort_long<PolicyD>(B, D.pool, D.longq, st, false, sms, s);
     launch_chained(k_query_long<PolicyD>, long_grid<PolicyD>(), 32 * kCoopWarps, 0, s, B, D.pool, D.longq, st, rp.slack,
                    rp.dyn, false);
   }
@@ -1476,6 +1620,7 @@ int run_bnb(const RunIO& io) {
   }
   {
     TraceScope tr(HD_K_LONG, s);
+    sort_long<P>(B, R.pool, R.longq, st, false, sms, s);
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
@@ -1585,11 +1730,18 @@ __global__ void k_points_out(const typename P::Vtx* v, int64_t n, const int4* tr
 // n below 2^30), the lane traversal hands long queries to k_query_long as in the rounds;
 // without one, every lane finishes its own query.  `st` must be zeroed.
 template <class P>
-void query_points(const BvhDev& B, typename P::Vtx* rec, int64_t n, RunState* st, int* list, cudaStream_t s) {
+void query_points(const BvhDev& B, typename P::Vtx* rec, int64_t n, RunState* st, int* list, cudaStream_t s,
+                  int* sorted = nullptr, unsigned* buckets = nullptr) {
   if (list && n <= INT32_MAX / 2) {
-    const LongList ll = {list, (int)n};
+    const LongList ll = {list, (int)n, sorted, buckets};
     launch_chained(k_query<P>, std::min(blocks_for(n, 128), query_grid<P>(128)), 128, 0, s, B, rec, 0, nullptr, 1,
                    (int)n, st, 0.0, nullptr, false, MidTable{nullptr, nullptr, nullptr, 0}, ll);
+    if (sorted) {
+      int dev = 0, sms = 1;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      sort_long<P>(B, rec, ll, st, false, sms, s);
+    }
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, rec, ll, st, 0.0, nullptr, false);
   } else {
     int dev = 0, sms = 0;
@@ -1606,10 +1758,16 @@ int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaS
   typename P::Vtx* tmp = nullptr;
   RunState* st = nullptr;
   int* list = nullptr;
+  int* sorted = nullptr;
+  unsigned* buckets = nullptr;
   const bool two_phase = n <= INT32_MAX / 2;  // k_query counts in int
   HD_TRY(cudaMallocAsync((void**)&tmp, sizeof(typename P::Vtx) * n, s));
   HD_TRY(cudaMallocAsync((void**)&st, sizeof(RunState), s));
   if (two_phase) HD_TRY(cudaMallocAsync((void**)&list, sizeof(int) * n, s));
+  if (two_phase && n >= kSortMin) {
+    HD_TRY(cudaMallocAsync((void**)&sorted, sizeof(int) * n, s));
+    HD_TRY(cudaMallocAsync((void**)&buckets, sizeof(unsigned) * kSortBuckets, s));
+  }
   HD_TRY(cudaMemsetAsync(st, 0, sizeof(RunState), s));
   if (ptype == HD_F64)
     launch_chained(k_points_in<P, double>, blocks_for(n, 256), 256, 0, s, (const double*)Pts, n, tmp);
@@ -1617,13 +1775,15 @@ int nearest_points(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaS
     launch_chained(k_points_in<P, float>, blocks_for(n, 256), 256, 0, s, (const float*)Pts, n, tmp);
   {
     TraceScope tr(HD_K_QUERY, s);
-    query_points<P>(bvh_dev(B), tmp, n, st, list, s);
+    query_points<P>(bvh_dev(B), tmp, n, st, list, s, sorted, buckets);
   }
   launch_chained(k_points_out<P>, blocks_for(n, 256), 256, 0, s, tmp, n, B->tri_vid, dist, idx, foot, dlo);
   HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(tmp, s));
   HD_TRY(cudaFreeAsync(st, s));
   if (list) HD_TRY(cudaFreeAsync(list, s));
+  if (sorted) HD_TRY(cudaFreeAsync(sorted, s));
+  if (buckets) HD_TRY(cudaFreeAsync(buckets, s));
   return HD_OK;
 }
 

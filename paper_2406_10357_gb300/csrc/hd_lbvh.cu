@@ -91,11 +91,13 @@ __device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit
   return x;
 }
 
+// Also zeroes the `ntot` digit totals of the sort passes that follow.
 __global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
-                         uint32_t* vals) {
+                         uint32_t* vals, unsigned* tot, int ntot) {
   grid_dep_wait();
   grid_dep_launch();
   int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = f; i < ntot; i += (int64_t)gridDim.x * blockDim.x) tot[i] = 0u;
   if (f >= nF) return;
   const float cells = (float)(1u << bits);
   float4 c = cent[f];
@@ -118,10 +120,11 @@ __global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, i
 // Small inputs use 4 rounds (1024-key tiles) so that more blocks share the work.
 constexpr int RS_WARPS = 8, RS_THREADS = RS_WARPS * 32;
 
-// Per-block digit counts: digit-major (hist[d * nblocks + b], scanned by k_rs_scan) or, for
+// Per-block digit counts: digit-major (hist[d * nblocks + b], scanned by k_rs_scan_digits) or, for
 // the fused small-input path, block-major (hist[b * 256 + d], read by every scatter block).
+// With `tot` (non-fused path), the block's counts are also added to the pass's digit totals.
 template <int ROUNDS, bool FUSED>
-__global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks) {
+__global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* hist, int nblocks, unsigned* tot) {
   grid_dep_wait();
   grid_dep_launch();
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
@@ -135,37 +138,60 @@ __global__ void k_rs_hist(const uint64_t* keys, int64_t n, int shift, unsigned* 
   }
   __syncthreads();
   for (int d = threadIdx.x; d < 256; d += blockDim.x) {
-    if (FUSED) hist[(int64_t)blockIdx.x * 256 + d] = cnt[d];
-    else hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+    if (FUSED) {
+      hist[(int64_t)blockIdx.x * 256 + d] = cnt[d];
+    } else {
+      hist[(int64_t)d * nblocks + blockIdx.x] = cnt[d];
+      if (cnt[d]) atomicAdd(&tot[d], cnt[d]);
+    }
   }
 }
 
 // Largest block count of the fused path: each scatter block then reads all nblocks x 256
 // counts itself instead of waiting for a separate scan launch.
 constexpr int RS_FUSED_MAX_BLOCKS = 64;
+constexpr int kMaxSortPasses = 6;  // 3 x 16-bit Morton keys, 8 bits per pass
 
-// exclusive scan of `n` counters in place, one block of 1024 threads
-__global__ void k_rs_scan(unsigned* a, int64_t n) {
+// The scatter offsets of one pass, one block per digit d (256 blocks of 256 threads): the
+// exclusive scan of digit d's per-block counts (hist[d * nblocks + b], contiguous), plus the
+// keys of all smaller digits (the sum of the pass's totals below d).
+__global__ void k_rs_scan_digits(unsigned* hist, int nblocks, const unsigned* tot) {
   grid_dep_wait();
   grid_dep_launch();
-  __shared__ unsigned part[1024];
-  int64_t per = (n + 1023) / 1024;
-  int64_t b = threadIdx.x * per, e = b + per < n ? b + per : n;
-  unsigned s = 0;
-  for (int64_t i = b; i < e; ++i) s += a[i];
-  part[threadIdx.x] = s;
+  __shared__ unsigned wsum[8];
+  __shared__ unsigned s_base;
+  const int d = blockIdx.x, t = threadIdx.x, w = t >> 5, lane = t & 31;
+  // keys of smaller digits
+  unsigned x = t < d ? tot[t] : 0u;
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  if (lane == 0) wsum[w] = x;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // Hillis-Steele inclusive scan of the 1024 partial sums
-    unsigned v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (t == 0) {
+    unsigned b = 0;
+    for (int k = 0; k < 8; ++k) b += wsum[k];
+    s_base = b;
   }
-  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int64_t i = b; i < e; ++i) {
-    unsigned v = a[i];
-    a[i] = run;
-    run += v;
+  __syncthreads();
+  unsigned carry = s_base;
+  unsigned* a = hist + (int64_t)d * nblocks;
+  for (int c0 = 0; c0 < nblocks; c0 += 256) {
+    const int i = c0 + t;
+    const unsigned v = i < nblocks ? a[i] : 0u;
+    unsigned y = v;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned z = __shfl_up_sync(0xffffffffu, y, o);
+      if (lane >= o) y += z;
+    }
+    __syncthreads();  // wsum is free again
+    if (lane == 31) wsum[w] = y;
+    __syncthreads();
+    unsigned before = 0, all = 0;
+    for (int k = 0; k < 8; ++k) {
+      before += k < w ? wsum[k] : 0u;
+      all += wsum[k];
+    }
+    if (i < nblocks) a[i] = carry + before + y - v;
+    carry += all;
   }
 }
 
@@ -644,7 +670,8 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   };
   size_t o_tri = carve(sizeof(double) * 9 * n), o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
          o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
-         o_ibox = carve(32 * n), o_lv = carve(32 * (n + 64)), o_int = carve(4 * 4 * n + 64), o_misc = carve(64);
+         o_ibox = carve(32 * n), o_lv = carve(32 * (n + 64)), o_int = carve(4 * 4 * n + 64), o_misc = carve(64),
+         o_tot = carve(4 * 256 * kMaxSortPasses);
   // weld: canonical vertex ids, and a table of at least twice the vertices
   const bool weld = (o.flags & HD_FLAG_WELD_B) != 0;
   uint64_t weld_entries = 1024;
@@ -666,6 +693,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   int *left = ints, *right = ints + n, *first = ints + 2 * n, *last = ints + 3 * n;
   // [0..5] centroid box (ordered bits: minima start at all ones), [6] bad, [7] squared eta bits
   unsigned* misc = (unsigned*)(scratch + o_misc);
+  unsigned* tot = (unsigned*)(scratch + o_tot);  // digit totals of each sort pass (unfused path)
 
   TraceScope trace_build(HD_K_BUILD, s);  // the whole build counts as one launch
   HD_TRY(cudaMemsetAsync(misc, 0xff, 3 * sizeof(unsigned), s));
@@ -677,19 +705,21 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
   int bits = 10;
   while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
-  launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, k0, v0);
+  launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, k0, v0, tot,
+                 256 * kMaxSortPasses);
   HD_TRY_LAUNCH();
 
-  for (int shift = 0; shift < 3 * bits; shift += 8) {
+  for (int shift = 0, pass = 0; shift < 3 * bits; shift += 8, ++pass) {
     if (fused && rs_rounds == 4) {
-      launch_chained(k_rs_hist<4, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
+      launch_chained(k_rs_hist<4, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, (unsigned*)nullptr);
       launch_chained(k_rs_scatter<4, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     } else if (fused) {
-      launch_chained(k_rs_hist<16, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
+      launch_chained(k_rs_hist<16, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, (unsigned*)nullptr);
       launch_chained(k_rs_scatter<16, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     } else {
-      launch_chained(k_rs_hist<16, false>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk);
-      launch_chained(k_rs_scan, 1, 1024, 0, s, hist, 256 * (int64_t)nblk);
+      unsigned* tp = tot + 256 * pass;
+      launch_chained(k_rs_hist<16, false>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, tp);
+      launch_chained(k_rs_scan_digits, 256, 256, 0, s, hist, nblk, (const unsigned*)tp);
       launch_chained(k_rs_scatter<16, false>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
     }
     HD_TRY_LAUNCH();
