@@ -542,6 +542,9 @@ def batched_pairs(args, torch, hd, dev, prec):
         if best is None or t < best:
             best, rs = t, rr
     ok = sum(r["status"] == hd.HD_OK for r in rs)
+    statuses = {}
+    for r in rs:
+        statuses[r["status_str"]] = statuses.get(r["status_str"], 0) + 1
     # the same pairs as single runs on host threads with a stream each (HD_FLAG_BATCH_STREAMS)
     ost = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=prec, flags=hd.HD_FLAG_BATCH_STREAMS)
     t_st, r_st = ev_time(lambda: hd.hd_hausdorff_batched(bvhs, As, tol, ost))
@@ -551,11 +554,15 @@ def batched_pairs(args, torch, hd, dev, prec):
     nf = sum(len(q.FA) + len(q.FB) for q in pairs)
     return dict(workload=f"{n} pairs of the batched workload (triangles per side log-uniform in [1K, 200K], "
                          f"{nf:,} in total), tol 1e-4 x bbox diagonal of each A",
-                batched_mixed=dict(value=n / best, unit=UNIT, seconds=best, ok=ok,
+                batched_mixed=dict(value=n / best, unit=UNIT, seconds=best, ok=ok, statuses=statuses,
                                    rounds=max(r["stats"]["rounds"] for r in rs),
+                                   splits=sum(r["stats"]["splits"] for r in rs),
                                    kernel_launches=rs[0]["stats"]["kernel_launches"]),
                 streams_mixed=dict(value=n / t_st, unit=UNIT, seconds=t_st,
                                    ok=sum(r["status"] == hd.HD_OK for r in r_st),
+                                   splits=sum(r["stats"]["splits"] for r in r_st),
+                                   peak_frontier_sum=sum(r["stats"]["peak_frontier"] for r in r_st),
+                                   rounds_max=max(r["stats"]["rounds"] for r in r_st),
                                    note="single runs on host threads, one stream each (HD_FLAG_BATCH_STREAMS)"),
                 batched_mixed_with_builds=dict(value=n / (best + t_build), unit=UNIT, build_seconds=t_build),
                 sequential_fp64=dict(value=n / t64, unit=UNIT, seconds=t64, ok=ok64),

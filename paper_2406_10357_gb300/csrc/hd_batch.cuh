@@ -834,9 +834,13 @@ int alloc_batch(BatchBufs<P>& R, const Opts& o, int64_t min_pool, int64_t min_fr
   using Vtx = typename P::Vtx;
   using Item = typename P::Item;
   const int64_t per_v = sizeof(Vtx) + 4, per_i = sizeof(Item) + 4;
-  // room for midpoints: several times what A alone needs (the pool is not recycled between
-  // rounds), at least 2 GiB
-  const int64_t want = std::max<int64_t>((int64_t)2 << 30, 6 * (min_pool * per_v + min_front * per_i));
+  // All pairs' frontiers and midpoints share these buffers (the pool is not recycled between
+  // rounds), so the automatic budget is many times what A's vertices and faces alone need
+  // (at least 2 GiB), but at most half the device memory that is free.
+  int64_t want = std::max<int64_t>((int64_t)2 << 30, 16 * (min_pool * per_v + min_front * per_i));
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b > 0)
+    want = std::min<int64_t>(want, std::max<int64_t>((int64_t)(free_b / 2), (int64_t)2 << 30));
   const int64_t budget = o.max_frontier_bytes > 0 ? o.max_frontier_bytes : want;
   R.pool_cap = std::min<int64_t>(std::max<int64_t>(min_pool + 3, (int64_t)(0.6 * budget) / per_v), INT32_MAX / 2);
   R.front_cap = std::min<int64_t>(std::max<int64_t>(min_front + 4, (int64_t)((mixed ? 0.08 : 0.15) * budget) / per_i),

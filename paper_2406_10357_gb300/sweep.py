@@ -4,8 +4,9 @@ orders -- every cascade order of every non-empty subset of {u1, u2, u3, u4} (64 
           paper compares cascades in Section 5), timed on a batch of workload-4 pairs.
 tol    -- runtime against the tolerance, from 1e-1 to 1e-8 relative (the paper's runtime
           versus epsilon study, Section 5), on workloads 2 and 5.
-batch  -- workload 4: the batched call untuned and autotuned (MIXED), against sequential
-          per-pair calls in FP64 at the same tolerance.
+batch  -- workload 4: the batched call untuned and autotuned (MIXED), the host-thread stream
+          path, the batched call in FP64, and sequential per-pair calls in FP64, all at the
+          same tolerance.
 run    -- one workload at its own tolerance: a warm-up call, then timed calls (the command the
           kernel profiles of a workload are taken with).
 
@@ -119,6 +120,10 @@ def sweep_batch(n_pairs: int, tune_pairs: int, reps: int = 2):
 
     arms = [("batched MIXED, untuned", hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED), 1, True),
             ("batched MIXED, autotuned", opt_t, best["leaf_size"], True),
+            ("MIXED single runs on host-thread streams",
+             hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED, flags=hd.HD_FLAG_BATCH_STREAMS), 1,
+             True),
+            ("batched FP64", hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64), 1, True),
             ("sequential per-pair FP64", hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_FP64), 1, False)]
     for name, opt, leaf, batched in arms:
         res = [run(opt, leaf, batched) for _ in range(reps)]
