@@ -213,7 +213,10 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
  * queue holding the items of all pairs, each pair keeps its own l, u, tolerance and status on
  * the device and retires on its own gap, and the host reads one small snapshot per round for
  * the whole batch.  Each pair's bracket has the meaning of its single run's; kernel_launches and
- * d2h_bytes of every result are the batch's totals.  With HD_FLAG_BATCH_STREAMS (or
+ * d2h_bytes of every result are the batch's totals.  All pairs' frontiers and sub-triangle
+ * vertices share buffers sized from the batch (up to half the free device memory unless
+ * opt->max_frontier_bytes is set); pairs still running when those run out are finished
+ * afterwards as single runs, as with HD_FLAG_BATCH_STREAMS.  With HD_FLAG_BATCH_STREAMS (or
  * HD_FLAG_SHARE_MIDPOINTS, which the batched run does not implement), host threads (two per
  * host core, 8 to 64), each with its own non-blocking stream, take the pairs in turn as single
  * runs; they start after the work already queued on `stream`.  Every pair is complete when the

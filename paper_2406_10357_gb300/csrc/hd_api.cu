@@ -137,7 +137,7 @@ static void keep_pool_memory() {
 int run_fp64(const RunIO& io) { return run_bnb<PolicyD>(io); }
 int run_mixed(const RunIO& io);
 int run_batch_mixed(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol, const Opts& o,
-                    cudaStream_t s, hd_result* outs);
+                    cudaStream_t s, hd_result* outs, std::vector<int64_t>* redo);
 
 int nearest_points_fp64(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,
                         int32_t* idx, double* foot, double* dlo) {
@@ -211,6 +211,72 @@ static int hausdorff_one(const hd_bvh* B, const hd_mesh* A, double tol, const hd
   }
   return HD_OK;
 }
+
+// Pairs `todo` as independent single runs.  Pairs are independent: host threads, each with
+// its own non-blocking stream, take pairs in turn, so that the kernels of several small pairs
+// share the GPU (two threads per host core, 8 to 64: each thread spends much of a pair
+// waiting for its stream).  The streams start after the work queued so far on the caller's
+// stream; every pair is complete when the call returns.
+static int streams_batch(const hd_bvh* const* Bs, const hd_mesh* As, const std::vector<int64_t>& todo, double tol,
+                         const hd_options* opt, void* stream, hd_result* outs, int dev) {
+  const int64_t npairs = (int64_t)todo.size();
+  const unsigned cores = std::max(1u, std::thread::hardware_concurrency());
+  const int streams = (int)std::min(64u, std::max(8u, 2 * cores));
+  const int nw = (int)std::min<int64_t>(npairs, streams);
+  cudaEvent_t start;
+  HD_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(start, (cudaStream_t)stream);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(start);
+    return set_cuda_error(e, "cudaEventRecord", __FILE__, __LINE__);
+  }
+  std::atomic<int64_t> next{0};
+  std::atomic<int> fail{HD_OK};
+  std::mutex em;
+  std::string first_err;
+  auto work = [&]() {
+    cudaStream_t s = nullptr;
+    cudaError_t err = cudaSetDevice(dev);
+    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, start, 0);
+    if (err != cudaSuccess) {
+      set_cuda_error(err, "batch stream set-up", __FILE__, __LINE__);
+      int ok = HD_OK;
+      if (fail.compare_exchange_strong(ok, HD_ERR_CUDA)) {
+        std::lock_guard<std::mutex> g(em);
+        first_err = g_err;
+      }
+    }
+    while (err == cudaSuccess && fail.load() == HD_OK) {
+      const int64_t k = next.fetch_add(1);
+      if (k >= npairs) break;
+      const int64_t i = todo[k];
+      int rc = hausdorff_one(Bs[i], &As[i], tol, opt, s, &outs[i], 0.0);
+      if (rc == HD_ERR_INVALID || rc == HD_ERR_CUDA) {
+        int ok = HD_OK;
+        if (fail.compare_exchange_strong(ok, rc)) {
+          std::lock_guard<std::mutex> g(em);
+          first_err = g_err;
+        }
+      }
+    }
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < nw; ++w) pool.emplace_back(work);
+  work();
+  for (auto& t : pool) t.join();
+  cudaEventDestroy(start);
+  if (fail.load() != HD_OK) {
+    snprintf(g_err, sizeof g_err, "%s", first_err.c_str());
+    return fail.load();
+  }
+  return HD_OK;
+}
+
 
 extern "C" {
 
@@ -365,6 +431,7 @@ int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npa
     nF += As[i].nF;
   }
   keep_pool_memory();
+  std::vector<int64_t> todo;
   // the batched run: one launch per phase for all pairs (pool indices of all pairs' vertices
   // and the face enumeration must stay well inside int)
   if (!(o.flags & (HD_FLAG_BATCH_STREAMS | HD_FLAG_SHARE_MIDPOINTS)) && npairs <= INT32_MAX / 4 && nV <= INT32_MAX / 8 &&
@@ -373,68 +440,15 @@ int hd_hausdorff_batched(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npa
       memset(&outs[i], 0, sizeof outs[i]);
       outs[i].status = HD_ERR_INVALID;
     }
-    return o.precision == HD_FP64 ? run_batch<PolicyD>(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs)
-                                  : run_batch_mixed(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs);
+    const int rc = o.precision == HD_FP64 ? run_batch<PolicyD>(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs, &todo)
+                                          : run_batch_mixed(Bs, As, npairs, tol, o, (cudaStream_t)stream, outs, &todo);
+    // pairs the batch's shared buffers could not finish run again on their own below
+    if (rc != HD_OK || todo.empty()) return rc;
+  } else {
+    todo.resize(npairs);
+    for (int64_t i = 0; i < npairs; ++i) todo[i] = i;
   }
-  // Pairs are independent: host threads, each with its own non-blocking stream, take pairs
-  // in turn, so that the kernels of several small pairs share the GPU (two threads per host
-  // core, 8 to 64: each thread spends much of a pair waiting for its stream).  The streams
-  // start after the work queued so far on the caller's stream; every pair is complete when
-  // the call returns.
-  const unsigned cores = std::max(1u, std::thread::hardware_concurrency());
-  const int streams = (int)std::min(64u, std::max(8u, 2 * cores));
-  const int nw = (int)std::min<int64_t>(npairs, streams);
-  cudaEvent_t start;
-  HD_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-  cudaError_t e = cudaEventRecord(start, (cudaStream_t)stream);
-  if (e != cudaSuccess) {
-    cudaEventDestroy(start);
-    return set_cuda_error(e, "cudaEventRecord", __FILE__, __LINE__);
-  }
-  std::atomic<int64_t> next{0};
-  std::atomic<int> fail{HD_OK};
-  std::mutex em;
-  std::string first_err;
-  auto work = [&]() {
-    cudaStream_t s = nullptr;
-    cudaError_t err = cudaSetDevice(dev);
-    if (err == cudaSuccess) err = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(s, start, 0);
-    if (err != cudaSuccess) {
-      set_cuda_error(err, "batch stream set-up", __FILE__, __LINE__);
-      int ok = HD_OK;
-      if (fail.compare_exchange_strong(ok, HD_ERR_CUDA)) {
-        std::lock_guard<std::mutex> g(em);
-        first_err = g_err;
-      }
-    }
-    while (err == cudaSuccess && fail.load() == HD_OK) {
-      int64_t i = next.fetch_add(1);
-      if (i >= npairs) break;
-      int rc = hausdorff_one(Bs[i], &As[i], tol, opt, s, &outs[i], 0.0);
-      if (rc == HD_ERR_INVALID || rc == HD_ERR_CUDA) {
-        int ok = HD_OK;
-        if (fail.compare_exchange_strong(ok, rc)) {
-          std::lock_guard<std::mutex> g(em);
-          first_err = g_err;
-        }
-      }
-    }
-    if (s) {
-      cudaStreamSynchronize(s);
-      cudaStreamDestroy(s);
-    }
-  };
-  std::vector<std::thread> pool;
-  for (int w = 1; w < nw; ++w) pool.emplace_back(work);
-  work();
-  for (auto& t : pool) t.join();
-  cudaEventDestroy(start);
-  if (fail.load() != HD_OK) {
-    snprintf(g_err, sizeof g_err, "%s", first_err.c_str());
-    return fail.load();
-  }
-  return HD_OK;
+  return streams_batch(Bs, As, todo, tol, opt, stream, outs, dev);
 }
 
 int hd_nearest(const hd_bvh* B, const void* P, int32_t ptype, int64_t n, int32_t precision, void* stream,

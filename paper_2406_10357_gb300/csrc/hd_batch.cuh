@@ -720,8 +720,8 @@ static __global__ void k_batch_ctl(BatchCtx x, BatchCtl c, int init, int n_pool0
   long long K = min(c.chunk, (c.pool_cap - (long long)bs->n_pool) / 3);
   K = min(K, (c.front_cap - (long long)bs->n_front) / 3);
   if (s_active == 0 || K <= 0 || bs->overflow) {
-    // done, or out of room: the pairs still running stop with CAPACITY at the next close
-    // (their bracket is the valid one of the last round)
+    // done, or out of room: the pairs still running stop with CAPACITY (their bracket is the
+    // valid one of the last round), marked so that the host can finish them on their own
     if (s_active > 0) {
       for (int p = 0; p < x.npairs; ++p) {
         RunState& st = x.sts[p];
@@ -729,6 +729,7 @@ static __global__ void k_batch_ctl(BatchCtx x, BatchCtl c, int init, int n_pool0
           st.in_round = 0;
           st.status = HD_ERR_CAPACITY;
           st.stop = 1;
+          st.batch_capacity = 1;
         }
       }
     }
@@ -837,7 +838,7 @@ int alloc_batch(BatchBufs<P>& R, const Opts& o, int64_t min_pool, int64_t min_fr
   // All pairs' frontiers and midpoints share these buffers (the pool is not recycled between
   // rounds), so the automatic budget is many times what A's vertices and faces alone need
   // (at least 2 GiB), but at most half the device memory that is free.
-  int64_t want = std::max<int64_t>((int64_t)2 << 30, 16 * (min_pool * per_v + min_front * per_i));
+  int64_t want = std::max<int64_t>((int64_t)2 << 30, 48 * (min_pool * per_v + min_front * per_i));
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && free_b > 0)
     want = std::min<int64_t>(want, std::max<int64_t>((int64_t)(free_b / 2), (int64_t)2 << 30));
@@ -1050,9 +1051,11 @@ int batch_finish_fp64(const BatchCtx& xm, BatchBufs<P>& RM, int64_t n_pro, const
 }
 
 // npairs independent problems in one batched run of policy P (hd_hausdorff_batched).
+// Pairs stopped because the batch's shared buffers ran out (not by their own limits) are
+// listed in *redo, with a valid bracket and status CAPACITY in outs.
 template <class P>
 int run_batch(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol, const Opts& o, cudaStream_t s,
-              hd_result* outs) {
+              hd_result* outs, std::vector<int64_t>* redo) {
   const int np = (int)npairs;
   const long long launches0 = g_launches, d2h0 = g_d2h_bytes;
   if (o.block_size > round_block_limit<P>() || (!P::kFp64 && o.block_size > round_block_limit<PolicyD>()))
@@ -1255,6 +1258,7 @@ int run_batch(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double
       if (P::kFp64 && uret < l) status = HD_ERR_NUMERIC;
     }
     if (status == HD_ERR_INVALID) result = HD_ERR_INVALID;
+    if (h.batch_capacity && redo) redo->push_back(i);
     r.lower = l;
     r.upper = std::max(l, u_run);
     r.status = status;

@@ -27,7 +27,10 @@ namespace hd {
 #endif
 constexpr int kCoopStack = HD_COOP_STACK;  // stack entries per warp (8 bytes each, shared memory)
 constexpr int kCoopWarps = 4;              // warps per block of k_query_long
-constexpr int kCoopMinBlocks = 6;          // resident blocks per SM asked of the compiler (<= 80 registers)
+#ifndef HD_COOP_MIN_BLOCKS
+#define HD_COOP_MIN_BLOCKS 6
+#endif
+constexpr int kCoopMinBlocks = HD_COOP_MIN_BLOCKS;  // resident blocks per SM asked of the compiler (6: <= 80 registers)
 // Triangles a lane's traversal tests before it hands its query to a warp.  The hand-off
 // restarts the traversal from the root with the best triangle found so far as the radius,
 // so a small budget wastes little; most queries finish well within it (a point near B tests

@@ -133,7 +133,7 @@ struct RunState {
   int long_next;                 // work counter of k_query_long
   unsigned long long long_queries;  // queries finished by a whole warp (traverse_coop)
   int tail_rounds;               // rounds the last k_tail_rounds launch ran
-  int pad_;
+  int batch_capacity;            // batched run: stopped because the batch's shared buffers ran out
   unsigned long long node_visits;  // BVH nodes fetched by the traversals (128 bytes each)
   unsigned long long long_node_visits, long_leaf_tests;  // ... of which by k_query_long, and its leaf tests
 };

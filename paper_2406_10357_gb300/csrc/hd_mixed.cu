@@ -8,8 +8,8 @@ namespace hd {
 int run_mixed(const RunIO& io) { return run_bnb<PolicyM>(io); }
 
 int run_batch_mixed(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double tol, const Opts& o,
-                    cudaStream_t s, hd_result* outs) {
-  return run_batch<PolicyM>(Bs, As, npairs, tol, o, s, outs);
+                    cudaStream_t s, hd_result* outs, std::vector<int64_t>* redo) {
+  return run_batch<PolicyM>(Bs, As, npairs, tol, o, s, outs, redo);
 }
 
 int nearest_points_mixed(const hd_bvh* B, const void* Pts, int ptype, int64_t n, cudaStream_t s, double* dist,

@@ -160,3 +160,19 @@ def test_batched_bound_orders(hd, orc, order):
             assert r["status"] in (hd.HD_OK, hd.HD_ERR_CAPACITY), (order, p.name, r)
             ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, 1e-4, hd.HD_TOL_REL, max_face_factor=200)
             assert _meet(r, ro, eps), (order, p.name, r, ro)
+
+
+def test_batched_buffers_exhausted_pairs_finish_on_their_own(hd, orc):
+    """With a budget too small for the whole batch (4 MB shared by all pairs' frontiers and
+    midpoints), the pairs still running when it runs out are finished as single runs (each of
+    which fits the same budget): every pair ends OK, within eps, meeting the oracle's bracket."""
+    pairs = mg.batch_workload(n_pairs=8, lo=300, hi=2000)
+    o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED, max_frontier_bytes=4 << 20)
+    bvhs = [hd.hd_build_B(p.VB, p.FB) for p in pairs]
+    rs = hd.hd_hausdorff_batched(bvhs, [(p.VA, p.FA) for p in pairs], 1e-4, o)
+    for p, r in zip(pairs, rs):
+        eps = 1e-4 * _dA(p.VA, p.FA)
+        assert r["status"] == hd.HD_OK, (p.name, r)
+        assert r["upper"] - r["lower"] <= eps * (1 + 1e-12)
+        ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, 1e-4, hd.HD_TOL_REL, max_face_factor=200)
+        assert _meet(r, ro, eps), (p.name, r, ro)
