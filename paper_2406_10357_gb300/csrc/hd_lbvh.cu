@@ -31,53 +31,69 @@ __device__ inline D3 load_vertex(const T* V, int64_t i) {
   return {(double)V[3 * i], (double)V[3 * i + 1], (double)V[3 * i + 2]};
 }
 
+// A face's three vertices as doubles, or the origin three times when an index is out of range
+// or a coordinate is not finite (B is then invalid and flagged by k_prep; the face becomes a
+// point so that the tree stays finite and every later kernel stays in bounds until the flag
+// is read).
 template <typename T>
-__global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, double* tri_unsorted, float4* cent,
+__device__ inline bool load_face(const T* V, int64_t nV, const int32_t* F, int64_t f, D3& a, D3& b, D3& c) {
+  const int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+  a = b = c = {0, 0, 0};
+  if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV) return false;
+  a = load_vertex(V, i0);
+  b = load_vertex(V, i1);
+  c = load_vertex(V, i2);
+  const bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
+                   isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
+  if (!fin) a = b = c = {0, 0, 0};
+  return fin;
+}
+
+// Validation, the centroids and their bounding box.  Grid-stride, so that the box is reduced
+// per thread, then per block, and ends in one atomic per block and bound.
+template <typename T>
+__global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, float4* cent,
                        unsigned* cbox /*6 ordered floats: min xyz (as ~max), max xyz*/, int* bad) {
   grid_dep_wait();
   grid_dep_launch();
-  int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  __shared__ float part[6][kThreads / 32];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
-  if (f < nF) {
-    int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
-    const bool in_range = !(i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV);
-    D3 a = {0, 0, 0}, b = {0, 0, 0}, c = {0, 0, 0};
-    if (in_range) {
-      a = load_vertex(V, i0);
-      b = load_vertex(V, i1);
-      c = load_vertex(V, i2);
-    }
-    const bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
-                     isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
-    if (!in_range || !fin) {
-      // flagged; the face becomes a point at the origin, so that the tree stays finite and
-      // every later kernel stays in bounds until the flag is read
+  for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nF; f += (int64_t)gridDim.x * blockDim.x) {
+    D3 a, b, c;
+    if (!load_face(V, nV, F, f, a, b, c)) {
       atomicExch(bad, 1);
-      a = b = c = {0, 0, 0};
       cent[f] = make_float4(0.f, 0.f, 0.f, 0.f);
-    } else {
-      D3 m = (1.0 / 3.0) * (a + b + c);
-      lo[0] = hi[0] = (float)m.x;
-      lo[1] = hi[1] = (float)m.y;
-      lo[2] = hi[2] = (float)m.z;
-      cent[f] = make_float4(lo[0], lo[1], lo[2], 0.f);
+      continue;
     }
-    double* t = tri_unsorted + 9 * f;
-    t[0] = a.x; t[1] = a.y; t[2] = a.z;
-    t[3] = b.x; t[4] = b.y; t[5] = b.z;
-    t[6] = c.x; t[7] = c.y; t[8] = c.z;
+    const D3 m = (1.0 / 3.0) * (a + b + c);
+    const float mx = (float)m.x, my = (float)m.y, mz = (float)m.z;
+    lo[0] = fminf(lo[0], mx);
+    lo[1] = fminf(lo[1], my);
+    lo[2] = fminf(lo[2], mz);
+    hi[0] = fmaxf(hi[0], mx);
+    hi[1] = fmaxf(hi[1], my);
+    hi[2] = fmaxf(hi[2], mz);
+    cent[f] = make_float4(mx, my, mz, 0.f);
   }
-  // block reduction of the centroid box, then one atomic per block and axis
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int k = 0; k < 3; ++k) {
     for (int o = 16; o > 0; o >>= 1) {
       lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
       hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
     }
+    if (lane == 0) {
+      part[k][w] = lo[k];
+      part[3 + k][w] = hi[k];
+    }
   }
-  if ((threadIdx.x & 31) == 0 && isfinite(lo[0])) {
-    for (int k = 0; k < 3; ++k) {
-      atomicMin(&cbox[k], float_to_ordered(lo[k]));
-      atomicMax(&cbox[3 + k], float_to_ordered(hi[k]));
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x;
+    float r = k < 3 ? INFINITY : -INFINITY;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) r = k < 3 ? fminf(r, part[k][q]) : fmaxf(r, part[k][q]);
+    if (isfinite(r)) {
+      if (k < 3) atomicMin(&cbox[k], float_to_ordered(r));
+      else atomicMax(&cbox[k], float_to_ordered(r));
     }
   }
 }
@@ -311,16 +327,19 @@ __global__ void k_weld(const T* V, int64_t nV, int* table, unsigned long long ma
 __device__ inline float rd(double x) { return __double2float_rd(x); }
 __device__ inline float ru(double x) { return __double2float_ru(x); }
 
-__global__ void k_gather(const double* tri_unsorted, const int32_t* F, const uint32_t* order, int64_t nF,
-                         const int* canon, int64_t nV, double* tri64, float4* tri32, int4* tri_vid, int* inv,
-                         float4* leafbox /*2 per leaf*/, unsigned* e2_bits) {
+template <typename T>
+__global__ void k_gather(const T* V, const int32_t* F, const uint32_t* order, int64_t nF, const int* canon, int64_t nV,
+                         double* tri64, float4* tri32, int4* tri_vid, int* inv, float4* leafbox /*2 per leaf*/,
+                         unsigned* e2_bits) {
   grid_dep_wait();
   grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   double e2 = 0.0;  // squared distance between a float vertex and its input vertex
   if (i < nF) {
     uint32_t f = order[i];
-    const double* s = tri_unsorted + 9 * (size_t)f;
+    D3 a, b, c;
+    load_face(V, nV, F, f, a, b, c);
+    const double s[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
     double* t = tri64 + 9 * i;
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float4 out[3];
@@ -596,10 +615,10 @@ __global__ void k_build_meta(const unsigned* misc, float* meta) {
 }
 
 template <typename T>
-int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, double* tri_unsorted, float4* cent, unsigned* cbox,
-                int* bad, cudaStream_t s) {
-  launch_chained(k_prep<T>, blocks_for(B->nF, kThreads), kThreads, 0, s, (const T*)V, B->nV, F, B->nF, tri_unsorted, cent, cbox,
-                                                              bad);
+int launch_prep(const hd_mesh* B, const void* V, const int32_t* F, float4* cent, unsigned* cbox, int* bad, int sms,
+                cudaStream_t s) {
+  launch_chained(k_prep<T>, std::min(blocks_for(B->nF, kThreads), (unsigned)sms * 8), kThreads, 0, s, (const T*)V, B->nV,
+                 F, B->nF, cent, cbox, bad);
   HD_TRY_LAUNCH();
   return HD_OK;
 }
@@ -668,7 +687,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     off += (bytes + 255) & ~(size_t)255;
     return at;
   };
-  size_t o_tri = carve(sizeof(double) * 9 * n), o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
+  size_t o_cent = carve(16 * n), o_k0 = carve(8 * n), o_k1 = carve(8 * n), o_v0 = carve(4 * n),
          o_v1 = carve(4 * n), o_hist = carve(4 * 256 * (size_t)nblk), o_leafbox = carve(32 * n),
          o_ibox = carve(32 * n), o_lv = carve(32 * (n + 64)), o_int = carve(4 * 4 * n + 64), o_misc = carve(64),
          o_tot = carve(4 * 256 * kMaxSortPasses);
@@ -679,7 +698,6 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   const size_t o_canon = weld ? carve(4 * (size_t)B->nV) : 0, o_wtab = weld ? carve(4 * weld_entries) : 0;
   char* scratch = nullptr;
   HD_TRY(cudaMallocAsync((void**)&scratch, off, s));
-  double* tri_unsorted = (double*)(scratch + o_tri);
   float4* cent = (float4*)(scratch + o_cent);
   uint64_t* k0 = (uint64_t*)(scratch + o_k0);
   uint64_t* k1 = (uint64_t*)(scratch + o_k1);
@@ -698,8 +716,10 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   TraceScope trace_build(HD_K_BUILD, s);  // the whole build counts as one launch
   HD_TRY(cudaMemsetAsync(misc, 0xff, 3 * sizeof(unsigned), s));
   HD_TRY(cudaMemsetAsync(misc + 3, 0, 5 * sizeof(unsigned), s));
-  int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, tri_unsorted, cent, misc, (int*)(misc + 6), s)
-                              : launch_prep<float>(B, V, F, tri_unsorted, cent, misc, (int*)(misc + 6), s);
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, cent, misc, (int*)(misc + 6), sms, s)
+                              : launch_prep<float>(B, V, F, cent, misc, (int*)(misc + 6), sms, s);
   if (rc != HD_OK) return rc;
   // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
   // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
@@ -739,8 +759,12 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
       launch_chained(k_weld<float>, blocks_for(B->nV, kThreads), kThreads, 0, s, (const float*)V, B->nV, wtab,
                      (unsigned long long)(weld_entries - 1), canon);
   }
-  launch_chained(k_gather, blocks_for(n, kThreads), kThreads, 0, s, tri_unsorted, F, v0, n, (const int*)canon,
-                 (int64_t)B->nV, h->tri64, h->tri32, h->tri_vid, h->inv, leafbox, misc + 7);
+  if (B->vtype == HD_F64)
+    launch_chained(k_gather<double>, blocks_for(n, kThreads), kThreads, 0, s, (const double*)V, F, v0, n,
+                   (const int*)canon, (int64_t)B->nV, h->tri64, h->tri32, h->tri_vid, h->inv, leafbox, misc + 7);
+  else
+    launch_chained(k_gather<float>, blocks_for(n, kThreads), kThreads, 0, s, (const float*)V, F, v0, n,
+                   (const int*)canon, (int64_t)B->nV, h->tri64, h->tri32, h->tri_vid, h->inv, leafbox, misc + 7);
   HD_TRY_LAUNCH();
   if (n > o.leaf_size) {
     launch_chained(k_karras, blocks_for(n - 1, kThreads), kThreads, 0, s, k0, n, left, right, first, last);

@@ -163,13 +163,21 @@ def test_batched_bound_orders(hd, orc, order):
 
 
 def test_batched_buffers_exhausted_pairs_finish_on_their_own(hd, orc):
-    """With a budget too small for the whole batch (4 MB shared by all pairs' frontiers and
-    midpoints), the pairs still running when it runs out are finished as single runs (each of
-    which fits the same budget): every pair ends OK, within eps, meeting the oracle's bracket."""
+    """With a budget (12 MB) that each pair's single run fits but the batch as a whole does not
+    (all pairs' frontiers and midpoints share it), the pairs still running when it runs out are
+    finished as single runs: every pair ends OK, within eps, meeting the oracle's bracket, and
+    some pairs were indeed finished that way (their statistics are their own run's, not the
+    batch's totals)."""
     pairs = mg.batch_workload(n_pairs=8, lo=300, hi=2000)
-    o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED, max_frontier_bytes=4 << 20)
+    o = hd.hd_options_default(tol_mode=hd.HD_TOL_REL, precision=hd.HD_MIXED, max_frontier_bytes=12 << 20)
     bvhs = [hd.hd_build_B(p.VB, p.FB) for p in pairs]
+    single = [hd.hd_hausdorff(b, p.VA, p.FA, 1e-4, o) for p, b in zip(pairs, bvhs)]
+    keep = [i for i, r in enumerate(single) if r["status"] == hd.HD_OK]
+    assert len(keep) >= 6
+    pairs, bvhs = [pairs[i] for i in keep], [bvhs[i] for i in keep]
     rs = hd.hd_hausdorff_batched(bvhs, [(p.VA, p.FA) for p in pairs], 1e-4, o)
+    batch_total = max(r["stats"]["kernel_launches"] for r in rs)
+    assert any(r["stats"]["kernel_launches"] != batch_total for r in rs)  # some pairs were finished singly
     for p, r in zip(pairs, rs):
         eps = 1e-4 * _dA(p.VA, p.FA)
         assert r["status"] == hd.HD_OK, (p.name, r)
