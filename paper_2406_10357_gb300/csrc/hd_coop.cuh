@@ -20,10 +20,10 @@ namespace hd {
 
 // Build-time tunables (measured on GB300: the sliver, large-soup and benchmark workloads).
 #ifndef HD_LONG_BUDGET
-#define HD_LONG_BUDGET 10
+#define HD_LONG_BUDGET 6
 #endif
 #ifndef HD_COOP_STACK
-#define HD_COOP_STACK 512
+#define HD_COOP_STACK 320
 #endif
 #ifndef HD_COOP_SORT
 #define HD_COOP_SORT 0
@@ -31,16 +31,18 @@ namespace hd {
 constexpr int kCoopStack = HD_COOP_STACK;  // stack entries per warp (8 bytes each, shared memory)
 constexpr int kCoopWarps = 4;              // warps per block of k_query_long
 #ifndef HD_COOP_MIN_BLOCKS
-#define HD_COOP_MIN_BLOCKS 8
+#define HD_COOP_MIN_BLOCKS 12
 #endif
-// resident blocks per SM asked of the compiler: 8 blocks of 4 warps (<= 64 registers, 16 KB of
-// stacks each); on the large soup's long queries 8 x 512 entries measured 8% faster than
-// 6 x 768 (more warps in flight to cover the dependent node fetches)
+// resident blocks per SM asked of the compiler: 12 blocks of 4 warps (<= 40 registers, a few
+// values spilled to L1; 10 KB of stacks each).  The traversal waits on dependent node fetches,
+// so warps in flight pay: on the large soup's long queries, blocks x stack entries of 6 x 768,
+// 8 x 512, 10 x 384, 12 x 320 and 16 x 256 took 2.03, 1.86, 1.70, 1.67 and 1.80 ms per call.
 constexpr int kCoopMinBlocks = HD_COOP_MIN_BLOCKS;
 // Triangles a lane's traversal tests before it hands its query to a warp.  The hand-off
 // restarts the traversal from the root with the best triangle found so far as the radius,
 // so a small budget wastes little; most queries finish well within it (a point near B tests
-// a few triangles).
+// a few triangles).  6 against 10 on the large soup: lane pass 0.64 -> 0.55 ms, cooperative
+// pass 1.67 -> 1.72 ms (8% more queries handed off).
 constexpr int kLongBudget = HD_LONG_BUDGET;
 
 __device__ inline float warp_min_f(float v) {

@@ -118,10 +118,14 @@ def main():
         if entry is None:
             print(f"{key}: no oracle bracket within {a.budget} s even with the face cap", flush=True)
             continue
-        table["cases"][key] = entry
         print(key, json.dumps(entry), flush=True)
-        with open(OUT, "w") as f:
+        # merge into the file as it is now (another run of this script may have added entries)
+        table = json.load(open(OUT)) if os.path.exists(OUT) else table
+        table["cases"][key] = entry
+        tmp = OUT + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
             json.dump(table, f, indent=1, sort_keys=True)
+        os.replace(tmp, OUT)
 
 
 def stored(key: str, p):
