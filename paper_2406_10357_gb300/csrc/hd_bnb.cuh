@@ -581,6 +581,79 @@ __device__ inline typename P::UT bound_item(const BvhDev& B, const typename P::V
     return P::upper_bound(B, pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.l, lv.lf, rp, code, c);
 }
 
+// The paper-order cascade with the items that reach u3 gathered into full warps (MIXED).  The
+// exact case, u1 and u2 are cheap and decide many items; u3 costs 4 to 15 point-triangle
+// evaluations.  Run item by item, the lanes whose items were decided early idle while the
+// others evaluate u3.  Here each warp takes batches of 32 items, runs the cheap part on them,
+// and appends the items that still need u3 to its queue in shared memory (64 entries); when 32
+// are waiting, every lane takes one and finishes it, so u3 runs on full warps.  The values and
+// result codes are those of the item-by-item cascade; only the order of the classification
+// changes.  `make(t, it, up)` gives item t (false: no item) and the bound it is clamped to
+// (its parent's U, or +inf).
+struct RebinEntry {
+  int v[3];
+  float u12;  // min(u1, u2)
+  float up;   // clamp
+};
+constexpr int kRebinQueue = 64;  // entries per warp
+inline size_t rebin_smem(int block) { return (size_t)(block / 32) * kRebinQueue * sizeof(RebinEntry); }
+
+template <class P, class Make>
+__device__ inline void bound_rebin(const BvhDev& B, const typename P::Vtx* pool, int64_t count, int* counter,
+                                   const Level<P>& lv, const RunParams& rp, RunState* st, typename P::Item* next,
+                                   int next_cap, typename P::Item* u4list, RebinEntry* q, Counters& c, Tally<P>& ty,
+                                   Make make) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int qn = 0;  // entries waiting in this warp's queue (uniform over the warp)
+  bool more = true;
+  while (more || qn > 0) {
+    if (more && qn < 32) {
+      const int64_t base = warp_batch(counter);
+      if (base >= count) {
+        more = false;
+      } else {
+        const int64_t t = base + lane;
+        bool need = false;
+        RebinEntry e;
+        typename P::Item it;
+        float up = INFINITY;
+        if (t < count && make(t, it, up)) {
+          float U, u12;
+          int code;
+          if (P::paper_cheap(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], lv.lf, rp, &U, &code, &u12)) {
+            need = true;
+            e = RebinEntry{{it.v[0], it.v[1], it.v[2]}, u12, up};
+          } else {
+            it.U = up < U ? up : U;
+            classify<P>(st, it, lv.th, code, next, next_cap, u4list, ty);
+          }
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) q[qn + __popc(m & lt)] = e;
+        qn += __popc(m);
+        __syncwarp();
+      }
+    }
+    if (qn >= 32 || (!more && qn > 0)) {
+      const int take = min(qn, 32);
+      if (lane < take) {
+        const RebinEntry e = q[qn - take + lane];
+        typename P::Item it;
+        it.v[0] = e.v[0];
+        it.v[1] = e.v[1];
+        it.v[2] = e.v[2];
+        int code;
+        const float U = P::paper_u3(B, pool[e.v[0]], pool[e.v[1]], pool[e.v[2]], lv.lf, rp, e.u12, code, c);
+        it.U = e.up < U ? e.up : U;
+        classify<P>(st, it, lv.th, code, next, next_cap, u4list, ty);
+      }
+      qn -= take;
+      __syncwarp();  // the entries taken are read before new ones overwrite them
+    }
+  }
+}
+
 // Round 0: UpperBound for every face of A.
 template <class P, bool kPaper = false>
 __global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* pool, const int32_t* FA, int64_t nFA, RunState* st,
@@ -593,6 +666,21 @@ __global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* poo
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
+  if constexpr (kPaper) {
+    extern __shared__ RebinEntry rebin_q[];
+    bound_rebin<P>(B, pool, nFA, &st->b_next, lv, rp, st, next, next_cap, u4list, rebin_q + (threadIdx.x >> 5) * kRebinQueue,
+                   c, ty, [&](int64_t f, typename P::Item& it, float&) {
+                     it.v[0] = FA[3 * f];
+                     it.v[1] = FA[3 * f + 1];
+                     it.v[2] = FA[3 * f + 2];
+                     // A is validated concurrently: skip bad rows
+                     return it.v[0] >= 0 && it.v[1] >= 0 && it.v[2] >= 0 && it.v[0] < n_pool_valid &&
+                            it.v[1] < n_pool_valid && it.v[2] < n_pool_valid;
+                   });
+    flush_counters(st, c);
+    flush_tally(st, ty);
+    return;
+  }
   for (;;) {
     const int64_t base = warp_batch(&st->b_next);
     if (base >= nFA) break;
@@ -809,6 +897,26 @@ __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
+  if constexpr (kPaper) {
+    extern __shared__ RebinEntry rebin_q[];
+    bound_rebin<P>(B, pool, 4 * (int64_t)S, &st->b_next, lv, rp, st, next, next_cap, u4list,
+                   rebin_q + (threadIdx.x >> 5) * kRebinQueue, c, ty,
+                   [&](int64_t t, typename P::Item& it, float& up) {
+                     const int s = (int)(t >> 2), k = (int)(t & 3);
+                     const int4 par = split_par[s];
+                     const int4 mid = share ? split_mid[s] : make_int4(mbase + 3 * s, mbase + 3 * s + 1, mbase + 3 * s + 2, 0);
+                     if (k == 0) { it.v[0] = par.x; it.v[1] = mid.x; it.v[2] = mid.z; }
+                     else if (k == 1) { it.v[0] = mid.x; it.v[1] = par.y; it.v[2] = mid.y; }
+                     else if (k == 2) { it.v[0] = mid.z; it.v[1] = mid.y; it.v[2] = par.z; }
+                     else { it.v[0] = mid.x; it.v[1] = mid.y; it.v[2] = mid.z; }
+                     // the child lies inside its parent: h(child, B) <= U(parent)
+                     if (rp.parent_clamp) up = __int_as_float(par.w);
+                     return true;
+                   });
+    flush_counters(st, c);
+    flush_tally(st, ty);
+    return;
+  }
   for (;;) {
     const int64_t base = warp_batch(&st->b_next);
     if (base >= 4 * (int64_t)S) break;
@@ -1145,21 +1253,21 @@ int round_block_limit() {
 // Blocks of `bs` threads that fill every SM once with `kernel` (at least one per SM): the
 // grid of the persistent kernels, whose warps take batches of work (warp_batch).
 template <typename K>
-unsigned persistent_grid(K kernel, int bs, int sms) {
+unsigned persistent_grid(K kernel, int bs, int sms, size_t smem = 0) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   return (unsigned)(per_sm * sms);
 }
 
 // persistent_grid, remembered per block size (32 to 1024 threads, a multiple of 32).
 template <typename K>
-unsigned persistent_grid_bs(K kernel, int bs, std::atomic<unsigned> (&cache)[33]) {
+unsigned persistent_grid_bs(K kernel, int bs, std::atomic<unsigned> (&cache)[33], size_t smem = 0) {
   unsigned g = cache[bs / 32].load(std::memory_order_relaxed);
   if (!g) {
     int dev = 0, sms = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g = persistent_grid(kernel, bs, sms);
+    g = persistent_grid(kernel, bs, sms, smem);
     cache[bs / 32].store(g, std::memory_order_relaxed);
   }
   return g;
@@ -1335,7 +1443,9 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
   static std::atomic<unsigned> grid_b_cache[2][33];
   const bool paper = paper_cascade(rp);
   const auto k_children = bound_children_kernel<P>(paper);
-  const unsigned grid_q = query_grid<P>(bs), grid_b = persistent_grid_bs(k_children, bs, grid_b_cache[paper ? 1 : 0]);
+  const size_t smem_b = rebin_smem(bs);  // the u3 queues of the paper-order kernels
+  const unsigned grid_q = query_grid<P>(bs),
+                 grid_b = persistent_grid_bs(k_children, bs, grid_b_cache[paper ? 1 : 0], smem_b);
   const unsigned grid_long = long_grid<P>();
   int64_t front_bound = first_front_bound;  // the first round is queued without a wait
   int cur = R.cur;
@@ -1373,7 +1483,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      launch_chained(k_children, g_b, bs, 0, s, B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1],
+      launch_chained(k_children, g_b, bs, smem_b, s, B, R.pool, R.split_par, R.split_mid, st, rp, R.front[cur ^ 1],
                      (int)R.front_cap, R.u4list);
       if (R.u4list)
         launch_chained(k_bound_u4<P>, g_u4, bs, 0, s, B, R.pool, R.u4list, (int)R.front_cap, st, rp, R.front[cur ^ 1],
@@ -1627,7 +1737,8 @@ int run_bnb(const RunIO& io) {
   {
     TraceScope tr(HD_K_BOUND, s);
     const auto k_faces = bound_faces_kernel<P>(paper_cascade(rp));
-    launch_chained(k_faces, std::min(blocks_for(io.nFA, bs), persistent_grid(k_faces, bs, sms)), bs, 0, s, 
+    launch_chained(k_faces, std::min(blocks_for(io.nFA, bs), persistent_grid(k_faces, bs, sms, rebin_smem(bs))), bs,
+                   rebin_smem(bs), s, 
         B, R.pool, io.FA, io.nFA, st, rp, R.front[1],
                                                            (int)R.front_cap, R.u4list, io.nVA);
     if (R.u4list)

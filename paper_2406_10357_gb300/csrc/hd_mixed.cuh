@@ -969,6 +969,52 @@ struct PolicyM {
                      {pos(c), c.dhi, c.tri, {0.f, 0.f, 0.f}, 0.f}};
     return upper_bound_m_paper(B, t, lf, rp, code, cnt);
   }
+  // The paper-order cascade in two parts, for kernels that gather the items reaching u3 into
+  // full warps: paper_cheap runs the exact case, u1 and u2; it returns true when u3 is still
+  // needed (U so far in *u12), else the result in *U and *code as upper_bound_paper.
+  // paper_u3 then finishes such an item; together they give upper_bound_paper's values.
+  __device__ static bool paper_cheap(const Vtx& a, const Vtx& b, const Vtx& c, float lf, const RunParams& rp,
+                                     float* U, int* code, float* u12) {
+    const VM t[3] = {{pos(a), a.dhi, a.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(b), b.dhi, b.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(c), c.dhi, c.tri, {0.f, 0.f, 0.f}, 0.f}};
+    if (t[0].I == t[1].I && t[1].I == t[2].I) {
+      *code = 0;
+      *U = __fadd_ru(fmaxf(t[0].dhi, fmaxf(t[1].dhi, t[2].dhi)), rp.slack_f);
+      return false;
+    }
+    const EdgesM E(t);
+    const float u1 = ubm_u1(t, E);
+    if (u1 < lf) {
+      *code = 1;
+      *U = __fadd_ru(u1, rp.slack_f);
+      return false;
+    }
+    const float u2 = ubm_u2(t, E);
+    if (u2 < lf) {
+      *code = 2;
+      *U = __fadd_ru(u2, rp.slack_f);
+      return false;
+    }
+    *u12 = fminf(u1, u2);
+    return true;
+  }
+  __device__ static UT paper_u3(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, float lf, const RunParams& rp,
+                                float u12, int& code, Counters& cnt) {
+    const VM t[3] = {{pos(a), a.dhi, a.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(b), b.dhi, b.tri, {0.f, 0.f, 0.f}, 0.f},
+                     {pos(c), c.dhi, c.tri, {0.f, 0.f, 0.f}, 0.f}};
+    const float u3 = ubm_u3(B, t, lf, cnt.evals);
+    float U;
+    if (u3 < lf) {
+      code = 3;
+      U = u3;
+    } else {
+      code = kDeferU4;
+      U = fminf(u12, u3);
+    }
+    return __fadd_ru(U, rp.slack_f);
+  }
   __device__ static UT upper_bound(const BvhDev& B, const Vtx& a, const Vtx& b, const Vtx& c, double,
                                    float lf, const RunParams& rp, int& code, Counters& cnt) {
     VM t[3] = {{pos(a), a.dhi, a.tri, {a.qx, a.qy, a.qz}, a.qerr},
