@@ -411,6 +411,85 @@ __global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks)
 
 // ----------------------------------------------------------------------------- bounds
 
+// The paper-order cascade with the items that reach u3 gathered into full warps, as
+// bound_rebin of a single run, each item with its pair.  `make(t, it, up)` gives item t's
+// vertices and clamp and returns its pair (-1: no item).
+struct BatchRebinEntry {
+  int v[3];
+  float u12;
+  float up;
+  int pair;
+};
+inline size_t batch_rebin_smem(int block) { return (size_t)(block / 32) * kRebinQueue * sizeof(BatchRebinEntry); }
+
+template <class P, class Make>
+__device__ inline void batch_bound_rebin(const BatchCtx& x, const typename P::Vtx* pool, int64_t count, int* counter,
+                                         typename P::Item* next, int* next_pair, int next_cap, typename P::Item* u4list,
+                                         int* u4_pair, BatchRebinEntry* q, Make make) {
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int qn = 0;
+  bool more = true;
+  while (more || qn > 0) {
+    if (more && qn < 32) {
+      const int64_t base = warp_batch(counter);
+      if (base >= count) {
+        more = false;
+      } else {
+        const int64_t t = base + lane;
+        bool need = false;
+        BatchRebinEntry e;
+        typename P::Item it;
+        float up = INFINITY;
+        int p = -1;
+        PairTally<P> ty;
+        if (t < count) p = make(t, it, up);
+        if (p >= 0) {
+          const PairLevel<P> pl = pair_level<P>(x, p);
+          float U, u12;
+          int code;
+          if (P::paper_cheap(pool[it.v[0]], pool[it.v[1]], pool[it.v[2]], pl.lv.lf, pl.rp, &U, &code, &u12)) {
+            need = true;
+            e = BatchRebinEntry{{it.v[0], it.v[1], it.v[2]}, u12, up, p};
+          } else {
+            it.U = up < U ? up : U;
+            classify_pair<P>(x.bs, it, p, pl.lv.th, code, next, next_pair, next_cap, u4list, u4_pair, ty);
+          }
+        }
+        flush_tally_pair<P>(x.sts, need ? -1 : p, ty);
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        if (need) q[qn + __popc(m & lt)] = e;
+        qn += __popc(m);
+        __syncwarp();
+      }
+    }
+    if (qn >= 32 || (!more && qn > 0)) {
+      const int take = min(qn, 32);
+      int p = -1;
+      Counters cnt;
+      PairTally<P> ty;
+      if (lane < take) {
+        const BatchRebinEntry e = q[qn - take + lane];
+        p = e.pair;
+        typename P::Item it;
+        it.v[0] = e.v[0];
+        it.v[1] = e.v[1];
+        it.v[2] = e.v[2];
+        const PairLevel<P> pl = pair_level<P>(x, p);
+        int code;
+        const float U =
+            P::paper_u3(x.pd[p].B, pool[e.v[0]], pool[e.v[1]], pool[e.v[2]], pl.lv.lf, pl.rp, e.u12, code, cnt);
+        it.U = e.up < U ? e.up : U;
+        classify_pair<P>(x.bs, it, p, pl.lv.th, code, next, next_pair, next_cap, u4list, u4_pair, ty);
+      }
+      qn -= take;
+      __syncwarp();  // the entries taken are read before new ones overwrite them
+      flush_counters_pair(x.sts, p, cnt);
+      flush_tally_pair<P>(x.sts, p, ty);
+    }
+  }
+}
+
 // UpperBound of the round-0 items: every face of every pair (tri == nullptr), or n given
 // index triples with their pairs (the promoted items of the FP64 phase).
 template <class P, bool kPaper = false>
@@ -421,6 +500,29 @@ __global__ void HD_BOUND_REGS k_batch_bound_faces(BatchCtx x, const typename P::
   grid_dep_launch();
   BatchState* bs = x.bs;
   const int count = tri ? n : x.nF;
+  if constexpr (kPaper && HD_REBIN) {
+    extern __shared__ BatchRebinEntry batch_rebin_q[];
+    batch_bound_rebin<P>(x, pool, count, &bs->b_next, next, next_pair, next_cap, u4list, u4_pair,
+                         batch_rebin_q + (threadIdx.x >> 5) * kRebinQueue,
+                         [&](int64_t f, typename P::Item& it, float&) -> int {
+                           if (tri) {
+                             it.v[0] = tri[3 * f];
+                             it.v[1] = tri[3 * f + 1];
+                             it.v[2] = tri[3 * f + 2];
+                             return tri_pair[f];
+                           }
+                           const int p = find_pair(x.fbase, x.npairs, (int)f);
+                           const PairDev& d = x.pd[p];
+                           const int32_t* F = d.FA + 3 * (int64_t)(f - x.fbase[p]);
+                           const int a = F[0], b = F[1], c = F[2];
+                           if (!(a >= 0 && b >= 0 && c >= 0 && a < d.nVA && b < d.nVA && c < d.nVA)) return -1;
+                           it.v[0] = d.vbase + a;
+                           it.v[1] = d.vbase + b;
+                           it.v[2] = d.vbase + c;
+                           return p;
+                         });
+    return;
+  }
   for (;;) {
     const int base = warp_batch(&bs->b_next);
     if (base >= count) break;
@@ -603,6 +705,25 @@ __global__ void HD_BOUND_REGS k_batch_bound_children(BatchCtx x, const typename 
   if (bs->stop) return;
   const int mbase = bs->n_pool;
   const int S = min(*(volatile int*)&bs->n_split, bs->K);
+  if constexpr (kPaper && HD_REBIN) {
+    extern __shared__ BatchRebinEntry batch_rebin_q[];
+    batch_bound_rebin<P>(x, pool, 4 * (int64_t)S, &bs->b_next, next, next_pair, next_cap, u4list, u4_pair,
+                         batch_rebin_q + (threadIdx.x >> 5) * kRebinQueue,
+                         [&](int64_t t, typename P::Item& it, float& up) -> int {
+                           const int s = (int)(t >> 2), k = (int)(t & 3);
+                           const int p = split_pair[s];
+                           if (p < 0) return -1;
+                           const int4 par = split_par[s];
+                           const int m12 = mbase + 3 * s, m23 = m12 + 1, m31 = m12 + 2;
+                           if (k == 0) { it.v[0] = par.x; it.v[1] = m12; it.v[2] = m31; }
+                           else if (k == 1) { it.v[0] = m12; it.v[1] = par.y; it.v[2] = m23; }
+                           else if (k == 2) { it.v[0] = m31; it.v[1] = m23; it.v[2] = par.z; }
+                           else { it.v[0] = m12; it.v[1] = m23; it.v[2] = m31; }
+                           if (x.rp.parent_clamp) up = __int_as_float(par.w);
+                           return p;
+                         });
+    return;
+  }
   for (;;) {
     const int64_t base = warp_batch(&bs->b_next);
     if (base >= 4 * (int64_t)S) break;
@@ -905,9 +1026,9 @@ inline int batch_host_res(BatchHostRes*& out) {
 
 // Persistent grid of a kernel at block size bs (cached per kernel and block size).
 template <typename K>
-unsigned batch_grid(K kernel, int bs, int sms) {
+unsigned batch_grid(K kernel, int bs, int sms, size_t smem = 0) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, bs, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
   return (unsigned)(per_sm * sms);
 }
 
@@ -926,7 +1047,8 @@ int batch_rounds(const BatchCtx& x, BatchBufs<P>& R, const BatchCtl& c, int n_po
   }
   const bool paper = !P::kFp64 && paper_cascade(x.rp);
   auto k_children = batch_children_kernel<P>(paper);
-  const unsigned g_q = batch_grid(k_batch_query<P>, bs_, sms), g_b = batch_grid(k_children, bs_, sms);
+  const size_t smem_b = batch_rebin_smem(bs_);  // the u3 queues of the paper-order kernels
+  const unsigned g_q = batch_grid(k_batch_query<P>, bs_, sms), g_b = batch_grid(k_children, bs_, sms, smem_b);
   const unsigned g_long = batch_grid(k_batch_query_long<P>, 32 * kCoopWarps, sms);
   const unsigned g_sel = (unsigned)sms * 8, g_u4 = (unsigned)sms * 8;
   int cur = 1;
@@ -950,7 +1072,7 @@ int batch_rounds(const BatchCtx& x, BatchBufs<P>& R, const BatchCtl& c, int n_po
     }
     {
       TraceScope tr(HD_K_BOUND, s);
-      launch_chained(k_children, g_b, bs_, 0, s, x, R.pool, R.split_par, (const int*)R.split_pair, R.front[cur ^ 1],
+      launch_chained(k_children, g_b, bs_, smem_b, s, x, R.pool, R.split_par, (const int*)R.split_pair, R.front[cur ^ 1],
                      R.front_pair[cur ^ 1], (int)R.front_cap, R.u4list, R.u4_pair);
       if (R.u4list)
         launch_chained(k_batch_bound_u4<P>, g_u4, bs_, 0, s, x, R.pool, R.u4list, (const int*)R.u4_pair, (int)R.front_cap,
@@ -1188,7 +1310,8 @@ int run_batch(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double
   {
     TraceScope tr(HD_K_BOUND, s);
     auto k_faces = batch_faces_kernel<P>(paper);
-    launch_chained(k_faces, std::min(blocks_for(nF, bsz), batch_grid(k_faces, bsz, sms)), bsz, 0, s, x,
+    launch_chained(k_faces, std::min(blocks_for(nF, bsz), batch_grid(k_faces, bsz, sms, batch_rebin_smem(bsz))), bsz,
+                   batch_rebin_smem(bsz), s, x,
                    (const typename P::Vtx*)R.pool, (const int32_t*)nullptr, (const int*)nullptr, 0, R.front[1],
                    R.front_pair[1], (int)R.front_cap, R.u4list, R.u4_pair);
     if (R.u4list)

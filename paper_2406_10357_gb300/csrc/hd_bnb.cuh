@@ -590,6 +590,9 @@ __device__ inline typename P::UT bound_item(const BvhDev& B, const typename P::V
 // result codes are those of the item-by-item cascade; only the order of the classification
 // changes.  `make(t, it, up)` gives item t (false: no item) and the bound it is clamped to
 // (its parent's U, or +inf).
+#ifndef HD_REBIN
+#define HD_REBIN 1
+#endif
 struct RebinEntry {
   int v[3];
   float u12;  // min(u1, u2)
@@ -666,7 +669,7 @@ __global__ void HD_BOUND_REGS k_bound_faces(BvhDev B, const typename P::Vtx* poo
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
-  if constexpr (kPaper) {
+  if constexpr (kPaper && HD_REBIN) {
     extern __shared__ RebinEntry rebin_q[];
     bound_rebin<P>(B, pool, nFA, &st->b_next, lv, rp, st, next, next_cap, u4list, rebin_q + (threadIdx.x >> 5) * kRebinQueue,
                    c, ty, [&](int64_t f, typename P::Item& it, float&) {
@@ -897,7 +900,7 @@ __device__ inline void bound_children_body(BvhDev B, const typename P::Vtx* pool
   const Thresholds<P>& th = lv.th;
   Counters c;
   Tally<P> ty;
-  if constexpr (kPaper) {
+  if constexpr (kPaper && HD_REBIN) {
     extern __shared__ RebinEntry rebin_q[];
     bound_rebin<P>(B, pool, 4 * (int64_t)S, &st->b_next, lv, rp, st, next, next_cap, u4list,
                    rebin_q + (threadIdx.x >> 5) * kRebinQueue, c, ty,
