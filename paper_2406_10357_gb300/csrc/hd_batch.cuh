@@ -420,7 +420,9 @@ struct BatchRebinEntry {
   float up;
   int pair;
 };
-inline size_t batch_rebin_smem(int block) { return (size_t)(block / 32) * kRebinQueue * sizeof(BatchRebinEntry); }
+inline size_t batch_rebin_smem(int block) {
+  return HD_BATCH_REBIN ? (size_t)(block / 32) * kRebinQueue * sizeof(BatchRebinEntry) : 0;
+}
 
 template <class P, class Make>
 __device__ inline void batch_bound_rebin(const BatchCtx& x, const typename P::Vtx* pool, int64_t count, int* counter,
@@ -500,7 +502,7 @@ __global__ void HD_BOUND_REGS k_batch_bound_faces(BatchCtx x, const typename P::
   grid_dep_launch();
   BatchState* bs = x.bs;
   const int count = tri ? n : x.nF;
-  if constexpr (kPaper && HD_REBIN) {
+  if constexpr (kPaper && HD_BATCH_REBIN) {
     extern __shared__ BatchRebinEntry batch_rebin_q[];
     batch_bound_rebin<P>(x, pool, count, &bs->b_next, next, next_pair, next_cap, u4list, u4_pair,
                          batch_rebin_q + (threadIdx.x >> 5) * kRebinQueue,
@@ -705,7 +707,7 @@ __global__ void HD_BOUND_REGS k_batch_bound_children(BatchCtx x, const typename 
   if (bs->stop) return;
   const int mbase = bs->n_pool;
   const int S = min(*(volatile int*)&bs->n_split, bs->K);
-  if constexpr (kPaper && HD_REBIN) {
+  if constexpr (kPaper && HD_BATCH_REBIN) {
     extern __shared__ BatchRebinEntry batch_rebin_q[];
     batch_bound_rebin<P>(x, pool, 4 * (int64_t)S, &bs->b_next, next, next_pair, next_cap, u4list, u4_pair,
                          batch_rebin_q + (threadIdx.x >> 5) * kRebinQueue,
