@@ -184,3 +184,19 @@ def test_batched_buffers_exhausted_pairs_finish_on_their_own(hd, orc):
         assert r["upper"] - r["lower"] <= eps * (1 + 1e-12)
         ro = orc.hausdorff(p.VA, p.FA, p.VB, p.FB, 1e-4, hd.HD_TOL_REL, max_face_factor=200)
         assert _meet(r, ro, eps), (p.name, r, ro)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_batched_one_pair_equals_single_run(hd, orc, precision):
+    """A batch of one pair: the same bracket, status and counts as the single run (the same
+    items are split in the same rounds), and an empty batch returns at once."""
+    p = mg.workload(2, 0.02)
+    prec = hd.HD_MIXED if precision == "mixed" else hd.HD_FP64
+    o = hd.hd_options_default(tol_mode=p.tol_mode, precision=prec, flags=hd.HD_FLAG_NO_SMALL_ROUNDS)
+    bvh = hd.hd_build_B(p.VB, p.FB)
+    (r,) = hd.hd_hausdorff_batched([bvh], [(p.VA, p.FA)], p.tol, o)
+    r1 = hd.hd_hausdorff(bvh, p.VA, p.FA, p.tol, o)
+    assert (r["lower"], r["upper"], r["status"]) == (r1["lower"], r1["upper"], r1["status"])
+    for k in ("rounds", "splits", "queries", "retired", "promoted"):
+        assert r["stats"][k] == r1["stats"][k], k
+    assert hd.hd_hausdorff_batched([], [], p.tol, o) == []
