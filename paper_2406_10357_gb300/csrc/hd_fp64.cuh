@@ -94,6 +94,7 @@ __device__ inline bool traverse(const BvhDev& B, D3 p, Test& test, Counters& c, 
 struct NearestD {
   D3 p;
   const double* tri64;
+  const float4* tri32;
   double best2 = INFINITY;
   int best = -1;
   D3 q = {0, 0, 0};
@@ -102,7 +103,7 @@ struct NearestD {
   __device__ float coop_r2() const { return __double2float_ru(best2); }
   __device__ void test1(int j) {
     D3 a, b, c;
-    load_tri64(tri64, j, a, b, c);
+    load_tri_d(tri64, tri32, j, a, b, c);
     D3 x = closest_on_triangle(p, a, b, c);
     D3 e = p - x;
     double d2 = dot(e, e);
@@ -120,7 +121,7 @@ struct NearestD {
 
 __device__ inline double dist_to_tri64(const BvhDev& B, int j, D3 x) {
   D3 a, b, c;
-  load_tri64(B.tri64, j, a, b, c);
+  load_tri_d(B.tri64, B.tri32, j, a, b, c);
   return len(x - closest_on_triangle(x, a, b, c));
 }
 
@@ -193,8 +194,12 @@ __device__ inline bool shared_edge(const BvhDev& B, int f, int g, int& fs0, int&
 }
 
 __device__ inline D3 tri_vertex(const BvhDev& B, int j, int slot) {
-  const double* t = B.tri64 + 9 * (size_t)j + 3 * slot;
-  return {t[0], t[1], t[2]};
+  if (B.tri64) {
+    const double* t = B.tri64 + 9 * (size_t)j + 3 * slot;
+    return {t[0], t[1], t[2]};
+  }
+  const float4 v = __ldg(B.tri32 + 3 * (size_t)j + slot);
+  return {v.x, v.y, v.z};
 }
 
 // Kang et al. 2018 bound, Eqs. (Kang2018_case1) and (Kang2018_case2).
@@ -346,6 +351,7 @@ struct PolicyD {
     NearestD t;
     t.p = {v.x, v.y, v.z};
     t.tri64 = B.tri64;
+    t.tri32 = B.tri32;
     if (v.hint >= 0) t.test1(v.hint);
     const bool finished = traverse(B, t.p, t, c, budget);
     c.leaf += t.evals;
@@ -371,6 +377,7 @@ struct PolicyD {
     NearestD t;
     t.p = {v.x, v.y, v.z};
     t.tri64 = B.tri64;
+    t.tri32 = B.tri32;
     if (lane == 0 && v.hint >= 0) {  // the lane traversal's best so far
       t.best = v.hint;
       t.best2 = v.d;

@@ -53,7 +53,8 @@ struct hd_bvh {
   void* block;         // one stream-ordered allocation; the arrays below are carved from it
   hd::BvhNode* nodes;  // n_nodes
   float4* tri32;       // 3 per triangle: a.xyz|orig-index-bits, b.xyz|0, c.xyz|0 (RN of input)
-  double* tri64;       // 9 per triangle: a, b, c (exact input values)
+  double* tri64;       // 9 per triangle: a, b, c (exact input values); null for float32 input,
+                       // whose values tri32 holds exactly
   int4* tri_vid;       // per triangle: the F_B row (vertex indices) and the original face index
   int* inv;            // original face index -> sorted position
   float eta;           // max distance between a float vertex of tri32 and its input value (0 for f32
@@ -142,7 +143,7 @@ struct RunState {
 struct BvhDev {
   const BvhNode* nodes;
   const float4* tri32;
-  const double* tri64;
+  const double* tri64;  // null for float32 input (tri32 is exact then)
   const int4* tri_vid;
   int64_t nF;
   const float* meta;  // [0] eta: max distance between a float vertex of tri32 and its input
@@ -322,11 +323,21 @@ __device__ inline D3 closest_on_triangle(D3 p, D3 a, D3 b, D3 c) {
   return dot(p - qe, p - qe) < e ? qe : q;
 }
 
-__device__ inline void load_tri64(const double* tri64, int i, D3& a, D3& b, D3& c) {
-  const double* t = tri64 + 9 * (size_t)i;
-  a = {t[0], t[1], t[2]};
-  b = {t[3], t[4], t[5]};
-  c = {t[6], t[7], t[8]};
+// Triangle i of B in double: the exact input values (tri64, float64 input) or, for float32
+// input, which tri32 holds exactly, its float vertices widened (tri64 is not kept then).
+__device__ inline void load_tri_d(const double* tri64, const float4* tri32, int i, D3& a, D3& b, D3& c) {
+  if (tri64) {
+    const double* t = tri64 + 9 * (size_t)i;
+    a = {t[0], t[1], t[2]};
+    b = {t[3], t[4], t[5]};
+    c = {t[6], t[7], t[8]};
+    return;
+  }
+  const float4* t = tri32 + 3 * (size_t)i;
+  const float4 x = __ldg(t), y = __ldg(t + 1), z = __ldg(t + 2);
+  a = {x.x, x.y, x.z};
+  b = {y.x, y.y, y.z};
+  c = {z.x, z.y, z.z};
 }
 
 // Squared distance from p to an axis-aligned box (0 inside).

@@ -340,14 +340,14 @@ __global__ void k_gather(const T* V, const int32_t* F, const uint32_t* order, in
     D3 a, b, c;
     load_face(V, nV, F, f, a, b, c);
     const double s[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
-    double* t = tri64 + 9 * i;
+    double* t = tri64 ? tri64 + 9 * i : nullptr;  // null: float32 input, not kept
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float4 out[3];
     for (int v = 0; v < 3; ++v) {
       float c[3];
       for (int k = 0; k < 3; ++k) {
         double x = s[3 * v + k];
-        t[3 * v + k] = x;
+        if (t) t[3 * v + k] = x;
         lo[k] = fminf(lo[k], rd(x));
         hi[k] = fmaxf(hi[k], ru(x));
         c[k] = (float)x;
@@ -657,8 +657,10 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   {
     // the BVH's own arrays: one allocation from the device's stream-ordered pool
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    // the FP64 copy of the triangles only for float64 input (tri32 holds float32 input exactly)
     const size_t b_nodes = up(sizeof(BvhNode) * h->n_nodes), b_t32 = up(sizeof(float4) * 3 * n),
-                 b_t64 = up(sizeof(double) * 9 * n), b_vid = up(sizeof(int4) * n), b_inv = up(sizeof(int) * n),
+                 b_t64 = h->input_f64 ? up(sizeof(double) * 9 * n) : 0, b_vid = up(sizeof(int4) * n),
+                 b_inv = up(sizeof(int) * n),
                  b_meta = up(4 * sizeof(float));
     cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta, s);
     if (e != cudaSuccess) {
@@ -668,7 +670,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     char* c = (char*)h->block;
     h->nodes = (BvhNode*)c;
     h->tri32 = (float4*)(c + b_nodes);
-    h->tri64 = (double*)(c + b_nodes + b_t32);
+    h->tri64 = h->input_f64 ? (double*)(c + b_nodes + b_t32) : nullptr;
     h->tri_vid = (int4*)(c + b_nodes + b_t32 + b_t64);
     h->inv = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid);
     h->meta = (float*)(c + b_nodes + b_t32 + b_t64 + b_vid + b_inv);
