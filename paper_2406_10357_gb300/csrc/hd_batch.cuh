@@ -361,7 +361,7 @@ __global__ void HD_QUERY_REGS k_batch_query(BatchCtx x, typename P::Vtx* pool, c
     Counters c;
     bool over = false;
     const BvhDev B = x.pd[q ? p : 0].B;
-    P::query(B, v, c, q, ll.idx ? kLongBudget : INT_MAX, &over);
+    P::query(B, v, c, q, ll.idx ? P::kLongBudget : INT_MAX, &over);
     double lmax = 0.0;
     int nq = 0;
     if (q) {
@@ -383,7 +383,7 @@ __global__ void HD_QUERY_REGS k_batch_query(BatchCtx x, typename P::Vtx* pool, c
 
 // The handed-off queries, one warp each (traverse_coop), with their pair's BVH.
 template <class P>
-__global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks)
+__global__ void __launch_bounds__(32 * kCoopWarps, P::kCoopBlocks)
     k_batch_query_long(BatchCtx x, typename P::Vtx* pool, const int* vpair, LongList ll, bool round_midpoints) {
   __shared__ unsigned s_code[kCoopWarps * kCoopStack];
   __shared__ float s_e[kCoopWarps * kCoopStack];

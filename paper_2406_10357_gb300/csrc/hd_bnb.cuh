@@ -294,7 +294,7 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
     }
     bool q = active && v.tri != -1;
     bool over = false;
-    P::query(B, v, c, q, ll.idx ? kLongBudget : INT_MAX, &over);
+    P::query(B, v, c, q, ll.idx ? P::kLongBudget : INT_MAX, &over);
     if (q) {
       pool[beg + t] = v;
       if (over) {
@@ -377,7 +377,7 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
 }
 
 template <class P>
-__global__ void __launch_bounds__(32 * kCoopWarps, kCoopMinBlocks) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
+__global__ void __launch_bounds__(32 * kCoopWarps, P::kCoopBlocks) k_query_long(BvhDev B, typename P::Vtx* pool, LongList ll,
                                                                 RunState* st, double slack_in, const DynParams* dyn,
                                                                 bool round_midpoints) {
   __shared__ unsigned s_code[kCoopWarps * kCoopStack];
@@ -1103,6 +1103,10 @@ static __global__ void k_round_ctl(RunState* st, RoundCtl c, int init, int n_poo
 // any frontier is correct.
 constexpr int kTailThreads = 256;
 constexpr int kTailWarps = kTailThreads / 32;
+#ifndef HD_TAIL_LONG
+#define HD_TAIL_LONG kTailWarps
+#endif
+constexpr int kTailLong = HD_TAIL_LONG;  // most long queries a round may hand off and stay in the small-round kernel
 constexpr int kTailFront = 64;
 constexpr size_t kTailSmem = (sizeof(unsigned) + sizeof(float)) * kTailWarps * kCoopStack;
 
@@ -1135,7 +1139,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_rounds(BvhDev B, TailBufs
   for (;;) {
     if (threadIdx.x == 0) {
       // the control step of k_round_ctl, refusing to open a round over kTailFront items
-      round_ctl_body(st, c, init, n_pool0, kTailFront, kTailWarps);
+      round_ctl_body(st, c, init, n_pool0, kTailFront, kTailLong);
       s_go = !st->stop && st->in_round;
     }
     init = 0;
@@ -1523,7 +1527,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     const long long ahead = seen >= HD_AHEAD_FROM ? 2 : 1;  // rounds in flight, the one being read included
     while (issued < seen + ahead && tail_at < 0) {
       int rc;
-      if (front_bound <= kTailFront && last_long <= kTailWarps && !(o.flags & HD_FLAG_NO_SMALL_ROUNDS)) {
+      if (front_bound <= kTailFront && last_long <= kTailLong && !(o.flags & HD_FLAG_NO_SMALL_ROUNDS)) {
         rc = issue_tail((int)(issued & 1));
         tail_at = issued;
       } else {

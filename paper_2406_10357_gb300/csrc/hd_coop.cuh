@@ -48,6 +48,15 @@ constexpr int kCoopWarps = 4;              // warps per block of k_query_long
 // so warps in flight pay: on the large soup's long queries, blocks x stack entries of 6 x 768,
 // 8 x 512, 10 x 384, 12 x 320 and 16 x 256 took 2.03, 1.86, 1.70, 1.67 and 1.80 ms per call.
 constexpr int kCoopMinBlocks = HD_COOP_MIN_BLOCKS;
+// The FP64 policy's cooperative traversal keeps doubles in flight (its query point, the best
+// squared distance and closest point, the triangle being tested): at 40 registers it spills
+// heavily, so it asks for fewer blocks per SM, and its lanes keep their queries longer.
+#ifndef HD_COOP_MIN_BLOCKS_D
+#define HD_COOP_MIN_BLOCKS_D 6
+#endif
+#ifndef HD_LONG_BUDGET_D
+#define HD_LONG_BUDGET_D 10
+#endif
 // Triangles a lane's traversal tests before it hands its query to a warp.  The hand-off
 // restarts the traversal from the root with the best triangle found so far as the radius,
 // so a small budget wastes little; most queries finish well within it (a point near B tests

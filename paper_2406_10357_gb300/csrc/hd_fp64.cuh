@@ -340,6 +340,8 @@ struct PolicyD {
   using Item = ItemD;
   using UT = double;
   static constexpr bool kFp64 = true;
+  static constexpr int kCoopBlocks = HD_COOP_MIN_BLOCKS_D;  // resident blocks per SM of the cooperative traversal
+  static constexpr int kLongBudget = HD_LONG_BUDGET_D;      // triangle tests of a lane before the hand-off
   static constexpr int kBoundRegs = HD_FP64_BOUND_REGS;  // register cap of the UpperBound kernels
 
   // Nearest triangle of v.  With `over` given, a traversal that tests more than `budget`

@@ -23,6 +23,9 @@ namespace hd {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef HD_KEEP_TRI64
+#define HD_KEEP_TRI64 0  // 1: keep the FP64 copy of B for float32 input too
+#endif
 
 // ---------------------------------------------------------------- 1-2: centroids, Morton codes
 
@@ -659,7 +662,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     // the FP64 copy of the triangles only for float64 input (tri32 holds float32 input exactly)
     const size_t b_nodes = up(sizeof(BvhNode) * h->n_nodes), b_t32 = up(sizeof(float4) * 3 * n),
-                 b_t64 = h->input_f64 ? up(sizeof(double) * 9 * n) : 0, b_vid = up(sizeof(int4) * n),
+                 b_t64 = (h->input_f64 || HD_KEEP_TRI64) ? up(sizeof(double) * 9 * n) : 0, b_vid = up(sizeof(int4) * n),
                  b_inv = up(sizeof(int) * n),
                  b_meta = up(4 * sizeof(float));
     cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta, s);
@@ -670,7 +673,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     char* c = (char*)h->block;
     h->nodes = (BvhNode*)c;
     h->tri32 = (float4*)(c + b_nodes);
-    h->tri64 = h->input_f64 ? (double*)(c + b_nodes + b_t32) : nullptr;
+    h->tri64 = (h->input_f64 || HD_KEEP_TRI64) ? (double*)(c + b_nodes + b_t32) : nullptr;
     h->tri_vid = (int4*)(c + b_nodes + b_t32 + b_t64);
     h->inv = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid);
     h->meta = (float*)(c + b_nodes + b_t32 + b_t64 + b_vid + b_inv);

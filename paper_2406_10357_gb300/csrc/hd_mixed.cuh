@@ -830,6 +830,8 @@ struct PolicyM {
   using Item = ItemM;
   using UT = float;
   static constexpr bool kFp64 = false;
+  static constexpr int kCoopBlocks = kCoopMinBlocks;  // resident blocks per SM of the cooperative traversal
+  static constexpr int kLongBudget = ::hd::kLongBudget;  // triangle tests of a lane before the hand-off
   static constexpr int kBoundRegs = HD_MIXED_BOUND_REGS;  // register cap of the UpperBound kernels
   static constexpr int kPaperRegs = HD_MIXED_PAPER_REGS;  // ... of their paper-order instantiation
 
