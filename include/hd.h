@@ -89,8 +89,17 @@ enum {
   HD_FLAG_SHARE_MIDPOINTS = 4,
   HD_FLAG_WELD_B = 8,
   HD_FLAG_NO_SMALL_ROUNDS = 16,
-  HD_FLAG_BATCH_STREAMS = 32
+  HD_FLAG_BATCH_STREAMS = 32,
+  HD_FLAG_EXACT_QUERIES = 64
 };
+/* HD_FLAG_EXACT_QUERIES: every vertex query runs until its nearest triangle of B is certain,
+ * as in the paper (Section 4).  By default (when u1 is in bound_order) a query stops as soon
+ * as it has found a triangle of B within l - e of the vertex, l the running lower bound and e
+ * the longest edge of A: u1 then discards every sub-triangle at that vertex whatever its exact
+ * distance, so the vertex keeps the triangle found, with a lower bound of 0.  The sub-triangles
+ * discarded, the splits, the rounds and the bracket are the same either way (up to the FP32
+ * certification width of MIXED distances, which can only make a face survive that exact
+ * queries would discard); only the traversal work differs. */
 /* HD_FLAG_BATCH_STREAMS (read by hd_hausdorff_batched): run the pairs as independent single
  * runs on host threads with one stream each, instead of the default batched run in which every
  * kernel launch works on the items of all pairs. */
@@ -146,6 +155,10 @@ typedef struct {
   int64_t long_node_visits;  /* ... of which by the warp-cooperative traversal of long queries */
   int64_t long_leaf_tests;   /* leaf tests of the warp-cooperative traversal (part of
                                 leaf_tests)                                                  */
+  int64_t queries_cut;       /* queries stopped before the nearest triangle was certain,
+                                once the triangle found was close enough that bound u1
+                                (Eq. u1) discards every face at the vertex (part of queries;
+                                0 with HD_FLAG_EXACT_QUERIES)                               */
 } hd_stats;
 
 typedef struct {

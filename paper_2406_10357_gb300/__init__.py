@@ -25,6 +25,7 @@ HD_FLAG_SHARE_MIDPOINTS = 4
 HD_FLAG_WELD_B = 8
 HD_FLAG_NO_SMALL_ROUNDS = 16
 HD_FLAG_BATCH_STREAMS = 32
+HD_FLAG_EXACT_QUERIES = 64
 BOUND_NAMES = ("exact", "u1", "u2", "u3", "u4", "late")
 
 
@@ -46,7 +47,8 @@ class HdStats(C.Structure):
                 ("fp64_escalations", C.c_int64), ("peak_frontier", C.c_int64), ("pool_vertices", C.c_int64),
                 ("eps_abs", C.c_double), ("dA", C.c_double), ("long_queries", C.c_int64),
                 ("kernel_launches", C.c_int64), ("d2h_bytes", C.c_int64), ("promoted", C.c_int64),
-                ("node_visits", C.c_int64), ("long_node_visits", C.c_int64), ("long_leaf_tests", C.c_int64)]
+                ("node_visits", C.c_int64), ("long_node_visits", C.c_int64), ("long_leaf_tests", C.c_int64),
+                ("queries_cut", C.c_int64)]
 
 
 class HdResult(C.Structure):
@@ -220,7 +222,8 @@ def _result(r: HdResult) -> dict:
                            pool_vertices=s.pool_vertices, eps_abs=s.eps_abs, dA=s.dA,
                            long_queries=s.long_queries, kernel_launches=s.kernel_launches,
                            d2h_bytes=s.d2h_bytes, promoted=s.promoted, node_visits=s.node_visits,
-                           long_node_visits=s.long_node_visits, long_leaf_tests=s.long_leaf_tests))
+                           long_node_visits=s.long_node_visits, long_leaf_tests=s.long_leaf_tests,
+                           queries_cut=s.queries_cut))
 
 
 def hd_hausdorff(bvh: Bvh, VA, FA, tol: float, opt: HdOptions | None = None, stream=None) -> dict:

@@ -98,7 +98,7 @@ int resolve_options(const hd_options* in, Opts* o) {
   memcpy(o->order, x.bound_order, 4);
   o->flags = x.flags;
   if (x.reserved != 0 || (o->flags & ~(int)(HD_FLAG_NO_PARENT_CLAMP | HD_FLAG_ASYNC_BUILD | HD_FLAG_SHARE_MIDPOINTS | HD_FLAG_WELD_B |
-                                      HD_FLAG_NO_SMALL_ROUNDS | HD_FLAG_BATCH_STREAMS))) return HD_ERR_INVALID;
+                                      HD_FLAG_NO_SMALL_ROUNDS | HD_FLAG_BATCH_STREAMS | HD_FLAG_EXACT_QUERIES))) return HD_ERR_INVALID;
   if (o->tol_mode != HD_TOL_ABS && o->tol_mode != HD_TOL_REL) return HD_ERR_INVALID;
   if (o->precision != HD_FP64 && o->precision != HD_MIXED) return HD_ERR_INVALID;
   if (!(o->max_face_factor >= 1.0)) return HD_ERR_INVALID;
@@ -411,6 +411,7 @@ int hd_hausdorff_sym(const hd_bvh* bvhB, const hd_mesh* A, const hd_bvh* bvhA, c
   S.node_visits = X.node_visits + Y.node_visits;
   S.long_node_visits = X.long_node_visits + Y.long_node_visits;
   S.long_leaf_tests = X.long_leaf_tests + Y.long_leaf_tests;
+  S.queries_cut = X.queries_cut + Y.queries_cut;
   S.eps_abs = X.eps_abs;
   S.dA = X.dA;
   return HD_OK;

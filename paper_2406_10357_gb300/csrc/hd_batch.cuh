@@ -327,6 +327,7 @@ static __global__ void k_batch_prep_finish(BatchCtx x, unsigned long long* boxes
   d.slack = slack;
   d.slack_f = __double2float_ru(slack);
   d.pad = 0;
+  d.emax = INFINITY;  // the batched queries are never cut
 }
 
 // ----------------------------------------------------------------------------- queries
@@ -1406,6 +1407,7 @@ int run_batch(const hd_bvh* const* Bs, const hd_mesh* As, int64_t npairs, double
     S.node_visits = (int64_t)h.node_visits;
     S.long_node_visits = (int64_t)h.long_node_visits;
     S.long_leaf_tests = (int64_t)h.long_leaf_tests;
+    S.queries_cut = (int64_t)h.queries_cut;
     // the batch's launches and read-backs are shared by its pairs: each result holds the totals
     S.kernel_launches = g_launches - launches0;
     S.d2h_bytes = g_d2h_bytes - d2h0;

@@ -86,15 +86,50 @@ __device__ inline void flush_counters(RunState* st, const Counters& c, bool long
 // ----------------------------------------------------------------------------- round 0 helpers
 
 // Referenced vertices of A (the paper assumes every vertex is referenced, Section 3; l and
-// dA use only referenced ones, Section 5.3) and the validity of F_A.
-static __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t* ref, int* bad) {
+// dA use only referenced ones, Section 5.3), the validity of F_A, and the largest squared
+// edge length of A's faces (for cut_radius; as the bits of a non-negative double, one
+// atomic per block that raises it).  Entry i = 3 f + k is the edge from corner k of face f
+// to corner k + 1.  Launched with 256 threads per block on a grid-stride loop (a bounded
+// grid, so that few blocks contend for the edge maximum).
+template <typename T>
+__global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t* ref, int* bad, const T* VA,
+                           unsigned long long* e2max_bits) {
   grid_dep_wait();
   grid_dep_launch();
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= 3 * nFA) return;
-  int32_t v = FA[i];
-  if (v < 0 || v >= nVA) atomicExch(bad, 1);
-  else ref[v] = 1;
+  T e2t = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < 3 * nFA; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = FA[i];
+    if (v < 0 || v >= nVA) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    ref[v] = 1;
+#if HD_CUT_EDGE
+    const int64_t f = i / 3;
+    const int k = (int)(i - 3 * f);
+    const int32_t w = FA[3 * f + (k == 2 ? 0 : k + 1)];
+    if (w >= 0 && w < nVA) {
+      // in the input's precision (FP64 is slow on this GPU): float rounding of a float edge
+      // is ~2^-23 relative, covered by the margin k_prep_finish adds
+      const T dx = VA[3 * (int64_t)w] - VA[3 * (int64_t)v];
+      const T dy = VA[3 * (int64_t)w + 1] - VA[3 * (int64_t)v + 1];
+      const T dz = VA[3 * (int64_t)w + 2] - VA[3 * (int64_t)v + 2];
+      const T x = dx * dx + dy * dy + dz * dz;
+      if (x > e2t) e2t = x;  // NaN (invalid input, flagged elsewhere) is dropped
+    }
+#endif
+  }
+  double e2 = (double)e2t;
+  for (int o = 16; o > 0; o >>= 1) e2 = fmax(e2, __shfl_xor_sync(0xffffffffu, e2, o));
+  __shared__ double part[8];
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = e2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) m = fmax(m, part[k]);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+    if (m > 0.0 && b > *(volatile unsigned long long*)e2max_bits) atomicMax(e2max_bits, b);
+  }
 }
 
 __device__ inline unsigned long long double_to_ordered(double d) {
@@ -159,7 +194,7 @@ __device__ inline double ordered_to_double(unsigned long long u) {
 
 // dA, eps and the slack from A's bounding box, on the device (one thread).
 static __global__ void k_prep_finish(unsigned long long* box, double tol, int tol_rel, double slack_scale,
-                                     DynParams* dyn, RunState* st, double l0, const float* b_meta) {
+                                     DynParams* dyn, RunState* st, double l0, const float* b_meta, int cut) {
   grid_dep_wait();
   grid_dep_launch();
   // B's validity flag (from its build) joins A's in the flag word the host reads with round 0
@@ -177,6 +212,9 @@ static __global__ void k_prep_finish(unsigned long long* box, double tol, int to
   dyn->slack = slack;
   dyn->slack_f = __double2float_ru(slack);
   dyn->pad = 0;
+  // the longest edge of A, with a relative margin above the rounding of any edge length the
+  // cascade computes (sub-triangle edges are about half their parent's)
+  dyn->emax = cut && HD_CUT_EDGE ? sqrt(__longlong_as_double((long long)box[7])) * (1.0 + 0x1p-20) : INFINITY;
 }
 
 // The round's table of split edges (Section 4's midpoint subdivision, with the midpoint of an
@@ -257,6 +295,11 @@ __device__ inline unsigned long_bucket(const BvhDev& B, float px, float py, floa
 // traversal).  With a list, a lane whose traversal tests more than kLongBudget triangles
 // stops and hands its query to k_query_long, which runs next and counts it.  Registers are
 // capped at 128 (a few spilled to L1), for 8 resident blocks of 64 threads per SM.
+#ifndef HD_QUERY_SEGMENTS
+#define HD_QUERY_SEGMENTS 8
+#endif
+constexpr int kQuerySegments = HD_QUERY_SEGMENTS;
+
 template <class P>
 __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, const int* count_ptr, int mult, int cap,
                         RunState* st, double slack_in, const DynParams* dyn, bool round_midpoints, MidTable tab,
@@ -271,12 +314,20 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
     count = min(*count_ptr * mult, cap);
   }
   const double slack = dyn ? dyn->slack : slack_in;
+  const bool cutting = HD_CUT_LANE && cut_on(dyn);
+  // With cuts, the batches of 32 are taken from kQuerySegments interleaved parts of the
+  // list, so that vertices from every part of A (the far ones among them) raise l early and
+  // the queries after them cut sooner; each part is still taken in order.
+  const int nb = (count + 31) >> 5, segs = cutting ? kQuerySegments : 1, per = (nb + segs - 1) / segs;
   Counters c;
   double lmax = 0.0;
-  int nq = 0;
+  int nq = 0, ncut = 0;
   for (;;) {
-    const int base = warp_batch(&st->q_next);
-    if (base >= count) break;
+    const int b = warp_batch(&st->q_next) >> 5;
+    if (b >= segs * per) break;
+    const int base = ((b % segs) * per + b / segs) << 5;
+    if (base >= count) continue;
+    const double lnow = cutting ? read_lower(st) : 0.0;
     const int t = base + (threadIdx.x & 31);
     bool active = t < count;
     // every lane of the warp enters the query (the MIXED traversal votes across the warp);
@@ -293,8 +344,9 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
       }
     }
     bool q = active && v.tri != -1;
-    bool over = false;
-    P::query(B, v, c, q, ll.idx ? P::kLongBudget : INT_MAX, &over);
+    bool over = false, was_cut = false;
+    P::query(B, v, c, q, ll.idx ? P::kLongBudget : INT_MAX, &over, cutting ? cut_radius(lnow, dyn) : -1.0,
+             &was_cut);
     if (q) {
       pool[beg + t] = v;
       if (over) {
@@ -304,16 +356,22 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
         else
           atomicExch(&st->overflow, 1);  // cannot happen: the list has room for every query
       } else {
-        lmax = fmax(lmax, P::lower(v) - slack);
+        if (!was_cut) lmax = fmax(lmax, P::lower(v) - slack);  // a cut query has no lower bound
         ++nq;
+        ncut += was_cut;
       }
+    }
+    if (cutting) {  // a larger l at once, so that the other warps cut sooner
+      const double w = warp_max(lmax);
+      if ((threadIdx.x & 31) == 0 && w > lnow) atomic_max_nonneg(&st->l_bits, w);
     }
   }
   lmax = warp_max(lmax);
-  unsigned long long q = warp_sum((unsigned long long)nq);
+  unsigned long long q = warp_sum((unsigned long long)nq), qc = warp_sum((unsigned long long)ncut);
   if ((threadIdx.x & 31) == 0) {
     atomic_max_nonneg(&st->l_bits, lmax);
     if (q) atomicAdd(&st->queries, q);
+    if (qc) atomicAdd(&st->queries_cut, qc);
   }
   flush_counters(st, c);
 }
@@ -346,9 +404,10 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
   const bool sorted = ll.sorted && n >= kSortMin;
   const int* list = sorted ? ll.sorted : ll.idx;
   const int chunk = sorted ? kLongChunk : 1;
+  const bool cutting = HD_CUT_LONG && cut_on(dyn);
   Counters c;
   double lmax = 0.0;
-  int nq = 0;
+  int nq = 0, ncut = 0;
   for (;;) {
     int i0 = 0;
     if (lane == 0) i0 = atomicAdd(&st->long_next, chunk);
@@ -357,21 +416,25 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
     for (int i = i0; i < min(i0 + chunk, n); ++i) {
       const int k = list[i];
       typename P::Vtx v = pool[k];
-      P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack);
+      const bool cut = P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack,
+                                     cutting ? cut_radius(read_lower(st), dyn) : -1.0);
       if (lane == 0) {
         pool[k] = v;
-        lmax = fmax(lmax, P::lower(v) - slack);
+        const double prev = lmax;
+        if (!cut) lmax = fmax(lmax, P::lower(v) - slack);  // a cut query has no lower bound
         ++nq;
+        ncut += cut;
+        if (cutting && lmax > prev) atomic_max_nonneg(&st->l_bits, lmax);  // other warps cut sooner
       }
     }
   }
-  lmax = warp_max(lmax);
   if (lane == 0) {
     atomic_max_nonneg(&st->l_bits, lmax);
     if (nq) {
       atomicAdd(&st->queries, (unsigned long long)nq);
       atomicAdd(&st->long_queries, (unsigned long long)nq);
     }
+    if (ncut) atomicAdd(&st->queries_cut, (unsigned long long)ncut);
   }
   flush_counters(st, c, true);
 }
@@ -1203,6 +1266,15 @@ inline double bits_to_double(unsigned long long b) {
   return d;
 }
 
+// Queries may be cut (cut_radius) unless exact ones are asked for, and only when u1 is in
+// the cascade: u1 is what discards the faces at a cut vertex.
+inline bool cut_enabled(const Opts& o) {
+  if (o.flags & HD_FLAG_EXACT_QUERIES) return false;
+  for (int k = 0; k < o.n_bounds; ++k)
+    if (o.order[k] == 1) return true;
+  return false;
+}
+
 // Shared part of round 0 (validation, referenced vertices, dA) lives in hd_api.cu.
 // Enqueues the validation of A, its bounding box and the device-side parameters (no sync).
 // Round-0 set-up of A, all on the stream with no host round trip: referenced vertices,
@@ -1214,13 +1286,18 @@ int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams*
   cudaStream_t s = io.s;
   int* bad = (int*)(box + 6);
   TraceScope tr(HD_K_PREP, s);
-  launch_chained(k_mark_ref, blocks_for(3 * io.nFA, 256), 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad);
-  if (io.vtype == HD_F64)
+  const int g_ref = (int)std::min<int64_t>(blocks_for(3 * io.nFA, 256), 16 * 152);
+  if (io.vtype == HD_F64) {
+    launch_chained(k_mark_ref<double>, g_ref, 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad,
+                   (const double*)io.VA, box + 7);
     launch_chained(k_check_init<P, double>, blocks_for(io.nVA, 256), 256, 0, s, (const double*)io.VA, io.nVA, ref, box, bad, pool);
-  else
+  } else {
+    launch_chained(k_mark_ref<float>, g_ref, 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad,
+                   (const float*)io.VA, box + 7);
     launch_chained(k_check_init<P, float>, blocks_for(io.nVA, 256), 256, 0, s, (const float*)io.VA, io.nVA, ref, box, bad, pool);
+  }
   launch_chained(k_prep_finish, 1, 1, 0, s, box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0,
-                                io.B->meta);
+                                io.B->meta, cut_enabled(*io.o) ? 1 : 0);
   HD_TRY_LAUNCH();
   return HD_OK;
 }
@@ -1699,7 +1776,7 @@ int run_bnb(const RunIO& io) {
   unsigned char* small = nullptr;
   HD_TRY(cudaMallocAsync((void**)&small, ref_bytes + 256 + 256 + sizeof(RunState), s));
   uint8_t* ref = small;
-  unsigned long long* box = (unsigned long long*)(small + ref_bytes);  // [0..5] bbox, [6] invalid flag
+  unsigned long long* box = (unsigned long long*)(small + ref_bytes);  // [0..5] bbox, [6] invalid flags, [7] A's longest edge squared
   DynParams* dyn = (DynParams*)(small + ref_bytes + 256);
   RunState* st = (RunState*)(small + ref_bytes + 512);
   HD_TRY(cudaMemsetAsync(small, 0, ref_bytes + 512 + sizeof(RunState), s));
@@ -1810,6 +1887,7 @@ int run_bnb(const RunIO& io) {
   S.node_visits = (int64_t)hst->node_visits;
   S.long_node_visits = (int64_t)hst->long_node_visits;
   S.long_leaf_tests = (int64_t)hst->long_leaf_tests;
+  S.queries_cut = (int64_t)hst->queries_cut;
   S.peak_frontier = T.peak;
   S.pool_vertices = io.nVA + T.mids;
 

@@ -73,18 +73,23 @@ __device__ inline float warp_min_f(float v) {
 // nearest state (test1 / range over triangle indices; r2(): its squared radius rounded up to
 // float); `box(lx, ly, lz, hx, hy, hz)` returns a lower bound of the squared distance from the
 // query point to a box, rounded down to float.  s_code / s_e: this warp's kCoopStack entries
-// (node index, box bound).
-template <class Near, class Box>
-__device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, unsigned* s_code, float* s_e,
-                                     Counters& c) {
+// (node index, box bound).  With kCut, the traversal stops early, returning true, once the
+// warp's squared radius is below cut2 (cut_radius).  The two forms are separate
+// instantiations, chosen per query: the loop without the checks is compiled as if they did
+// not exist (on the large soup the checks alone cost 20% in the queries that never cut).
+template <bool kCut, class Near, class Box>
+__device__ inline bool traverse_coop(const BvhDev& B, Near& t, const Box& box, unsigned* s_code, float* s_e,
+                                     Counters& c, float cut2) {
   const int lane = threadIdx.x & 31, g = lane >> 2, ch = lane & 3;
   if (lane == 0) {
     s_code[0] = 0u;  // the root, an inner node
     s_e[0] = 0.f;
   }
   int sp = 1;
-  __syncwarp();
   float r2 = warp_min_f(t.coop_r2());
+  if constexpr (kCut) {
+    if (r2 < cut2) return true;  // the triangle the lane traversal found is close enough
+  }
 #if HD_COOP_LEAFQ
   // leaf children wait in a queue (the top kLeafQ entries of the stack array) until
   // HD_COOP_LEAFQ of them are there, then up to 32 are tested at once, one per lane
@@ -92,10 +97,12 @@ __device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, u
   constexpr int cap = kCoopStack - kLeafQ;
   unsigned* lq_code = s_code + cap;
   int lq = 0;
+  __syncwarp();
   while (sp > 0 || lq > 0) {
     if (sp > 0) {
 #else
   constexpr int cap = kCoopStack;
+  __syncwarp();
   while (sp > 0) {
     {
 #endif
@@ -133,6 +140,9 @@ __device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, u
 #else
     if (hit && code_count(code) > 0) t.range(code_ref(code), code_count(code));
     r2 = warp_min_f(t.coop_r2());
+    if constexpr (kCut) {
+      if (r2 < cut2) return true;
+    }
 #endif
     const bool push = hit && code_count(code) == 0 && e <= r2;
     const unsigned m = __ballot_sync(0xffffffffu, push);
@@ -194,9 +204,13 @@ __device__ inline void traverse_coop(const BvhDev& B, Near& t, const Box& box, u
       lq -= take;
       __syncwarp();  // the entries taken are read before new ones overwrite them
       r2 = warp_min_f(t.coop_r2());
+      if constexpr (kCut) {
+        if (r2 < cut2) return true;
+      }
     }
 #endif
   }
+  return false;
 }
 
 }  // namespace hd

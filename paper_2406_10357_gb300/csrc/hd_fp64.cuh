@@ -13,16 +13,21 @@ constexpr int kStack = 96;  // up to 3 pushes per 4-wide node
 // boxes come with one node fetch, leaf children are tested at once, the nearer internal
 // child is entered and the farther one pushed with its box distance, which is re-checked
 // when popped.  `Test` gets a triangle range and may shrink the pruning radius it holds.
-// Returns false once `test` has tested more than `budget` triangles, with the traversal
-// unfinished (what `test` holds is then the best triangle found so far).
-template <class Test>
-__device__ inline bool traverse(const BvhDev& B, D3 p, Test& test, Counters& c, int budget = INT_MAX) {
+// Returns kTravOver once `test` has tested more than `budget` triangles, and kTravCut once
+// its squared radius is below test.cut2 (cut_radius), with the traversal unfinished (what
+// `test` holds is then the best triangle found so far); kTravDone when it finished.
+constexpr int kTravDone = 0, kTravOver = 1, kTravCut = 2;
+template <bool kCut, class Test>
+__device__ inline int traverse(const BvhDev& B, D3 p, Test& test, Counters& c, int budget = INT_MAX) {
   int stack_node[kStack];
   double stack_d[kStack];
   int sp = 0;
   int node = 0;
   for (;;) {
-    if ((int)test.evals > budget) return false;
+    if ((int)test.evals > budget) return kTravOver;
+    if constexpr (kCut) {
+      if (test.radius2() < test.cut2) return kTravCut;
+    }
     const float4* np = reinterpret_cast<const float4*>(B.nodes + node);
     const float4 lx = __ldg(np), ly = __ldg(np + 1), lz = __ldg(np + 2);
     const float4 hx = __ldg(np + 3), hy = __ldg(np + 4), hz = __ldg(np + 5);
@@ -88,7 +93,7 @@ __device__ inline bool traverse(const BvhDev& B, D3 p, Test& test, Counters& c, 
     }
     if (!found) break;
   }
-  return true;
+  return kTravDone;
 }
 
 struct NearestD {
@@ -96,6 +101,7 @@ struct NearestD {
   const double* tri64;
   const float4* tri32;
   double best2 = INFINITY;
+  double cut2 = -1.0;  // the traversal may stop once best2 < cut2 (cut_radius)
   int best = -1;
   D3 q = {0, 0, 0};
   unsigned evals = 0;
@@ -347,17 +353,21 @@ struct PolicyD {
   // Nearest triangle of v.  With `over` given, a traversal that tests more than `budget`
   // triangles stops, sets *over and leaves its best triangle so far in v (hint, d = its
   // squared distance, q) for query_coop to finish.
+  // With cut_r >= 0 (cut_radius), the query may stop at a triangle within cut_r of v: it
+  // then sets *was_cut and keeps that triangle and its distance (not a lower bound then).
   __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active, int budget = INT_MAX,
-                               bool* over = nullptr) {
+                               bool* over = nullptr, double cut_r = -1.0, bool* was_cut = nullptr) {
     if (!active) return;  // no warp-collective operations below
     NearestD t;
     t.p = {v.x, v.y, v.z};
     t.tri64 = B.tri64;
     t.tri32 = B.tri32;
+    if (cut_r > 0.0) t.cut2 = cut_r * cut_r;
     if (v.hint >= 0) t.test1(v.hint);
-    const bool finished = traverse(B, t.p, t, c, budget);
+    const int how = cut_r > 0.0 ? traverse<true>(B, t.p, t, c, budget) : traverse<false>(B, t.p, t, c, budget);
     c.leaf += t.evals;
-    if (!finished) {
+    if (how == kTravCut && was_cut) *was_cut = true;
+    if (how == kTravOver) {
       *over = true;
       v.hint = t.best;
       v.d = t.best2;
@@ -374,7 +384,10 @@ struct PolicyD {
   }
   // query() of a vertex that a lane's traversal handed off, by the whole warp (every lane
   // passes the same v; lane 0 returns the result in it).
-  __device__ static void query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e) {
+  // With cut_r >= 0 the traversal may stop as query() does (the same for the whole warp);
+  // returns true if it did.
+  __device__ static bool query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e,
+                                    double cut_r = -1.0) {
     const int lane = threadIdx.x & 31;
     NearestD t;
     t.p = {v.x, v.y, v.z};
@@ -389,7 +402,9 @@ struct PolicyD {
     auto box = [p](float lx, float ly, float lz, float hx, float hy, float hz) {
       return __double2float_rd(box_dist2(p, lx, ly, lz, hx, hy, hz));
     };
-    traverse_coop(B, t, box, s_code, s_e, c);
+    const float cut2 = cut_r > 0.0 ? __double2float_rd(cut_r * cut_r) : 0.f;
+    const bool cut = cut2 > 0.f ? traverse_coop<true>(B, t, box, s_code, s_e, c, cut2)
+                                : traverse_coop<false>(B, t, box, s_code, s_e, c, 0.f);
     c.leaf += t.evals;
     double m = t.best2;
     for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -402,6 +417,7 @@ struct PolicyD {
     v.qx = qx;
     v.qy = qy;
     v.qz = qz;
+    return cut;
   }
   __device__ static double lower(const Vtx& v) { return v.d; }
   __device__ static double out_dist(const Vtx& v) { return v.d; }

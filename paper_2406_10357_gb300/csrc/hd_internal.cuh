@@ -137,6 +137,7 @@ struct RunState {
   int batch_capacity;            // batched run: stopped because the batch's shared buffers ran out
   unsigned long long node_visits;  // BVH nodes fetched by the traversals (128 bytes each)
   unsigned long long long_node_visits, long_leaf_tests;  // ... of which by k_query_long, and its leaf tests
+  unsigned long long queries_cut;  // queries stopped once their vertex could no longer keep a face (cut_radius)
 };
 
 // Device view of hd_bvh, passed to kernels by value.
@@ -158,7 +159,36 @@ struct DynParams {
   double dA;      // bbox diagonal of A's referenced vertices
   float slack_f;  // slack rounded up to float
   int pad;
+  double emax;    // above every edge length of A's faces (cut_radius); +inf: queries are never cut
 };
+
+// Early end of a vertex query.  Bound u1 (Eq. u1) of a face containing vertex v is at most
+// (longest edge at v) + d(v, B), so once a query has found a triangle of B within
+// l - emax of v (l the running lower bound, emax above every edge of A), every face (and
+// sub-triangle) at v is discarded by u1, whatever v's exact distance: the nearest triangle
+// is no longer needed.  The vertex then keeps the triangle found (its upper bounds stay
+// valid, since every bound of Section 3.2 holds for any point of B in place of q_i) and a
+// lower bound of 0, so it never raises l; l itself can only have been larger than d(v, B).
+// The discarded faces, hence the splits, rounds and the final bracket, are those of exact
+// queries.  Returns the radius below which a query may stop (negative: never), before the
+// policy's own rounding margins, for the lower bound l read from the run state (a smaller,
+// older l only cuts less).
+#ifndef HD_CUT_EDGE
+#define HD_CUT_EDGE 1  // 0: no cut at all (A's longest edge is not measured)
+#endif
+#ifndef HD_CUT_LANE
+#define HD_CUT_LANE 1  // 0: the lane traversal never cuts
+#endif
+#ifndef HD_CUT_LONG
+#define HD_CUT_LONG 1  // 0: the cooperative traversal never cuts
+#endif
+__device__ inline bool cut_on(const DynParams* dyn) { return dyn != nullptr && dyn->emax < INFINITY; }
+__device__ inline double read_lower(const RunState* st) {
+  return __longlong_as_double((long long)*(const volatile unsigned long long*)&st->l_bits);
+}
+__device__ inline double cut_radius(double l, const DynParams* dyn) {
+  return l * (1.0 - 0x1p-12) - dyn->emax;  // the margin covers the rounding of the FP32 bounds
+}
 
 // Per-run constants of the round kernels.
 struct RunParams {

@@ -14,6 +14,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "hd_internal.cuh"
@@ -52,8 +53,27 @@ __device__ inline bool load_face(const T* V, int64_t nV, const int32_t* F, int64
   return fin;
 }
 
+// The same for float input, in float: a float vertex is exact as it is, and FP64 arithmetic
+// is slow on this GPU (the build's per-triangle FP64 work dominated its time).
+struct F3v {
+  float x, y, z;
+};
+__device__ inline bool load_face_f(const float* V, int64_t nV, const int32_t* F, int64_t f, F3v& a, F3v& b, F3v& c) {
+  const int32_t i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+  a = b = c = {0.f, 0.f, 0.f};
+  if (i0 < 0 || i1 < 0 || i2 < 0 || i0 >= nV || i1 >= nV || i2 >= nV) return false;
+  a = {V[3 * (int64_t)i0], V[3 * (int64_t)i0 + 1], V[3 * (int64_t)i0 + 2]};
+  b = {V[3 * (int64_t)i1], V[3 * (int64_t)i1 + 1], V[3 * (int64_t)i1 + 2]};
+  c = {V[3 * (int64_t)i2], V[3 * (int64_t)i2 + 1], V[3 * (int64_t)i2 + 2]};
+  const bool fin = isfinite(a.x) && isfinite(a.y) && isfinite(a.z) && isfinite(b.x) && isfinite(b.y) &&
+                   isfinite(b.z) && isfinite(c.x) && isfinite(c.y) && isfinite(c.z);
+  if (!fin) a = b = c = {0.f, 0.f, 0.f};
+  return fin;
+}
+
 // Validation, the centroids and their bounding box.  Grid-stride, so that the box is reduced
-// per thread, then per block, and ends in one atomic per block and bound.
+// per thread, then per block, and ends in one atomic per block and bound.  The centroids only
+// order the triangles (Morton codes), so float input keeps them in float.
 template <typename T>
 __global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, float4* cent,
                        unsigned* cbox /*6 ordered floats: min xyz (as ~max), max xyz*/, int* bad) {
@@ -62,14 +82,29 @@ __global__ void k_prep(const T* V, int64_t nV, const int32_t* F, int64_t nF, flo
   __shared__ float part[6][kThreads / 32];
   float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
   for (int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; f < nF; f += (int64_t)gridDim.x * blockDim.x) {
-    D3 a, b, c;
-    if (!load_face(V, nV, F, f, a, b, c)) {
-      atomicExch(bad, 1);
-      cent[f] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
+    float mx, my, mz;
+    if constexpr (std::is_same<T, float>::value) {
+      F3v a, b, c;
+      if (!load_face_f(V, nV, F, f, a, b, c)) {
+        atomicExch(bad, 1);
+        cent[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      mx = (a.x + b.x + c.x) * (1.f / 3.f);
+      my = (a.y + b.y + c.y) * (1.f / 3.f);
+      mz = (a.z + b.z + c.z) * (1.f / 3.f);
+    } else {
+      D3 a, b, c;
+      if (!load_face(V, nV, F, f, a, b, c)) {
+        atomicExch(bad, 1);
+        cent[f] = make_float4(0.f, 0.f, 0.f, 0.f);
+        continue;
+      }
+      const D3 m = (1.0 / 3.0) * (a + b + c);
+      mx = (float)m.x;
+      my = (float)m.y;
+      mz = (float)m.z;
     }
-    const D3 m = (1.0 / 3.0) * (a + b + c);
-    const float mx = (float)m.x, my = (float)m.y, mz = (float)m.z;
     lo[0] = fminf(lo[0], mx);
     lo[1] = fminf(lo[1], my);
     lo[2] = fminf(lo[2], mz);
@@ -340,25 +375,41 @@ __global__ void k_gather(const T* V, const int32_t* F, const uint32_t* order, in
   double e2 = 0.0;  // squared distance between a float vertex and its input vertex
   if (i < nF) {
     uint32_t f = order[i];
-    D3 a, b, c;
-    load_face(V, nV, F, f, a, b, c);
-    const double s[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
     double* t = tri64 ? tri64 + 9 * i : nullptr;  // null: float32 input, not kept
     float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     float4 out[3];
-    for (int v = 0; v < 3; ++v) {
-      float c[3];
-      for (int k = 0; k < 3; ++k) {
-        double x = s[3 * v + k];
-        if (t) t[3 * v + k] = x;
-        lo[k] = fminf(lo[k], rd(x));
-        hi[k] = fmaxf(hi[k], ru(x));
-        c[k] = (float)x;
+    if constexpr (std::is_same<T, float>::value) {
+      // float input is its own float copy: no rounding, eta = 0, no FP64 arithmetic
+      F3v a, b, c;
+      load_face_f(V, nV, F, f, a, b, c);
+      const float s[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
+      for (int v = 0; v < 3; ++v) {
+        for (int k = 0; k < 3; ++k) {
+          const float x = s[3 * v + k];
+          if (t) t[3 * v + k] = (double)x;
+          lo[k] = fminf(lo[k], x);
+          hi[k] = fmaxf(hi[k], x);
+        }
+        out[v] = make_float4(s[3 * v], s[3 * v + 1], s[3 * v + 2], 0.0f);
       }
-      // x - float(x) is exact in double
-      double ex = s[3 * v] - c[0], ey = s[3 * v + 1] - c[1], ez = s[3 * v + 2] - c[2];
-      e2 = fmax(e2, ex * ex + ey * ey + ez * ez);
-      out[v] = make_float4(c[0], c[1], c[2], 0.0f);
+    } else {
+      D3 a, b, c;
+      load_face(V, nV, F, f, a, b, c);
+      const double s[9] = {a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z};
+      for (int v = 0; v < 3; ++v) {
+        float c[3];
+        for (int k = 0; k < 3; ++k) {
+          double x = s[3 * v + k];
+          if (t) t[3 * v + k] = x;
+          lo[k] = fminf(lo[k], rd(x));
+          hi[k] = fmaxf(hi[k], ru(x));
+          c[k] = (float)x;
+        }
+        // x - float(x) is exact in double
+        double ex = s[3 * v] - c[0], ey = s[3 * v + 1] - c[1], ez = s[3 * v + 2] - c[2];
+        e2 = fmax(e2, ex * ex + ey * ey + ez * ez);
+        out[v] = make_float4(c[0], c[1], c[2], 0.0f);
+      }
     }
     out[0].w = __int_as_float((int)f);
     tri32[3 * i] = out[0];
@@ -376,11 +427,13 @@ __global__ void k_gather(const T* V, const int32_t* F, const uint32_t* order, in
     leafbox[2 * i] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     leafbox[2 * i + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
   }
-  // the largest squared error, rounded up (the host takes its square root): the squares and
-  // their sum carry at most 3 * 2^-53 relative error, covered by the margin
-  float e2f = __double2float_ru(e2 * (1.0 + 1e-12));
-  for (int o = 16; o > 0; o >>= 1) e2f = fmaxf(e2f, __shfl_xor_sync(0xffffffffu, e2f, o));
-  if ((threadIdx.x & 31) == 0 && e2f > 0.0f) atomicMax(e2_bits, __float_as_uint(e2f));
+  if constexpr (!std::is_same<T, float>::value) {
+    // the largest squared error, rounded up (the host takes its square root): the squares and
+    // their sum carry at most 3 * 2^-53 relative error, covered by the margin
+    float e2f = __double2float_ru(e2 * (1.0 + 1e-12));
+    for (int o = 16; o > 0; o >>= 1) e2f = fmaxf(e2f, __shfl_xor_sync(0xffffffffu, e2f, o));
+    if ((threadIdx.x & 31) == 0 && e2f > 0.0f) atomicMax(e2_bits, __float_as_uint(e2f));
+  }
 }
 
 // ---------------------------------------------------------------- 5: Karras binary radix tree

@@ -257,6 +257,7 @@ struct NearestM {
   const float4* tri32;
   float best_hi = INFINITY;
   float dlo = INFINITY;
+  float cut = -1.f;  // the traversal may stop once best_hi < cut (cut_radius)
   int best = -1;
   F3 q = {0.f, 0.f, 0.f};
   float qerr = 0.f;
@@ -315,9 +316,12 @@ __device__ inline void push_code(unsigned* stack_code, float* stack_d, int& sp, 
 
 // Must be called by all 32 lanes of the warp; inactive lanes start finished.  A lane that
 // has tested more than `budget` triangles stops unfinished before its next stack pop and sets
-// `over` (t then holds its best so far).
+// `over` (t then holds its best so far); one whose best distance bound fell below t.cut stops
+// there too and sets `cut` (kCut only: the traversal without the check is a separate
+// instantiation, as in traverse_coop).
+template <bool kCut>
 __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, bool active, int budget,
-                                  bool& over) {
+                                  bool& over, bool& cut) {
   unsigned stack_code[kStack];
   float stack_d[kStack];
   int sp = 0;
@@ -330,6 +334,12 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
   for (;;) {
     while (!done && lcount == 0) {
       if (node < 0) {
+        if constexpr (kCut) {
+          if (t.best_hi < t.cut) {
+            cut = done = true;
+            continue;
+          }
+        }
         bool found = false;
         while (sp > 0) {
           --sp;
@@ -874,21 +884,32 @@ struct PolicyM {
   // Nearest triangle of v, certified.  With `over` given, a traversal that tests more than
   // `budget` triangles stops, sets *over and leaves its best triangle so far in v (hint, dhi =
   // its distance bound without eta, q, qerr) for query_coop to finish.
+  // With cut_r >= 0 (cut_radius), the query may stop at a triangle within cut_r of v: it
+  // then sets *was_cut and keeps that triangle with a lower bound of 0.
   __device__ static void query(const BvhDev& B, Vtx& v, Counters& c, bool active, int budget = INT_MAX,
-                               bool* over = nullptr) {
+                               bool* over = nullptr, double cut_r = -1.0, bool* was_cut = nullptr) {
     NearestM t;
     t.tri32 = B.tri32;
     if (active) {
       t.P = pos(v);
       if (v.hint >= 0) t.test1(v.hint);
+      t.cut = cut_bound(B, cut_r);
     } else {
       t.P = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     }
-    bool unfinished = false;
-    traverse_m(B, t, c, active, budget, unfinished);
+    bool unfinished = false, cut = active && t.best_hi < t.cut;  // the hint may be close enough
+    if (cut_r > 0.0)  // the same for every lane of the warp
+      traverse_m<true>(B, t, c, active && !cut, budget, unfinished, cut);
+    else
+      traverse_m<false>(B, t, c, active, budget, unfinished, cut);
     if (!active) return;
     c.leaf += t.evals;
     c.escalations += t.esc;
+    if (cut) {
+      finish(B, v, t.best, t.best_hi, 0.f, t.q, t.qerr);
+      if (was_cut) *was_cut = true;
+      return;
+    }
     if (unfinished) {
       *over = true;
       v.hint = t.best;
@@ -900,6 +921,12 @@ struct PolicyM {
       return;
     }
     finish(B, v, t.best, t.best_hi, t.dlo, t.q, t.qerr);
+  }
+  // The bound on best_hi (the certified distance to B's float triangles, before eta) below
+  // which a query stops: best_hi + eta < cut_r, rounded so that it holds in exact arithmetic.
+  __device__ static float cut_bound(const BvhDev& B, double cut_r) {
+    if (!(cut_r > 0.0)) return -1.f;
+    return __fsub_rd(__double2float_rd(cut_r), __ldg(B.meta));
   }
   // The query's result in v: eta (the distance between B's float triangles and its input)
   // widens both bounds.
@@ -917,7 +944,10 @@ struct PolicyM {
   // passes the same v; lane 0 returns the result in it).  The certified lower bound is the
   // smallest lower bound over the triangles tested and the final best upper bound (every
   // pruned box lies beyond the radius of the moment, which is at least that).
-  __device__ static void query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e) {
+  // With cut_r >= 0 the traversal may stop as query() does (the same for the whole warp);
+  // returns true if it did.
+  __device__ static bool query_coop(const BvhDev& B, Vtx& v, Counters& c, unsigned* s_code, float* s_e,
+                                    double cut_r = -1.0) {
     const int lane = threadIdx.x & 31;
     NearestM t;
     t.tri32 = B.tri32;
@@ -933,16 +963,19 @@ struct PolicyM {
     auto box = [plo, phi](float lx, float ly, float lz, float hx, float hy, float hz) {
       return box_lo2(plo, phi, lx, ly, lz, hx, hy, hz);
     };
-    traverse_coop(B, t, box, s_code, s_e, c);
+    const float cb = cut_bound(B, cut_r);
+    const bool cut = cb > 0.f ? traverse_coop<true>(B, t, box, s_code, s_e, c, __fmul_rd(cb, cb))
+                              : traverse_coop<false>(B, t, box, s_code, s_e, c, 0.f);
     c.leaf += t.evals;
     c.escalations += t.esc;
-    const float m = warp_min_f(t.best_hi), dlo = warp_min_f(t.dlo);
+    const float m = warp_min_f(t.best_hi), dlo = cut ? 0.f : warp_min_f(t.dlo);
     const int src = __ffs(__ballot_sync(0xffffffffu, t.best_hi == m)) - 1;
     const int best = __shfl_sync(0xffffffffu, t.best, src);
     const F3 q = {__shfl_sync(0xffffffffu, t.q.x, src), __shfl_sync(0xffffffffu, t.q.y, src),
                   __shfl_sync(0xffffffffu, t.q.z, src)};
     const float qerr = __shfl_sync(0xffffffffu, t.qerr, src);
     finish(B, v, best, m, dlo, q, qerr);
+    return cut;
   }
   __device__ static double lower(const Vtx& v) { return v.dlo; }
   __device__ static double out_dist(const Vtx& v) { return v.dhi; }

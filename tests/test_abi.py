@@ -48,8 +48,8 @@ def test_struct_layouts_match_header(hd):
     # sizes of the ABI structs as laid out by a C compiler for this header
     assert C.sizeof(hd.HdMesh) == 40
     assert C.sizeof(hd.HdOptions) == 64
-    assert C.sizeof(hd.HdStats) == 8 * 25
-    assert C.sizeof(hd.HdResult) == 24 + 8 * 25
+    assert C.sizeof(hd.HdStats) == 8 * 26
+    assert C.sizeof(hd.HdResult) == 24 + 8 * 26
     assert C.sizeof(hd.HdTrace) == 128
 
 
@@ -78,7 +78,7 @@ def test_invalid_arguments_rejected_before_any_launch(hd):
     V[1, 0] = V[2, 1] = 1.0
     Fi = np.array([[0, 1, 2]], np.int32)
     mv = hd.HdMesh(V.ctypes.data, 3, Fi.ctypes.data, 1, hd.HD_F64, 0)
-    for b in (hd.hd_options_default(flags=64), hd.hd_options_default(reserved=1)):
+    for b in (hd.hd_options_default(flags=128), hd.hd_options_default(reserved=1)):
         assert L.hd_build_B(C.byref(mv), C.byref(b), None, C.byref(out)) == hd.HD_ERR_INVALID
     if not _has_gpu():
         good = hd.hd_options_default(flags=hd.HD_FLAG_NO_PARENT_CLAMP)
