@@ -25,6 +25,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "hd_fp64.cuh"
 #include "hd_internal.cuh"
@@ -88,12 +89,12 @@ __device__ inline void flush_counters(RunState* st, const Counters& c, bool long
 // Referenced vertices of A (the paper assumes every vertex is referenced, Section 3; l and
 // dA use only referenced ones, Section 5.3), the validity of F_A, and the largest squared
 // edge length of A's faces (for cut_radius; as the bits of a non-negative double, one
-// atomic per block that raises it).  Entry i = 3 f + k is the edge from corner k of face f
-// to corner k + 1.  Launched with 256 threads per block on a grid-stride loop (a bounded
+// atomic per block that raises it), with `ev` the longest edge at each vertex.  Entry
+// i = 3 f + k is the edge from corner k of face f to corner k + 1.  Launched with 256 threads per block on a grid-stride loop (a bounded
 // grid, so that few blocks contend for the edge maximum).
 template <typename T>
 __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t* ref, int* bad, const T* VA,
-                           unsigned long long* e2max_bits) {
+                           unsigned long long* e2max_bits, unsigned* ev) {
   grid_dep_wait();
   grid_dep_launch();
   T e2t = 0;
@@ -107,15 +108,28 @@ __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t*
 #if HD_CUT_EDGE
     const int64_t f = i / 3;
     const int k = (int)(i - 3 * f);
-    const int32_t w = FA[3 * f + (k == 2 ? 0 : k + 1)];
+    const int32_t w = FA[3 * f + (k == 2 ? 0 : k + 1)], u = FA[3 * f + (k == 0 ? 2 : k - 1)];
+    // in the input's precision (FP64 is slow on this GPU): float rounding of a float edge is
+    // ~2^-23 relative, covered by the margins k_prep_finish and cut_r add
+    const T vx = VA[3 * (int64_t)v], vy = VA[3 * (int64_t)v + 1], vz = VA[3 * (int64_t)v + 2];
+    T xw = 0, xu = 0;  // the squared edges at this corner: to the next corner and the previous
     if (w >= 0 && w < nVA) {
-      // in the input's precision (FP64 is slow on this GPU): float rounding of a float edge
-      // is ~2^-23 relative, covered by the margin k_prep_finish adds
-      const T dx = VA[3 * (int64_t)w] - VA[3 * (int64_t)v];
-      const T dy = VA[3 * (int64_t)w + 1] - VA[3 * (int64_t)v + 1];
-      const T dz = VA[3 * (int64_t)w + 2] - VA[3 * (int64_t)v + 2];
-      const T x = dx * dx + dy * dy + dz * dz;
-      if (x > e2t) e2t = x;  // NaN (invalid input, flagged elsewhere) is dropped
+      const T dx = VA[3 * (int64_t)w] - vx, dy = VA[3 * (int64_t)w + 1] - vy, dz = VA[3 * (int64_t)w + 2] - vz;
+      xw = dx * dx + dy * dy + dz * dz;
+      if (xw > e2t) e2t = xw;  // each edge once; NaN (invalid input, flagged elsewhere) is dropped
+    }
+    if (ev && u >= 0 && u < nVA) {
+      const T dx = VA[3 * (int64_t)u] - vx, dy = VA[3 * (int64_t)u + 1] - vy, dz = VA[3 * (int64_t)u + 2] - vz;
+      xu = dx * dx + dy * dy + dz * dz;
+    }
+    const T x = xw > xu ? xw : xu;
+    if (ev && x > T(0)) {  // the longest edge at v (float bits: non-negative floats order as unsigned)
+      float e;
+      if constexpr (std::is_same<T, float>::value)
+        e = sqrtf(x);
+      else
+        e = __double2float_ru(sqrt(x));
+      atomicMax(&ev[v], __float_as_uint(e));
     }
 #endif
   }
@@ -143,17 +157,17 @@ __device__ inline unsigned long long double_to_ordered(double d) {
 // per block and bound.  Launched with 256 threads per block.
 template <class P, typename T>
 __global__ void k_check_init(const T* VA, int64_t nVA, const uint8_t* ref, unsigned long long* box, int* bad,
-                             typename P::Vtx* pool) {
+                             typename P::Vtx* pool, const unsigned* ev) {
   grid_dep_wait();
   grid_dep_launch();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   unsigned long long m[6] = {0, 0, 0, 0, 0, 0};  // ~lo xyz, hi xyz
   if (i < nVA) {
-    double x = VA[3 * i], y = VA[3 * i + 1], z = VA[3 * i + 2];
+    T x = VA[3 * i], y = VA[3 * i + 1], z = VA[3 * i + 2];
     const bool used = ref[i] != 0;
     if (!(isfinite(x) && isfinite(y) && isfinite(z))) {
       atomicExch(bad, 1);
-      x = y = z = 0.0;
+      x = y = z = 0;
     } else if (used) {
       m[3] = double_to_ordered(x);
       m[4] = double_to_ordered(y);
@@ -164,9 +178,13 @@ __global__ void k_check_init(const T* VA, int64_t nVA, const uint8_t* ref, unsig
     }
     typename P::Vtx v;
     memset(&v, 0, sizeof v);
-    P::set_pos(v, x, y, z);
+    if constexpr (std::is_same<T, float>::value)
+      P::set_pos_f(v, x, y, z);
+    else
+      P::set_pos(v, x, y, z);
     v.tri = used ? -2 : -1;
     v.hint = -1;
+    if (ev) P::set_edge(v, __uint_as_float(ev[i]));
     pool[i] = v;
   }
   __shared__ unsigned long long part[6][8];
@@ -345,8 +363,8 @@ __device__ inline void query_body(BvhDev B, typename P::Vtx* pool, int beg, cons
     }
     bool q = active && v.tri != -1;
     bool over = false, was_cut = false;
-    P::query(B, v, c, q, ll.idx ? P::kLongBudget : INT_MAX, &over, cutting ? cut_radius(lnow, dyn) : -1.0,
-             &was_cut);
+    const double cut_r = cutting && q ? P::cut_r(lnow, dyn, v) : -1.0;
+    P::query(B, v, c, q, ll.idx ? (cut_r > 0.0 ? kLongBudgetCut : P::kLongBudget) : INT_MAX, &over, cut_r, &was_cut);
     if (q) {
       pool[beg + t] = v;
       if (over) {
@@ -417,7 +435,7 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
       const int k = list[i];
       typename P::Vtx v = pool[k];
       const bool cut = P::query_coop(B, v, c, s_code + w * kCoopStack, s_e + w * kCoopStack,
-                                     cutting ? cut_radius(read_lower(st), dyn) : -1.0);
+                                     cutting ? P::cut_r(read_lower(st), dyn, v) : -1.0);
       if (lane == 0) {
         pool[k] = v;
         const double prev = lmax;
@@ -1282,19 +1300,21 @@ inline bool cut_enabled(const Opts& o) {
 // device.  `small` (ref | box | dyn | st) must be zero-filled first.
 template <class P>
 int prepare_A(const RunIO& io, uint8_t* ref, unsigned long long* box, DynParams* dyn, double slack_scale,
-              RunState* st, typename P::Vtx* pool) {
+              RunState* st, typename P::Vtx* pool, unsigned* ev) {
   cudaStream_t s = io.s;
   int* bad = (int*)(box + 6);
   TraceScope tr(HD_K_PREP, s);
   const int g_ref = (int)std::min<int64_t>(blocks_for(3 * io.nFA, 256), 16 * 152);
   if (io.vtype == HD_F64) {
     launch_chained(k_mark_ref<double>, g_ref, 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad,
-                   (const double*)io.VA, box + 7);
-    launch_chained(k_check_init<P, double>, blocks_for(io.nVA, 256), 256, 0, s, (const double*)io.VA, io.nVA, ref, box, bad, pool);
+                   (const double*)io.VA, box + 7, ev);
+    launch_chained(k_check_init<P, double>, blocks_for(io.nVA, 256), 256, 0, s, (const double*)io.VA, io.nVA, ref, box, bad, pool,
+                   (const unsigned*)ev);
   } else {
     launch_chained(k_mark_ref<float>, g_ref, 256, 0, s, io.FA, io.nFA, io.nVA, ref, bad,
-                   (const float*)io.VA, box + 7);
-    launch_chained(k_check_init<P, float>, blocks_for(io.nVA, 256), 256, 0, s, (const float*)io.VA, io.nVA, ref, box, bad, pool);
+                   (const float*)io.VA, box + 7, ev);
+    launch_chained(k_check_init<P, float>, blocks_for(io.nVA, 256), 256, 0, s, (const float*)io.VA, io.nVA, ref, box, bad, pool,
+                   (const unsigned*)ev);
   }
   launch_chained(k_prep_finish, 1, 1, 0, s, box, io.tol, io.o->tol_mode == HD_TOL_REL ? 1 : 0, slack_scale, dyn, st, io.l0,
                                 io.B->meta, cut_enabled(*io.o) ? 1 : 0);
@@ -1772,14 +1792,18 @@ int run_bnb(const RunIO& io) {
 
   // small per-call device block: referenced-vertex flags, A's bbox + invalid flag, the
   // device-side parameters, and the run state
+  // device-side parameters, and the run state; with cuts, the longest edge at each vertex
   const size_t ref_bytes = ((size_t)std::max<int64_t>(io.nVA, 1) + 255) & ~(size_t)255;
+  const size_t st_bytes = (sizeof(RunState) + 255) & ~(size_t)255;
+  const size_t ev_bytes = cut_enabled(o) && P::kEdgePerVertex ? sizeof(unsigned) * (size_t)std::max<int64_t>(io.nVA, 1) : 0;
   unsigned char* small = nullptr;
-  HD_TRY(cudaMallocAsync((void**)&small, ref_bytes + 256 + 256 + sizeof(RunState), s));
+  HD_TRY(cudaMallocAsync((void**)&small, ref_bytes + 512 + st_bytes + ev_bytes, s));
   uint8_t* ref = small;
   unsigned long long* box = (unsigned long long*)(small + ref_bytes);  // [0..5] bbox, [6] invalid flags, [7] A's longest edge squared
   DynParams* dyn = (DynParams*)(small + ref_bytes + 256);
   RunState* st = (RunState*)(small + ref_bytes + 512);
-  HD_TRY(cudaMemsetAsync(small, 0, ref_bytes + 512 + sizeof(RunState), s));
+  unsigned* ev = ev_bytes ? (unsigned*)(small + ref_bytes + 512 + st_bytes) : nullptr;
+  HD_TRY(cudaMemsetAsync(small, 0, ref_bytes + 512 + st_bytes + ev_bytes, s));
 
   Rounds<P> R;
   int rc = alloc_rounds<P>(R, o, io.nVA, io.nFA, !P::kFp64, s);
@@ -1789,7 +1813,7 @@ int run_bnb(const RunIO& io) {
   }
   // validation of A, its bbox and the pool entries of its vertices run asynchronously; the
   // host reads the result with round 0
-  rc = prepare_A<P>(io, ref, box, dyn, P::slack(1.0), st, R.pool);
+  rc = prepare_A<P>(io, ref, box, dyn, P::slack(1.0), st, R.pool, ev);
   if (rc != HD_OK) {
     free_rounds(R, s);
     cudaFreeAsync(small, s);

@@ -63,6 +63,13 @@ constexpr int kCoopMinBlocks = HD_COOP_MIN_BLOCKS;
 // a few triangles).  6 against 10 on the large soup: lane pass 0.64 -> 0.55 ms, cooperative
 // pass 1.67 -> 1.72 ms (8% more queries handed off).
 constexpr int kLongBudget = HD_LONG_BUDGET;
+// The budget of a query that may be cut (cut_radius > 0): most such queries stop after a few
+// tests anyway, and the ones near the cut radius are cheaper to finish in the lane than to
+// restart in a warp.
+#ifndef HD_LONG_BUDGET_CUT
+#define HD_LONG_BUDGET_CUT HD_LONG_BUDGET
+#endif
+constexpr int kLongBudgetCut = HD_LONG_BUDGET_CUT;
 
 __device__ inline float warp_min_f(float v) {
   for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));

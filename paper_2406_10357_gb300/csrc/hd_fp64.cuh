@@ -55,6 +55,21 @@ __device__ inline int traverse(const BvhDev& B, D3 p, Test& test, Counters& c, i
         k[b] = tk;
       }
     }
+    if constexpr (kCut) {
+      // a child box wholly within the cut radius: one of its triangles is close enough
+      const uint4 rp = __ldg(reinterpret_cast<const uint4*>(np + 7));
+      const float px = (float)p.x, py = (float)p.y, pz = (float)p.z;
+      const float c2 = (float)test.cut2;
+      int pick = -1;
+      if (cd.w != kNoChild && box_far2(px, py, pz, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w) < c2) pick = (int)rp.w;
+      if (cd.z != kNoChild && box_far2(px, py, pz, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z) < c2) pick = (int)rp.z;
+      if (cd.y != kNoChild && box_far2(px, py, pz, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y) < c2) pick = (int)rp.y;
+      if (cd.x != kNoChild && box_far2(px, py, pz, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x) < c2) pick = (int)rp.x;
+      if (pick >= 0) {
+        test.range(pick, 1);
+        if (test.radius2() < test.cut2) return kTravCut;
+      }
+    }
     // leaf ranges first, nearest first, so that the radius shrinks before the inner
     // children are kept or dropped
 #pragma unroll
@@ -428,6 +443,11 @@ struct PolicyD {
   __device__ static double bound_u4(const Vtx&, const Vtx&, const Vtx&, const RunParams&, double) { return INFINITY; }
   __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
   __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
+  __device__ static void set_pos_f(Vtx& v, float x, float y, float z) { set_pos(v, x, y, z); }
+  // no room in the vertex for its own edge bound: the longest edge of A for every vertex
+  static constexpr bool kEdgePerVertex = false;
+  __device__ static void set_edge(Vtx&, float) {}
+  __device__ static double cut_r(double l, const DynParams* dyn, const Vtx&) { return cut_radius(l, dyn->emax); }
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {
     v.x = x;
     v.y = y;

@@ -29,11 +29,12 @@ int set_cuda_error(cudaError_t e, const char* what, const char* file, int line);
 // fetches): the children's boxes stored by component (lo.x of children 0..3, then lo.y, ...),
 // and per child a code, count << 27 | index -- an inner node (count 0), a leaf range
 // [index, index + count) of sorted triangles (count > 0), or no child (kNoChild, with an
-// empty box: lo = +inf, hi = -inf).
+// empty box: lo = +inf, hi = -inf).  `rep` lets a cut query (cut_radius) stop at a child
+// whose whole box lies within the cut radius: any triangle inside is then close enough.
 struct __align__(16) BvhNode {
   float4 lox, loy, loz, hix, hiy, hiz;
   uint4 code;
-  uint4 pad;
+  uint4 rep;  // per child, one of its triangles (the first of its range; 0 for no child)
 };
 static_assert(sizeof(BvhNode) == 128, "node is 128 B");
 constexpr unsigned kNoChild = 0xffffffffu;
@@ -164,7 +165,9 @@ struct DynParams {
 
 // Early end of a vertex query.  Bound u1 (Eq. u1) of a face containing vertex v is at most
 // (longest edge at v) + d(v, B), so once a query has found a triangle of B within
-// l - emax of v (l the running lower bound, emax above every edge of A), every face (and
+// l - e_v of v (l the running lower bound, e_v above every edge at v of a face or
+// sub-triangle: the longest edge at v in A, or for a midpoint the larger bound of its edge's
+// ends; emax, above every edge of A, where the policy keeps no e_v), every face (and
 // sub-triangle) at v is discarded by u1, whatever v's exact distance: the nearest triangle
 // is no longer needed.  The vertex then keeps the triangle found (its upper bounds stay
 // valid, since every bound of Section 3.2 holds for any point of B in place of q_i) and a
@@ -186,8 +189,8 @@ __device__ inline bool cut_on(const DynParams* dyn) { return dyn != nullptr && d
 __device__ inline double read_lower(const RunState* st) {
   return __longlong_as_double((long long)*(const volatile unsigned long long*)&st->l_bits);
 }
-__device__ inline double cut_radius(double l, const DynParams* dyn) {
-  return l * (1.0 - 0x1p-12) - dyn->emax;  // the margin covers the rounding of the FP32 bounds
+__device__ inline double cut_radius(double l, double e) {
+  return l * (1.0 - 0x1p-12) - e;  // the margin covers the rounding of the FP32 bounds
 }
 
 // Per-run constants of the round kernels.
@@ -376,6 +379,16 @@ __device__ inline double box_dist2(D3 p, float lx, float ly, float lz, float hx,
   double dy = fmax(fmax((double)ly - p.y, p.y - (double)hy), 0.0);
   double dz = fmax(fmax((double)lz - p.z, p.z - (double)hz), 0.0);
   return dx * dx + dy * dy + dz * dz;
+}
+
+// Squared distance from p to the farthest point of the box: every triangle inside lies within
+// it.  A cut query tests one triangle of a child box within its cut radius (BvhNode::rep),
+// and stops if that triangle's own distance is below the cut radius: the box bound only
+// picks the moment, so it needs no directed rounding.
+__device__ inline float box_far2(float px, float py, float pz, float lx, float ly, float lz, float hx, float hy,
+                                float hz) {
+  const float dx = fmaxf(px - lx, hx - px), dy = fmaxf(py - ly, hy - py), dz = fmaxf(pz - lz, hz - pz);
+  return fmaf(dx, dx, fmaf(dy, dy, dz * dz));
 }
 
 // ----------------------------------------------------------------------------- launch helpers

@@ -11,6 +11,7 @@
 //      union of the aligned power-of-two blocks of leaves that tile its range;
 //   6. traversal nodes: 128 B each, holding up to four child boxes (a binary node with its
 //      grandchildren); subtrees of at most leaf_size triangles become leaf ranges.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -249,20 +250,34 @@ __global__ void k_rs_scan_digits(unsigned* hist, int nblocks, const unsigned* to
   }
 }
 
+// The keys of a tile go first to shared memory in the tile's digit order (each key at its
+// digit's block-local start + its warp's offset + its rank in the warp), then out to global
+// memory from there, so that consecutive threads write consecutive addresses of one digit's
+// run: writing each key straight from its lane scattered 8- and 4-byte stores over up to 256
+// runs (several times the bytes in partly written sectors).  Dynamic shared memory: 12 bytes
+// per key of the tile.
+template <int ROUNDS>
+constexpr size_t rs_scatter_smem() {
+  return (size_t)RS_THREADS * ROUNDS * (sizeof(uint64_t) + sizeof(uint32_t));
+}
+
 template <int ROUNDS, bool FUSED>
 __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t* kout, uint32_t* vout, int64_t n,
                              int shift, const unsigned* hist, int nblocks) {
   grid_dep_wait();
   grid_dep_launch();
   constexpr int RS_TILE = RS_THREADS * ROUNDS;
-  static_assert(RS_THREADS == 256, "one digit per thread in the fused offsets");
+  static_assert(RS_THREADS == 256, "one digit per thread");
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
+  uint32_t* sv = reinterpret_cast<uint32_t*>(rs_smem + sizeof(uint64_t) * RS_TILE);
   __shared__ unsigned wcnt[RS_WARPS][256];
-  __shared__ unsigned doff[256];
+  __shared__ unsigned doff[256];  // where this block's keys of digit d start in the output
+  __shared__ unsigned lofs[256];  // where they start in the tile's digit order
   __shared__ unsigned wsum[RS_WARPS];
-  int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (FUSED) {
-    // this block's start for digit d: all keys of smaller digits, plus the keys of digit d in
-    // earlier blocks
+    // all keys of smaller digits, plus the keys of digit d in earlier blocks
     const int d = threadIdx.x;
     unsigned tot = 0, mine = 0;
     for (int b = 0; b < nblocks; ++b) {
@@ -280,17 +295,22 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
     unsigned before = 0;
     for (int k = 0; k < w; ++k) before += wsum[k];
     doff[d] = before + x - tot + mine;
+  } else {
+    doff[threadIdx.x] = hist[(int64_t)threadIdx.x * nblocks + blockIdx.x];
   }
   for (int i = lane; i < 256; i += 32) wcnt[w][i] = 0;
   __syncwarp();
   const unsigned lt = (1u << lane) - 1u;
-  int64_t base = (int64_t)blockIdx.x * RS_TILE + w * (RS_TILE / RS_WARPS);
+  const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+  const int64_t base = tile0 + w * (RS_TILE / RS_WARPS);
   unsigned rank[ROUNDS];
+  uint64_t key[ROUNDS];
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     bool valid = i < n;
-    unsigned dig = valid ? (unsigned)((kin[i] >> shift) & 0xff) : 256u + lane;  // invalid lanes match only themselves
+    key[r] = valid ? kin[i] : 0ull;
+    unsigned dig = valid ? (unsigned)((key[r] >> shift) & 0xff) : 256u + lane;  // invalid lanes match only themselves
     unsigned peers = __match_any_sync(0xffffffffu, dig);
     unsigned before = __popc(peers & lt);
     unsigned c = valid ? wcnt[w][dig] : 0;
@@ -300,27 +320,62 @@ __global__ void k_rs_scatter(const uint64_t* kin, const uint32_t* vin, uint64_t*
     rank[r] = c + before;
   }
   __syncthreads();
-  // warp offsets within the block, per digit (exclusive over warps)
-  for (int d = threadIdx.x; d < 256; d += blockDim.x) {
+  // per digit (one per thread): the warps' offsets (exclusive over warps), then the digit's
+  // start in the tile (exclusive scan of the block's digit totals)
+  {
+    const int d = threadIdx.x;
     unsigned run = 0;
     for (int k = 0; k < RS_WARPS; ++k) {
       unsigned v = wcnt[k][d];
       wcnt[k][d] = run;
       run += v;
     }
+    unsigned x = run;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;  // (the fused offsets above read wsum before the last barrier)
+    __syncthreads();
+    unsigned before = 0;
+    for (int k = 0; k < w; ++k) before += wsum[k];
+    lofs[d] = before + x - run;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < ROUNDS; ++r) {
     int64_t i = base + r * 32 + lane;
     if (i < n) {
-      uint64_t key = kin[i];
-      unsigned dig = (unsigned)((key >> shift) & 0xff);
-      unsigned pos = (FUSED ? doff[dig] : hist[(int64_t)dig * nblocks + blockIdx.x]) + wcnt[w][dig] + rank[r];
-      kout[pos] = key;
-      vout[pos] = vin[i];
+      unsigned dig = (unsigned)((key[r] >> shift) & 0xff);
+      unsigned loc = lofs[dig] + wcnt[w][dig] + rank[r];
+      sk[loc] = key[r];
+      sv[loc] = vin[i];
     }
   }
+  __syncthreads();
+  const int cnt = (int)min((int64_t)RS_TILE, n - tile0);
+  for (int j = threadIdx.x; j < cnt; j += RS_THREADS) {
+    const uint64_t k = sk[j];
+    const unsigned dig = (unsigned)((k >> shift) & 0xff);
+    const unsigned pos = doff[dig] + (unsigned)j - lofs[dig];
+    kout[pos] = k;
+    vout[pos] = sv[j];
+  }
+}
+
+// Dynamic shared memory above the default 48 KB for the 16-round scatter, once per device.
+template <bool FUSED>
+cudaError_t rs_scatter_attr() {
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(k_rs_scatter<16, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)rs_scatter_smem<16>());
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_relaxed);
+  return e;
 }
 
 // ---------------------------------------------------------------- weld (option): one id per position
@@ -505,13 +560,16 @@ __device__ inline void child_meta(int c, const int* first, const int* last, int 
 // and an empty slot.  cbox is c's box; the children's boxes are read from ibox / leafbox.
 __device__ inline void wide_slots(int c, const float clo[3], const float chi[3], const int* left, const int* right,
                                   const int* first, const int* last, int L, const float4* leafbox,
-                                  const float4* ibox, float lo[2][3], float hi[2][3], unsigned code[2]) {
+                                  const float4* ibox, float lo[2][3], float hi[2][3], unsigned code[2],
+                                  unsigned rep[2]) {
   const bool expand = c >= 0 && last[c] - first[c] + 1 > L;
   if (!expand) {
     int r, k;
     child_meta(c, first, last, L, r, k);
     code[0] = node_code(r, k);
     code[1] = kNoChild;
+    rep[0] = (unsigned)(c >= 0 ? first[c] : ~c);
+    rep[1] = 0u;
     for (int a = 0; a < 3; ++a) {
       lo[0][a] = clo[a];
       hi[0][a] = chi[a];
@@ -526,6 +584,7 @@ __device__ inline void wide_slots(int c, const float clo[3], const float chi[3],
     int r, k;
     child_meta(g[j], first, last, L, r, k);
     code[j] = node_code(r, k);
+    rep[j] = (unsigned)(g[j] >= 0 ? first[g[j]] : ~g[j]);
     load_box(g[j] >= 0 ? ibox + 2 * g[j] : leafbox + 2 * (int64_t)(~g[j]), lo[j], hi[j]);
   }
 }
@@ -617,9 +676,9 @@ __global__ void k_emit(int64_t n, int L, const int* left, const int* right, cons
   load_box(cl >= 0 ? ibox + 2 * cl : leafbox + 2 * (int64_t)(~cl), lo0, hi0);
   load_box(cr >= 0 ? ibox + 2 * cr : leafbox + 2 * (int64_t)(~cr), lo1, hi1);
   float lo[4][3], hi[4][3];
-  unsigned code[4];
-  wide_slots(cl, lo0, hi0, left, right, first, last, L, leafbox, ibox, lo, hi, code);
-  wide_slots(cr, lo1, hi1, left, right, first, last, L, leafbox, ibox, lo + 2, hi + 2, code + 2);
+  unsigned code[4], rep[4];
+  wide_slots(cl, lo0, hi0, left, right, first, last, L, leafbox, ibox, lo, hi, code, rep);
+  wide_slots(cr, lo1, hi1, left, right, first, last, L, leafbox, ibox, lo + 2, hi + 2, code + 2, rep + 2);
   BvhNode nd;
   nd.lox = make_float4(lo[0][0], lo[1][0], lo[2][0], lo[3][0]);
   nd.loy = make_float4(lo[0][1], lo[1][1], lo[2][1], lo[3][1]);
@@ -628,7 +687,7 @@ __global__ void k_emit(int64_t n, int L, const int* left, const int* right, cons
   nd.hiy = make_float4(hi[0][1], hi[1][1], hi[2][1], hi[3][1]);
   nd.hiz = make_float4(hi[0][2], hi[1][2], hi[2][2], hi[3][2]);
   nd.code = make_uint4(code[0], code[1], code[2], code[3]);
-  nd.pad = make_uint4(0, 0, 0, 0);
+  nd.rep = make_uint4(rep[0], rep[1], rep[2], rep[3]);
   nodes[node] = nd;
 }
 
@@ -654,7 +713,7 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
   nd.hiy = make_float4(hi[1], -I, -I, -I);
   nd.hiz = make_float4(hi[2], -I, -I, -I);
   nd.code = make_uint4(node_code(0, (int)n), kNoChild, kNoChild, kNoChild);
-  nd.pad = make_uint4(0, 0, 0, 0);
+  nd.rep = make_uint4(0, 0, 0, 0);
   nodes[0] = nd;
 }
 
@@ -787,18 +846,22 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
                  256 * kMaxSortPasses);
   HD_TRY_LAUNCH();
 
+  if (!(fused && rs_rounds == 4)) HD_TRY(fused ? rs_scatter_attr<true>() : rs_scatter_attr<false>());
   for (int shift = 0, pass = 0; shift < 3 * bits; shift += 8, ++pass) {
     if (fused && rs_rounds == 4) {
       launch_chained(k_rs_hist<4, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, (unsigned*)nullptr);
-      launch_chained(k_rs_scatter<4, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_scatter<4, true>, nblk, RS_THREADS, rs_scatter_smem<4>(), s, k0, v0, k1, v1, n, shift, hist,
+                     nblk);
     } else if (fused) {
       launch_chained(k_rs_hist<16, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, (unsigned*)nullptr);
-      launch_chained(k_rs_scatter<16, true>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_scatter<16, true>, nblk, RS_THREADS, rs_scatter_smem<16>(), s, k0, v0, k1, v1, n, shift,
+                     hist, nblk);
     } else {
       unsigned* tp = tot + 256 * pass;
       launch_chained(k_rs_hist<16, false>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, tp);
       launch_chained(k_rs_scan_digits, 256, 256, 0, s, hist, nblk, (const unsigned*)tp);
-      launch_chained(k_rs_scatter<16, false>, nblk, RS_THREADS, 0, s, k0, v0, k1, v1, n, shift, hist, nblk);
+      launch_chained(k_rs_scatter<16, false>, nblk, RS_THREADS, rs_scatter_smem<16>(), s, k0, v0, k1, v1, n, shift,
+                     hist, nblk);
     }
     HD_TRY_LAUNCH();
     std::swap(k0, k1);

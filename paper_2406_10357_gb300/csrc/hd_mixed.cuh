@@ -257,7 +257,8 @@ struct NearestM {
   const float4* tri32;
   float best_hi = INFINITY;
   float dlo = INFINITY;
-  float cut = -1.f;  // the traversal may stop once best_hi < cut (cut_radius)
+  float cut = -1.f;   // the traversal may stop once best_hi < cut (cut_radius)
+  float cut2 = -1.f;  // cut squared, for the farthest-point box test
   int best = -1;
   F3 q = {0.f, 0.f, 0.f};
   float qerr = 0.f;
@@ -369,6 +370,15 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
       float e3 = box_lo2(plo, phi, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w);
       unsigned c0 = cd.x, c1 = cd.y, c2 = cd.z, c3 = cd.w;
       c.boxes += (c0 != kNoChild) + (c1 != kNoChild) + (c2 != kNoChild) + (c3 != kNoChild);
+      int pick = -1;  // kCut: a triangle of a child whose whole box lies within the cut radius
+      if constexpr (kCut) {
+        const float px = t.P.h.x, py = t.P.h.y, pz = t.P.h.z;
+        const uint4 rp = __ldg(reinterpret_cast<const uint4*>(np + 7));
+        if (c3 != kNoChild && box_far2(px, py, pz, lx.w, ly.w, lz.w, hx.w, hy.w, hz.w) < t.cut2) pick = (int)rp.w;
+        if (c2 != kNoChild && box_far2(px, py, pz, lx.z, ly.z, lz.z, hx.z, hy.z, hz.z) < t.cut2) pick = (int)rp.z;
+        if (c1 != kNoChild && box_far2(px, py, pz, lx.y, ly.y, lz.y, hx.y, hy.y, hz.y) < t.cut2) pick = (int)rp.y;
+        if (c0 != kNoChild && box_far2(px, py, pz, lx.x, ly.x, lz.x, hx.x, hy.x, hz.x) < t.cut2) pick = (int)rp.x;
+      }
       if (!(e0 <= r2) || c0 == kNoChild) e0 = INFINITY;
       if (!(e1 <= r2) || c1 == kNoChild) e1 = INFINITY;
       if (!(e2 <= r2) || c2 == kNoChild) e2 = INFINITY;
@@ -383,6 +393,17 @@ __device__ inline void traverse_m(const BvhDev& B, NearestM& t, Counters& c, boo
       push_code(stack_code, stack_d, sp, c3, e3, c);
       push_code(stack_code, stack_d, sp, c2, e2, c);
       push_code(stack_code, stack_d, sp, c1, e1, c);
+      if constexpr (kCut) {
+        if (pick >= 0) {
+          // test that one triangle; the check before the next pop then stops the query (should
+          // its certified distance miss the cut by a rounding, the children are all pushed)
+          push_code(stack_code, stack_d, sp, c0, e0, c);
+          lfirst = pick;
+          lcount = 1;
+          node = -1;
+          continue;
+        }
+      }
       if (e0 < INFINITY) {
         const int cnt = code_count(c0), ref = code_ref(c0);
         if (cnt > 0) {
@@ -870,6 +891,19 @@ struct PolicyM {
     return U - l <= 4.0 * (double)err + ldexp(U, -18);
   }
 
+  // a float input vertex is its own float pair (residual 0), with no FP64 arithmetic
+  __device__ static void set_pos_f(Vtx& v, float x, float y, float z) {
+    v.hx = x;
+    v.hy = y;
+    v.hz = z;
+    v.lx = v.ly = v.lz = 0.f;
+  }
+  // the longest edge at the vertex (cut_radius) lives in pad0
+  static constexpr bool kEdgePerVertex = true;
+  __device__ static void set_edge(Vtx& v, float e) { v.pad0 = e; }
+  __device__ static double cut_r(double l, const DynParams*, const Vtx& v) {
+    return cut_radius(l, (double)v.pad0 * (1.0 + 0x1p-20));
+  }
   __device__ static void set_pos(Vtx& v, double x, double y, double z) {
     v.hx = (float)x;
     v.hy = (float)y;
@@ -894,11 +928,12 @@ struct PolicyM {
       t.P = pos(v);
       if (v.hint >= 0) t.test1(v.hint);
       t.cut = cut_bound(B, cut_r);
+      if (t.cut > 0.f) t.cut2 = __fmul_rd(t.cut, t.cut);
     } else {
       t.P = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
     }
     bool unfinished = false, cut = active && t.best_hi < t.cut;  // the hint may be close enough
-    if (cut_r > 0.0)  // the same for every lane of the warp
+    if (__any_sync(0xffffffffu, t.cut > 0.f))  // one instantiation for the whole warp
       traverse_m<true>(B, t, c, active && !cut, budget, unfinished, cut);
     else
       traverse_m<false>(B, t, c, active, budget, unfinished, cut);
@@ -993,7 +1028,10 @@ struct PolicyM {
     m.qerr = m.dhi = m.dlo = 0.f;
     m.tri = -2;
     m.hint = a.tri;
-    m.pad0 = m.pad1 = 0.f;
+    // every edge of a sub-triangle at m is at most the longest edge at a or at b (each edge
+    // of the parent touches a or b)
+    m.pad0 = fmaxf(a.pad0, b.pad0);
+    m.pad1 = 0.f;
   }
   // upper_bound for the paper's cascade order with u4 deferred (only valid for those
   // options; the kernels pick it on the host): u4 comes later, so the footpoints are not read
