@@ -229,14 +229,15 @@ def profiled_traffic(kernel: str, workload: str):
 
 def build_launches(nB: int, leaf_size: int = 1) -> int:
     """Kernels one hd_build_B launches; the sequence is fixed by n_B: centroids, Morton codes,
-    per sort pass a digit count and a scatter (plus a scan when B needs more than 64 sort
+    per sort pass (8 code bits each, the code's last 1 or 2 bits dropped) a digit count and a scatter (plus a scan when B needs more than 64 sort
     tiles), the gather, then the radix tree, the aligned-block boxes (one launch per 8
     levels), the node boxes and the node emission (one root kernel instead when B fits in one
     leaf), and B's eta and validity."""
     bits = 10
     while bits < 16 and (1 << (3 * (bits - 4))) < nB:
         bits += 1
-    passes = -(-3 * bits // 8)
+    drop = (3 * bits) % 8 if (3 * bits) % 8 <= 2 else 0  # low code bits that would take a pass alone
+    passes = -(-(3 * bits - drop) // 8)
     tile = 256 * (4 if nB <= 64 * 256 * 4 else 16)
     fused = -(-nB // tile) <= 64
     levels = max(1, (nB - 1).bit_length())  # aligned-block levels, 8 per launch

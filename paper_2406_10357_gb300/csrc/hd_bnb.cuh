@@ -472,55 +472,72 @@ __global__ void __launch_bounds__(32 * kCoopWarps, P::kCoopBlocks) k_query_long(
 // kSortBuckets cells): per-cell counts, their exclusive scan, then each index to its cell's next
 // slot (the order within a cell is arbitrary).  Lists shorter than kSortMin are left as they are
 // (every kernel returns at once; uniform over the grid).
+//
+// The cell of a handed-off query in the reordered list: with cuts, the queries whose best
+// triangle so far is not yet within their cut radius (those that must traverse, the costly
+// ones) take the first half of the cells, so that the cooperative pass starts them first and
+// the cheap ones fill in behind (the Morton code then loses its lowest bit).  l does not
+// change between k_long_hist and k_long_scatter, so both find the same cell.
+template <class P>
+__device__ inline unsigned long_cell(const BvhDev& B, const typename P::Vtx& v, const RunState* st,
+                                     const DynParams* dyn) {
+  const D3 x = P::exact_pos(v);
+  const unsigned m = long_bucket(B, (float)x.x, (float)x.y, (float)x.z);
+  if (!cut_on(dyn)) return m;
+  const bool cheap = P::hint_within(B, v, P::cut_r(read_lower(st), dyn, v));
+  return (cheap ? kSortBuckets / 2 : 0u) + (m >> 1);
+}
+
 template <class P>
 __global__ void k_long_hist(BvhDev B, const typename P::Vtx* pool, LongList ll, const RunState* st,
-                            bool round_midpoints) {
+                            bool round_midpoints, const DynParams* dyn) {
   grid_dep_wait();
   grid_dep_launch();
   if (round_midpoints && st->stop) return;
   const int n = min(st->n_long, ll.cap);
   if (n < kSortMin) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const D3 x = P::exact_pos(pool[ll.idx[i]]);
-    atomicAdd(&ll.buckets[long_bucket(B, (float)x.x, (float)x.y, (float)x.z)], 1u);
-  }
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    atomicAdd(&ll.buckets[long_cell<P>(B, pool[ll.idx[i]], st, dyn)], 1u);
 }
 
-// One block of 1024 threads; each scans 32 consecutive counters.
+// Exclusive scan of the cell counts: one block of 1024 threads, kSortBuckets / 1024 rows of
+// 1024 consecutive counters, each row scanned across the block (coalesced) and carried on.
 static __global__ void k_long_scan(LongList ll, const RunState* st, bool round_midpoints) {
   grid_dep_wait();
   grid_dep_launch();
   if (round_midpoints && st->stop) return;
   if (min(st->n_long, ll.cap) < kSortMin) return;
-  constexpr int per = kSortBuckets / 1024;
-  __shared__ unsigned part[1024];
-  unsigned v[per];
-  unsigned sum = 0;
-  const int b = threadIdx.x * per;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    v[k] = ll.buckets[b + k];
-    sum += v[k];
-  }
-  part[threadIdx.x] = sum;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan of the 1024 partial sums
-    const unsigned y = threadIdx.x >= o ? part[threadIdx.x - o] : 0u;
+  __shared__ unsigned wtot[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned carry = 0;
+  for (int row = 0; row < kSortBuckets / 1024; ++row) {
+    const int i = row * 1024 + threadIdx.x;
+    const unsigned v = ll.buckets[i];
+    unsigned x = v;  // inclusive warp scan
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wtot[w] = x;
     __syncthreads();
-    part[threadIdx.x] += y;
+    if (w == 0) {  // the warps' totals, scanned
+      unsigned t = wtot[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wtot[lane] = t;
+    }
     __syncthreads();
-  }
-  unsigned run = threadIdx.x ? part[threadIdx.x - 1] : 0u;
-#pragma unroll
-  for (int k = 0; k < per; ++k) {
-    ll.buckets[b + k] = run;
-    run += v[k];
+    ll.buckets[i] = carry + (w ? wtot[w - 1] : 0u) + x - v;
+    carry += wtot[31];
+    __syncthreads();  // wtot is written again by the next row
   }
 }
 
 template <class P>
 __global__ void k_long_scatter(BvhDev B, const typename P::Vtx* pool, LongList ll, const RunState* st,
-                               bool round_midpoints) {
+                               bool round_midpoints, const DynParams* dyn) {
   grid_dep_wait();
   grid_dep_launch();
   if (round_midpoints && st->stop) return;
@@ -528,8 +545,7 @@ __global__ void k_long_scatter(BvhDev B, const typename P::Vtx* pool, LongList l
   if (n < kSortMin) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int k = ll.idx[i];
-    const D3 x = P::exact_pos(pool[k]);
-    const unsigned pos = atomicAdd(&ll.buckets[long_bucket(B, (float)x.x, (float)x.y, (float)x.z)], 1u);
+    const unsigned pos = atomicAdd(&ll.buckets[long_cell<P>(B, pool[k], st, dyn)], 1u);
     ll.sorted[pos] = k;  // pos < n: the cells' counts sum to n
   }
 }
@@ -538,11 +554,11 @@ __global__ void k_long_scatter(BvhDev B, const typename P::Vtx* pool, LongList l
 // (nothing happens on the device for short lists).
 template <class P>
 void sort_long(const BvhDev& B, const typename P::Vtx* pool, const LongList& ll, const RunState* st,
-               bool round_midpoints, int sms, cudaStream_t s) {
+               bool round_midpoints, int sms, cudaStream_t s, const DynParams* dyn) {
   if (!ll.sorted) return;
-  launch_chained(k_long_hist<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints);
+  launch_chained(k_long_hist<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints, dyn);
   launch_chained(k_long_scan, 1, 1024, 0, s, ll, st, round_midpoints);
-  launch_chained(k_long_scatter<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints);
+  launch_chained(k_long_scatter<P>, (unsigned)sms * 4, 256, 0, s, B, pool, ll, st, round_midpoints, dyn);
 }
 
 // Per-thread outcome counts and maxima of classified items, flushed once per warp.
@@ -1589,7 +1605,7 @@ int loop_rounds(const RunIO& io, Rounds<P>& R, RunState* st, HostRes& hr, const 
     }
     {
       TraceScope tr(HD_K_LONG, s);
-      sort_long<P>(B, R.pool, R.longq, st, true, sms, s);
+      sort_long<P>(B, R.pool, R.longq, st, true, sms, s, rp.dyn);
       launch_chained(k_query_long<P>, grid_long, 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, true);
     }
     {
@@ -1753,7 +1769,7 @@ int finish_in_fp64(const RunIO& io, Rounds<P>& RM, int64_t n_pro, RunState* st, 
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    sort_long<PolicyD>(B, D.pool, D.longq, st, false, sms, s);
+    sort_long<PolicyD>(B, D.pool, D.longq, st, false, sms, s, rp.dyn);
     launch_chained(k_query_long<PolicyD>, long_grid<PolicyD>(), 32 * kCoopWarps, 0, s, B, D.pool, D.longq, st, rp.slack,
                    rp.dyn, false);
   }
@@ -1845,7 +1861,7 @@ int run_bnb(const RunIO& io) {
   }
   {
     TraceScope tr(HD_K_LONG, s);
-    sort_long<P>(B, R.pool, R.longq, st, false, sms, s);
+    sort_long<P>(B, R.pool, R.longq, st, false, sms, s, rp.dyn);
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, R.pool, R.longq, st, rp.slack, rp.dyn, false);
   }
   HD_TRY_LAUNCH();
@@ -1967,7 +1983,7 @@ void query_points(const BvhDev& B, typename P::Vtx* rec, int64_t n, RunState* st
       int dev = 0, sms = 1;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      sort_long<P>(B, rec, ll, st, false, sms, s);
+      sort_long<P>(B, rec, ll, st, false, sms, s, nullptr);
     }
     launch_chained(k_query_long<P>, long_grid<P>(), 32 * kCoopWarps, 0, s, B, rec, ll, st, 0.0, nullptr, false);
   } else {

@@ -444,6 +444,11 @@ struct PolicyD {
   __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
   __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
   __device__ static void set_pos_f(Vtx& v, float x, float y, float z) { set_pos(v, x, y, z); }
+  // whether a handed-off query's best triangle so far (hint, d = its squared distance) is
+  // already within the cut radius cut_r
+  __device__ static bool hint_within(const BvhDev&, const Vtx& v, double cut_r) {
+    return v.hint >= 0 && cut_r > 0.0 && v.d < cut_r * cut_r;
+  }
   // no room in the vertex for its own edge bound: the longest edge of A for every vertex
   static constexpr bool kEdgePerVertex = false;
   __device__ static void set_edge(Vtx&, float) {}

@@ -147,7 +147,7 @@ __device__ inline uint64_t spread16(uint32_t v) {  // 16 bits -> every third bit
 }
 
 // Also zeroes the `ntot` digit totals of the sort passes that follow.
-__global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, int bits, uint64_t* keys,
+__global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, int bits, int drop, uint64_t* keys,
                          uint32_t* vals, unsigned* tot, int ntot) {
   grid_dep_wait();
   grid_dep_launch();
@@ -165,7 +165,7 @@ __global__ void k_morton(const float4* cent, int64_t nF, const unsigned* cbox, i
     float u = ext > 0.f ? (cc[k] - lo) * (cells / ext) : 0.5f * cells;
     q[k] = (uint32_t)fminf(fmaxf(u, 0.f), cells - 1.f);
   }
-  keys[f] = (spread16(q[0]) << 2) | (spread16(q[1]) << 1) | spread16(q[2]);
+  keys[f] = ((spread16(q[0]) << 2) | (spread16(q[1]) << 1) | spread16(q[2])) >> drop;
   vals[f] = (uint32_t)f;
 }
 
@@ -839,15 +839,18 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
                               : launch_prep<float>(B, V, F, cent, misc, (int*)(misc + 6), sms, s);
   if (rc != HD_OK) return rc;
   // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
-  // least 10 and at most 16 (3 x 16 = 48-bit codes); the sort runs ceil(3 bits / 8) passes
+  // least 10 and at most 16 (3 x 16 = 48-bit codes); the code's lowest 1 or 2 bits are dropped
+  // when they would take a sort pass of their own (33 bits -> 32: four passes instead of
+  // five; equal codes keep their input order), and the sort runs ceil(key bits / 8) passes
   int bits = 10;
   while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
-  launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, k0, v0, tot,
+  const int drop = (3 * bits) % 8 <= 2 ? (3 * bits) % 8 : 0, key_bits = 3 * bits - drop;
+  launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, drop, k0, v0, tot,
                  256 * kMaxSortPasses);
   HD_TRY_LAUNCH();
 
   if (!(fused && rs_rounds == 4)) HD_TRY(fused ? rs_scatter_attr<true>() : rs_scatter_attr<false>());
-  for (int shift = 0, pass = 0; shift < 3 * bits; shift += 8, ++pass) {
+  for (int shift = 0, pass = 0; shift < key_bits; shift += 8, ++pass) {
     if (fused && rs_rounds == 4) {
       launch_chained(k_rs_hist<4, true>, nblk, RS_THREADS, 0, s, k0, n, shift, hist, nblk, (unsigned*)nullptr);
       launch_chained(k_rs_scatter<4, true>, nblk, RS_THREADS, rs_scatter_smem<4>(), s, k0, v0, k1, v1, n, shift, hist,

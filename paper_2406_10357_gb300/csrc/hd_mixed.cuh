@@ -957,6 +957,11 @@ struct PolicyM {
     }
     finish(B, v, t.best, t.best_hi, t.dlo, t.q, t.qerr);
   }
+  // Whether a handed-off query's best triangle so far (hint, dhi without eta) is already
+  // within the cut radius cut_r.
+  __device__ static bool hint_within(const BvhDev& B, const Vtx& v, double cut_r) {
+    return v.hint >= 0 && v.dhi < cut_bound(B, cut_r);
+  }
   // The bound on best_hi (the certified distance to B's float triangles, before eta) below
   // which a query stops: best_hi + eta < cut_r, rounded so that it holds in exact arithmetic.
   __device__ static float cut_bound(const BvhDev& B, double cut_r) {
