@@ -507,12 +507,17 @@ static __global__ void k_long_scan(LongList ll, const RunState* st, bool round_m
   grid_dep_launch();
   if (round_midpoints && st->stop) return;
   if (min(st->n_long, ll.cap) < kSortMin) return;
+  constexpr int kRows = kSortBuckets / 1024;
   __shared__ unsigned wtot[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned val[kRows];  // every row's counter first: the loads overlap instead of one per row
+#pragma unroll
+  for (int row = 0; row < kRows; ++row) val[row] = ll.buckets[row * 1024 + threadIdx.x];
   unsigned carry = 0;
-  for (int row = 0; row < kSortBuckets / 1024; ++row) {
+#pragma unroll
+  for (int row = 0; row < kRows; ++row) {
     const int i = row * 1024 + threadIdx.x;
-    const unsigned v = ll.buckets[i];
+    const unsigned v = val[row];
     unsigned x = v;  // inclusive warp scan
     for (int o = 1; o < 32; o <<= 1) {
       const unsigned y = __shfl_up_sync(0xffffffffu, x, o);
