@@ -238,7 +238,7 @@ def build_launches(nB: int, leaf_size: int = 1) -> int:
         bits += 1
     drop = (3 * bits) % 8 if (3 * bits) % 8 <= 2 else 0  # low code bits that would take a pass alone
     passes = -(-(3 * bits - drop) // 8)
-    tile = 256 * (4 if nB <= 64 * 256 * 4 else 16)
+    tile = 256 * (4 if nB <= 64 * 256 * 4 else 8)
     fused = -(-nB // tile) <= 64
     levels = max(1, (nB - 1).bit_length())  # aligned-block levels, 8 per launch
     return 2 + passes * (2 if fused else 3) + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1) + 1
