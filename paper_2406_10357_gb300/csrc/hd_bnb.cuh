@@ -278,6 +278,9 @@ constexpr int kSortMin = 2048;                         // shorter lists keep the
 #define HD_LONG_CHUNK 4
 #endif
 constexpr int kLongChunk = HD_LONG_CHUNK;              // consecutive sorted queries per warp step
+#ifndef HD_LONG_LPT
+#define HD_LONG_LPT 1  // with cuts: the costly handed-off queries first, largest distance first (long_cell)
+#endif
 
 __device__ inline unsigned spread5(unsigned x) {  // bits 0..4 of x to bits 0, 3, 6, 9, 12
   x &= 31u;
@@ -421,7 +424,8 @@ __device__ inline void query_long_body(BvhDev B, typename P::Vtx* pool, LongList
   // a sorted list is taken kLongChunk neighbouring queries at a time
   const bool sorted = ll.sorted && n >= kSortMin;
   const int* list = sorted ? ll.sorted : ll.idx;
-  const int chunk = sorted ? kLongChunk : 1;
+  // (ordered by cost with cuts: one at a time, so that the costly ones spread over the warps)
+  const int chunk = sorted && !(HD_LONG_LPT && cut_on(dyn)) ? kLongChunk : 1;
   const bool cutting = HD_CUT_LONG && cut_on(dyn);
   Counters c;
   double lmax = 0.0;
@@ -473,10 +477,12 @@ __global__ void __launch_bounds__(32 * kCoopWarps, P::kCoopBlocks) k_query_long(
 // slot (the order within a cell is arbitrary).  Lists shorter than kSortMin are left as they are
 // (every kernel returns at once; uniform over the grid).
 //
-// The cell of a handed-off query in the reordered list: with cuts, the queries whose best
-// triangle so far is not yet within their cut radius (those that must traverse, the costly
-// ones) take the first half of the cells, so that the cooperative pass starts them first and
-// the cheap ones fill in behind (the Morton code then loses its lowest bit).  l does not
+// The cell of a handed-off query in the reordered list.  Without cuts: its Morton cell.  With
+// cuts, the queries whose best triangle so far is not yet within their cut radius (those that
+// must traverse) take the first half of the cells, ordered by that triangle's distance r,
+// largest first: a far query's search ball holds the most boxes, and starting the costliest
+// first keeps the pass from ending on a few warps still working (longest job first).  The
+// cheap ones fill in behind in Morton order (the code loses its lowest bit).  l does not
 // change between k_long_hist and k_long_scatter, so both find the same cell.
 template <class P>
 __device__ inline unsigned long_cell(const BvhDev& B, const typename P::Vtx& v, const RunState* st,
@@ -484,8 +490,13 @@ __device__ inline unsigned long_cell(const BvhDev& B, const typename P::Vtx& v, 
   const D3 x = P::exact_pos(v);
   const unsigned m = long_bucket(B, (float)x.x, (float)x.y, (float)x.z);
   if (!cut_on(dyn)) return m;
-  const bool cheap = P::hint_within(B, v, P::cut_r(read_lower(st), dyn, v));
-  return (cheap ? kSortBuckets / 2 : 0u) + (m >> 1);
+  const double l = read_lower(st);
+  if (P::hint_within(B, v, P::cut_r(l, dyn, v))) return kSortBuckets / 2 + (m >> 1);
+  if (!HD_LONG_LPT) return m >> 1;
+  // r in [0, 2 l) over the half's cells, larger r first
+  constexpr unsigned kHalf = kSortBuckets / 2;
+  const double q = l > 0.0 ? P::hint_dist(v) / (2.0 * l) * kHalf : 0.0;
+  return kHalf - 1u - (unsigned)fmin(fmax(q, 0.0), (double)(kHalf - 1));
 }
 
 template <class P>

@@ -444,6 +444,8 @@ struct PolicyD {
   __device__ static D3 exact_pos(const Vtx& v) { return {v.x, v.y, v.z}; }
   __device__ static bool promote(const Vtx&, const Vtx&, const Vtx&, double, double) { return false; }
   __device__ static void set_pos_f(Vtx& v, float x, float y, float z) { set_pos(v, x, y, z); }
+  // the distance of a handed-off query's best triangle so far (d holds its square then)
+  __device__ static double hint_dist(const Vtx& v) { return sqrt(v.d); }
   // whether a handed-off query's best triangle so far (hint, d = its squared distance) is
   // already within the cut radius cut_r
   __device__ static bool hint_within(const BvhDev&, const Vtx& v, double cut_r) {

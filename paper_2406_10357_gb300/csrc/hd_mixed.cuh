@@ -957,6 +957,8 @@ struct PolicyM {
     }
     finish(B, v, t.best, t.best_hi, t.dlo, t.q, t.qerr);
   }
+  // The distance bound of a handed-off query's best triangle so far.
+  __device__ static double hint_dist(const Vtx& v) { return v.dhi; }
   // Whether a handed-off query's best triangle so far (hint, dhi without eta) is already
   // within the cut radius cut_r.
   __device__ static bool hint_within(const BvhDev& B, const Vtx& v, double cut_r) {
