@@ -1308,7 +1308,7 @@ struct RunIO {
   double l0;  // a known lower bound to start l from (0: none)
 };
 
-inline BvhDev bvh_dev(const hd_bvh* B) { return {B->nodes, B->tri32, B->tri64, B->tri_vid, B->nF, B->meta}; }
+inline BvhDev bvh_dev(const hd_bvh* B) { return {B->nodes, B->tri32, B->tri64, B->tri_vid, B->nF, B->meta, B->grid}; }
 
 inline double bits_to_double(unsigned long long b) {
   double d;

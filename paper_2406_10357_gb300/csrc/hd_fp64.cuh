@@ -378,7 +378,10 @@ struct PolicyD {
     t.tri64 = B.tri64;
     t.tri32 = B.tri32;
     if (cut_r > 0.0) t.cut2 = cut_r * cut_r;
-    if (v.hint >= 0) t.test1(v.hint);
+    // start from the hint, or from a triangle of the point's grid cell (a first radius)
+    const int h0 = v.hint >= 0 ? v.hint : grid_hint(B, (float)v.x, (float)v.y, (float)v.z);
+    if (h0 >= 0) t.test1(h0);
+    if (v.hint < 0 && h0 >= 0 && budget < INT_MAX) ++budget;  // the grid's triangle is not the traversal's
     const int how = cut_r > 0.0 ? traverse<true>(B, t.p, t, c, budget) : traverse<false>(B, t.p, t, c, budget);
     c.leaf += t.evals;
     if (how == kTravCut && was_cut) *was_cut = true;

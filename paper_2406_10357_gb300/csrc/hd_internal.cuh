@@ -60,7 +60,12 @@ struct hd_bvh {
   int* inv;            // original face index -> sorted position
   float eta;           // max distance between a float vertex of tri32 and its input value (0 for f32
                        // input); the host copy, valid once the build has been waited for
-  float* meta;         // device: [0] eta as above, [1] nonzero if B was invalid (as bits)
+  float* meta;         // device: [0] eta as above, [1] nonzero if B was invalid (as bits), [4..9] the
+                       // centroid box of the Morton codes (lo xyz, hi xyz), [10] bits per axis,
+                       // [11] bits per axis of the hint grid (as int bits)
+  int* grid;           // hint grid: per coarse Morton cell, one triangle whose centroid lies in it
+                       // (the first in BVH order), or -1
+  int grid_bits;       // bits per axis of the hint grid (8^grid_bits cells)
 };
 
 namespace hd {
@@ -149,7 +154,38 @@ struct BvhDev {
   const int4* tri_vid;
   int64_t nF;
   const float* meta;  // [0] eta: max distance between a float vertex of tri32 and its input
+  const int* grid;    // the hint grid (hd_bvh::grid), or null
 };
+
+// 10 bits -> every third bit of 30 (the Morton interleave of the build's codes)
+__device__ inline unsigned spread10(unsigned v) {
+  unsigned x = v & 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+// A triangle of B near p to start a query from, when it has no hint of its own: the grid
+// cell of p in the quantisation of the build's Morton codes, coarsened to the hint grid's
+// bits (every index stays in range: the cell coordinates are clamped to the grid).  -1: none.
+__device__ inline int grid_hint(const BvhDev& B, float px, float py, float pz) {
+  if (B.grid == nullptr) return -1;
+  const float4 m1 = __ldg(reinterpret_cast<const float4*>(B.meta) + 1);  // lo xyz, hi x
+  const float4 m2 = __ldg(reinterpret_cast<const float4*>(B.meta) + 2);  // hi yz, bits, grid bits
+  const int bits = __float_as_int(m2.z), gbits = __float_as_int(m2.w);
+  const float cells = (float)(1u << bits);
+  const float lo[3] = {m1.x, m1.y, m1.z}, hi[3] = {m1.w, m2.x, m2.y}, p[3] = {px, py, pz};
+  unsigned q[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float ext = hi[k] - lo[k];
+    const float u = ext > 0.f ? (p[k] - lo[k]) * (cells / ext) : 0.5f * cells;
+    q[k] = ((unsigned)fminf(fmaxf(u, 0.f), cells - 1.f)) >> (bits - gbits);  // NaN -> 0
+  }
+  return __ldg(B.grid + ((spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2])));
+}
 
 // Per-run values that are only known on the device (they depend on A's bounding box):
 // written by k_prep_finish, read by every round kernel, so that no host round trip is needed

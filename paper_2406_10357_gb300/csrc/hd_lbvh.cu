@@ -725,7 +725,7 @@ __global__ void k_root_leaf(int64_t n, const float4* leafbox, BvhNode* nodes) {
 
 // eta (the largest distance between a float vertex of tri32 and its input value, the
 // square root of the gathered squared maximum, rounded up) and the validity flag of B.
-__global__ void k_build_meta(const unsigned* misc, float* meta) {
+__global__ void k_build_meta(const unsigned* misc, float* meta, int bits, int gbits) {
   grid_dep_wait();
   grid_dep_launch();
   const double r = sqrt((double)__uint_as_float(misc[7])) * (1.0 + 1e-15);
@@ -733,6 +733,20 @@ __global__ void k_build_meta(const unsigned* misc, float* meta) {
   meta[1] = __uint_as_float(misc[6] != 0u ? 1u : 0u);
   meta[2] = 0.f;
   meta[3] = 0.f;
+  for (int k = 0; k < 6; ++k) meta[4 + k] = ordered_to_float(misc[k]);  // the Morton codes' box
+  meta[10] = __int_as_float(bits);
+  meta[11] = __int_as_float(gbits);
+}
+
+// The hint grid from the sorted codes: the first triangle of every coarse cell that holds one
+// (a cell's triangles are contiguous in BVH order).
+__global__ void k_grid(const uint64_t* keys, int64_t n, int shift, int* grid) {
+  grid_dep_wait();
+  grid_dep_launch();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint64_t c = keys[i] >> shift;
+  if (i == 0 || (keys[i - 1] >> shift) != c) grid[c] = (int)i;
 }
 
 template <typename T>
@@ -766,9 +780,21 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     F = Ftmp;
   }
 
+  // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
+  // least 10 and at most 16 (3 x 16 = 48-bit codes); the code's lowest 1 or 2 bits are dropped
+  // when they would take a sort pass of their own (33 bits -> 32: four passes instead of
+  // five; equal codes keep their input order), and the sort runs ceil(key bits / 8) passes
+  int bits = 10;
+  while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
+  const int drop = (3 * bits) % 8 <= 2 ? (3 * bits) % 8 : 0, key_bits = 3 * bits - drop;
+  // the hint grid: about 2 triangles per coarse cell (gbits per axis, at most 10)
+  int gbits = 1;
+  while (gbits < 10 && gbits < bits - 1 && ((int64_t)1 << (3 * (gbits + 1) + 1)) <= n) ++gbits;
+
   hd_bvh* h = new hd_bvh();
   h->block = nullptr;
   h->meta = nullptr;
+  h->grid = nullptr;
   h->eta = 0.f;
   h->device = dev;
   h->nF = n;
@@ -782,8 +808,8 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     const size_t b_nodes = up(sizeof(BvhNode) * h->n_nodes), b_t32 = up(sizeof(float4) * 3 * n),
                  b_t64 = (h->input_f64 || HD_KEEP_TRI64) ? up(sizeof(double) * 9 * n) : 0, b_vid = up(sizeof(int4) * n),
                  b_inv = up(sizeof(int) * n),
-                 b_meta = up(4 * sizeof(float));
-    cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta, s);
+                 b_meta = up(16 * sizeof(float)), b_grid = up(sizeof(int) << (3 * gbits));
+    cudaError_t e = cudaMallocAsync(&h->block, b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta + b_grid, s);
     if (e != cudaSuccess) {
       delete h;
       return set_cuda_error(e, "cudaMallocAsync", __FILE__, __LINE__);
@@ -795,6 +821,8 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     h->tri_vid = (int4*)(c + b_nodes + b_t32 + b_t64);
     h->inv = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid);
     h->meta = (float*)(c + b_nodes + b_t32 + b_t64 + b_vid + b_inv);
+    h->grid = (int*)(c + b_nodes + b_t32 + b_t64 + b_vid + b_inv + b_meta);
+    h->grid_bits = gbits;
   }
 
   // scratch: one block, carved up
@@ -844,13 +872,6 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   int rc = B->vtype == HD_F64 ? launch_prep<double>(B, V, F, cent, misc, (int*)(misc + 6), sms, s)
                               : launch_prep<float>(B, V, F, cent, misc, (int*)(misc + 6), sms, s);
   if (rc != HD_OK) return rc;
-  // grid bits per axis: about 2^4 cells per triangle along each axis beyond n^(1/3), at
-  // least 10 and at most 16 (3 x 16 = 48-bit codes); the code's lowest 1 or 2 bits are dropped
-  // when they would take a sort pass of their own (33 bits -> 32: four passes instead of
-  // five; equal codes keep their input order), and the sort runs ceil(key bits / 8) passes
-  int bits = 10;
-  while (bits < 16 && ((int64_t)1 << (3 * (bits - 4))) < n) ++bits;
-  const int drop = (3 * bits) % 8 <= 2 ? (3 * bits) % 8 : 0, key_bits = 3 * bits - drop;
   launch_chained(k_morton, blocks_for(n, kThreads), kThreads, 0, s, cent, n, misc, bits, drop, k0, v0, tot,
                  256 * kMaxSortPasses);
   HD_TRY_LAUNCH();
@@ -876,6 +897,11 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     std::swap(k0, k1);
     std::swap(v0, v1);
   }
+
+  HD_TRY(cudaMemsetAsync(h->grid, 0xff, sizeof(int) << (3 * gbits), s));
+  launch_chained(k_grid, blocks_for(n, kThreads), kThreads, 0, s, (const uint64_t*)k0, n, 3 * (bits - gbits) - drop,
+                 h->grid);
+  HD_TRY_LAUNCH();
 
   int* canon = nullptr;
   if (weld) {
@@ -921,7 +947,7 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
   }
   HD_TRY_LAUNCH();
 
-  launch_chained(k_build_meta, 1, 1, 0, s, misc, h->meta);
+  launch_chained(k_build_meta, 1, 1, 0, s, misc, h->meta, bits, gbits);
   HD_TRY_LAUNCH();
   HD_TRY(cudaFreeAsync(scratch, s));
   if (Vtmp) HD_TRY(cudaFreeAsync(Vtmp, s));

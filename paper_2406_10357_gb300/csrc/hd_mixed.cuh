@@ -926,7 +926,11 @@ struct PolicyM {
     t.tri32 = B.tri32;
     if (active) {
       t.P = pos(v);
-      if (v.hint >= 0) t.test1(v.hint);
+      // start from the hint, or from a triangle of the point's grid cell: a first radius
+      // (often already within the cut radius)
+      const int h0 = v.hint >= 0 ? v.hint : grid_hint(B, t.P.h.x, t.P.h.y, t.P.h.z);
+      if (h0 >= 0) t.test1(h0);
+      if (v.hint < 0 && h0 >= 0 && budget < INT_MAX) ++budget;  // the grid's triangle is not the traversal's
       t.cut = cut_bound(B, cut_r);
       if (t.cut > 0.f) t.cut2 = __fmul_rd(t.cut, t.cut);
     } else {
