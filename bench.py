@@ -230,7 +230,7 @@ def profiled_traffic(kernel: str, workload: str):
 def build_launches(nB: int, leaf_size: int = 1) -> int:
     """Kernels one hd_build_B launches; the sequence is fixed by n_B: centroids, Morton codes,
     per sort pass (8 code bits each, the code's last 1 or 2 bits dropped) a digit count and a scatter (plus a scan when B needs more than 64 sort
-    tiles), the hint grid, the gather, then the radix tree, the aligned-block boxes (one launch per 8
+    tiles), the hint grid (cleared, then filled), the gather, then the radix tree, the aligned-block boxes (one launch per 8
     levels), the node boxes and the node emission (one root kernel instead when B fits in one
     leaf), and B's eta and validity."""
     bits = 10
@@ -241,7 +241,7 @@ def build_launches(nB: int, leaf_size: int = 1) -> int:
     tile = 256 * (4 if nB <= 64 * 256 * 4 else 8)
     fused = -(-nB // tile) <= 64
     levels = max(1, (nB - 1).bit_length())  # aligned-block levels, 8 per launch
-    return 2 + passes * (2 if fused else 3) + 1 + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1) + 1
+    return 2 + passes * (2 if fused else 3) + 2 + 1 + ((3 + -(-levels // 8)) if nB > leaf_size else 1) + 1
 
 
 def measured_peaks():

@@ -25,6 +25,9 @@ namespace hd {
 namespace {
 
 constexpr int kThreads = 256;
+#ifndef HD_GRID_MEMSET
+#define HD_GRID_MEMSET 0  // 1: clear the hint grid with cudaMemsetAsync instead of a chained kernel
+#endif
 #ifndef HD_KEEP_TRI64
 #define HD_KEEP_TRI64 0  // 1: keep the FP64 copy of B for float32 input too
 #endif
@@ -738,8 +741,14 @@ __global__ void k_build_meta(const unsigned* misc, float* meta, int bits, int gb
   meta[11] = __int_as_float(gbits);
 }
 
-// The hint grid from the sorted codes: the first triangle of every coarse cell that holds one
-// (a cell's triangles are contiguous in BVH order).
+// The hint grid from the sorted codes: -1 everywhere (k_grid_clear), then the first triangle
+// of every coarse cell that holds one (a cell's triangles are contiguous in BVH order).
+__global__ void k_grid_clear(int* grid, int64_t ncells) {
+  grid_dep_wait();
+  grid_dep_launch();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ncells; e += (int64_t)gridDim.x * blockDim.x)
+    grid[e] = -1;
+}
 __global__ void k_grid(const uint64_t* keys, int64_t n, int shift, int* grid) {
   grid_dep_wait();
   grid_dep_launch();
@@ -898,10 +907,17 @@ int build_bvh(const hd_mesh* B, const Opts& o, cudaStream_t s, hd_bvh** out) {
     std::swap(v0, v1);
   }
 
-  HD_TRY(cudaMemsetAsync(h->grid, 0xff, sizeof(int) << (3 * gbits), s));
-  launch_chained(k_grid, blocks_for(n, kThreads), kThreads, 0, s, (const uint64_t*)k0, n, 3 * (bits - gbits) - drop,
-                 h->grid);
-  HD_TRY_LAUNCH();
+  {
+    const int64_t ncells = (int64_t)1 << (3 * gbits);
+#if HD_GRID_MEMSET
+    HD_TRY(cudaMemsetAsync(h->grid, 0xff, sizeof(int) * ncells, s));
+#else
+    launch_chained(k_grid_clear, std::min<unsigned>(blocks_for(ncells, kThreads), 1024u), kThreads, 0, s, h->grid, ncells);
+#endif
+    launch_chained(k_grid, blocks_for(n, kThreads), kThreads, 0, s, (const uint64_t*)k0, n, 3 * (bits - gbits) - drop,
+                   h->grid);
+    HD_TRY_LAUNCH();
+  }
 
   int* canon = nullptr;
   if (weld) {
