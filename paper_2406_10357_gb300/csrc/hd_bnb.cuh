@@ -90,8 +90,9 @@ __device__ inline void flush_counters(RunState* st, const Counters& c, bool long
 // dA use only referenced ones, Section 5.3), the validity of F_A, and the largest squared
 // edge length of A's faces (for cut_radius; as the bits of a non-negative double, one
 // atomic per block that raises it), with `ev` the longest edge at each vertex.  Entry
-// i = 3 f + k is the edge from corner k of face f to corner k + 1.  Launched with 256 threads per block on a grid-stride loop (a bounded
-// grid, so that few blocks contend for the edge maximum).
+// i = 3 f + k is the edge from corner k of face f to corner k + 1.  Launched with 256 threads
+// per block on a grid-stride loop (a bounded grid, so that few blocks contend for the edge
+// maximum).
 template <typename T>
 __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t* ref, int* bad, const T* VA,
                            unsigned long long* e2max_bits, unsigned* ev) {
@@ -109,8 +110,9 @@ __global__ void k_mark_ref(const int32_t* FA, int64_t nFA, int64_t nVA, uint8_t*
     const int64_t f = i / 3;
     const int k = (int)(i - 3 * f);
     const int32_t w = FA[3 * f + (k == 2 ? 0 : k + 1)], u = FA[3 * f + (k == 0 ? 2 : k - 1)];
-    // in the input's precision (FP64 is slow on this GPU): float rounding of a float edge is
-    // ~2^-23 relative, covered by the margins k_prep_finish and cut_r add
+    // in the input's precision (FP64 runs at a small fraction of the FP32 rate on GB300):
+    // float rounding of a float edge is ~2^-23 relative, covered by the margins k_prep_finish
+    // and cut_r add
     const T vx = VA[3 * (int64_t)v], vy = VA[3 * (int64_t)v + 1], vz = VA[3 * (int64_t)v + 2];
     T xw = 0, xu = 0;  // the squared edges at this corner: to the next corner and the previous
     if (w >= 0 && w < nVA) {

@@ -63,9 +63,9 @@ constexpr int kCoopMinBlocks = HD_COOP_MIN_BLOCKS;
 // a few triangles).  6 against 10 on the large soup: lane pass 0.64 -> 0.55 ms, cooperative
 // pass 1.67 -> 1.72 ms (8% more queries handed off).
 constexpr int kLongBudget = HD_LONG_BUDGET;
-// The budget of a query that may be cut (cut_radius > 0): most such queries stop after a few
-// tests anyway, and the ones near the cut radius are cheaper to finish in the lane than to
-// restart in a warp.
+// The budget of a query that may be cut (cut_radius > 0).  On the large soup 6, 10, 16 and 32
+// tests took 1.49, 1.54, 1.68 and 1.97 ms per call: the queries that do not cut within a few
+// tests are the far ones, cheaper in a warp; so the default is the budget without cuts.
 #ifndef HD_LONG_BUDGET_CUT
 #define HD_LONG_BUDGET_CUT HD_LONG_BUDGET
 #endif

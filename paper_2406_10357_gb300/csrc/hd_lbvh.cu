@@ -58,7 +58,8 @@ __device__ inline bool load_face(const T* V, int64_t nV, const int32_t* F, int64
 }
 
 // The same for float input, in float: a float vertex is exact as it is, and FP64 arithmetic
-// is slow on this GPU (the build's per-triangle FP64 work dominated its time).
+// runs at a small fraction of the FP32 rate on GB300 (the build's per-triangle FP64 work
+// dominated its time).
 struct F3v {
   float x, y, z;
 };
