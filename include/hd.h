@@ -195,7 +195,10 @@ int64_t hd_bvh_num_faces(const hd_bvh* bvh);
  * *out.  A is read according to A->on_device.  The frontier-parallel rounds run on the
  * GPU (nearest queries through the BVH, atomic lower bound, the exact case and the
  * u1..u4 cascade, compaction and 1->4 split); only the final bracket and statistics
- * come back to the host.  opt may be NULL (defaults). */
+ * come back to the host.  opt may be NULL (defaults).  Host arrays of A (on_device = 0) are
+ * copied on an upload stream of the library's own that does not wait for work queued earlier
+ * on `stream` (so the copy overlaps, say, B's asynchronous build); `stream` waits for the
+ * copy.  They must therefore hold their values when the call is made. */
 int hd_hausdorff(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
                  hd_result* out);
 

@@ -174,6 +174,20 @@ __global__ void k_upper_bounds(BvhDev B, const int* inv, const double* T, const 
 
 using namespace hd;
 
+// The stream and event that host arrays of A go up with, one pair per host thread and device
+// (created once, kept for the process): the copy then overlaps what the caller queued before
+// the call (B's asynchronous build, say), and the caller's stream waits for the event.
+static int upload_stream(int dev, cudaStream_t* up, cudaEvent_t* ev) {
+  static thread_local cudaStream_t st[64] = {};
+  static thread_local cudaEvent_t evs[64] = {};
+  if (dev < 0 || dev >= 64) return HD_ERR_INVALID;
+  if (!st[dev]) HD_TRY(cudaStreamCreateWithFlags(&st[dev], cudaStreamNonBlocking));
+  if (!evs[dev]) HD_TRY(cudaEventCreateWithFlags(&evs[dev], cudaEventDisableTiming));
+  *up = st[dev];
+  *ev = evs[dev];
+  return HD_OK;
+}
+
 // One-sided h(A, B) with l starting at l0 (a known lower bound of the quantity bracketed).
 static int hausdorff_one(const hd_bvh* B, const hd_mesh* A, double tol, const hd_options* opt, void* stream,
                          hd_result* out, double l0) {
@@ -194,10 +208,21 @@ static int hausdorff_one(const hd_bvh* B, const hd_mesh* A, double tol, const hd
   void* Vtmp = nullptr;
   int32_t* Ftmp = nullptr;
   if (!A->on_device) {
-    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, s));
-    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)A->nF * 12, s));
-    HD_TRY(cudaMemcpyAsync(Vtmp, A->V, vbytes, cudaMemcpyHostToDevice, s));
-    HD_TRY(cudaMemcpyAsync(Ftmp, A->F, (size_t)A->nF * 12, cudaMemcpyHostToDevice, s));
+    // on the upload stream (the stream-ordered frees below, on s, follow the wait)
+    cudaStream_t up = s;
+    cudaEvent_t ev = nullptr;
+    if (upload_stream(dev, &up, &ev) != HD_OK) {
+      up = s;
+      ev = nullptr;
+    }
+    HD_TRY(cudaMallocAsync(&Vtmp, vbytes, up));
+    HD_TRY(cudaMallocAsync((void**)&Ftmp, (size_t)A->nF * 12, up));
+    HD_TRY(cudaMemcpyAsync(Vtmp, A->V, vbytes, cudaMemcpyHostToDevice, up));
+    HD_TRY(cudaMemcpyAsync(Ftmp, A->F, (size_t)A->nF * 12, cudaMemcpyHostToDevice, up));
+    if (ev) {
+      HD_TRY(cudaEventRecord(ev, up));
+      HD_TRY(cudaStreamWaitEvent(s, ev, 0));
+    }
     VA = Vtmp;
     FA = Ftmp;
   }
