@@ -466,7 +466,10 @@ def run_ours(args):
     roof = roofline_of(main_kind)
     roof.update(dominant_kind=max(trace, key=lambda k: trace[k]["ms"]), share=share,
                 timing="CUDA events around each kernel kind, on the launching stream, over a second pass of "
-                       "the K steps (value_traced)")
+                       "the K steps (value_traced)",
+                choice="the traversal or bound kind with the largest traced time (the build, several kernels, "
+                       "has no single roofline); the query_long kind also times its list reordering "
+                       "(k_long_hist, k_long_scan, k_long_scatter: about 15% of the kind in the launch list)")
     roof_other = {k: roofline_of(k) for k in kinds if k != main_kind}
 
     launches = sum(build_launches(len(p.FB)) + int(r["stats"]["kernel_launches"]) for r in rs)  # the timed steps
