@@ -329,6 +329,47 @@ def test_every_bound_is_an_upper_bound(orc, seed):
         assert seen_case1
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_bounds_hold_for_any_points_of_B(orc, seed):
+    """The proofs of Section 3.2 (exact case, u1..u4) use each vertex's footpoint q_i only as a
+    point of B, so every bound stays an upper bound of h(T, B) when q_i is the closest point of
+    any triangle S_i of B instead of the nearest one.  That reading is what lets a vertex
+    query stop at a triangle that is merely close enough (cut queries).  Sampled h against
+    each bound, with S_i drawn at random (one S for all three vertices in a third of the cases,
+    so that the exact case applies), on a soup and on a closed mesh; and u1 at most the
+    longest edge at any vertex plus that vertex's distance, the inequality the cut relies on."""
+    rng = np.random.default_rng(300 + seed)
+    if seed % 2 == 0:
+        VB, FB = _random_small_mesh(rng, 12)
+    else:
+        VB, FB = mg.icosphere(1)
+        VB = VB * 0.8
+    W = bary_grid(24)
+    exact_seen = 0
+    for t in range(60):
+        kind = ["generic", "sliver", "tiny"][t % 3]
+        T = random_triangle(rng, kind) * (0.5 if kind == "generic" else 1.0)
+        if seed % 2 == 1:
+            T = T * 0.3 + rng.normal(size=3) * 0.6
+        I = np.full(3, rng.integers(len(FB))) if t % 3 == 0 else rng.integers(len(FB), size=3)
+        I = I.astype(np.int32)
+        d, q = np.zeros(3), np.zeros((3, 3))
+        for i in range(3):
+            a, b, c = (np.asarray(VB, float)[j] for j in FB[I[i]])
+            d[i], q[i] = orc.point_triangle(T[i], a, b, c)
+        bnd = orc.bounds_all(T, d, I, q, VB, FB)
+        ds, _, _ = orc.nearest(W @ T, VB, FB)
+        h = ds.max()
+        for k, name in enumerate(["exact", "u1", "u2", "u3", "u4"]):
+            if not np.isnan(bnd[k]):
+                assert h <= bnd[k] * (1 + 1e-12) + 1e-12, (name, t, h, bnd[k])
+        exact_seen += not np.isnan(bnd[0])
+        e = [np.linalg.norm(T[(i + 1) % 3] - T[i]) for i in range(3)]  # e[i]: edge from vertex i to i + 1
+        for i in range(3):
+            assert bnd[1] <= (max(e[i], e[(i + 2) % 3]) + d[i]) * (1 + 1e-12) + 1e-15
+    assert exact_seen >= 10
+
+
 # ----------------------------------------------------------------------------- full loop pins
 
 
